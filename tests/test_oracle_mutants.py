@@ -1,0 +1,91 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a temporary copy of the oracle's C source (a
+dropped term, a wrong index, a flipped tie-break, an off-by-one), builds it,
+swaps it in, and checks that at least one pin of test_oracle_pins fails.  The
+committed oracle is never modified.
+
+The pivot tie-break of the SCT recursion is not among the cases: any pivot
+yields a valid SCT and the paper's example is tie-free, so no fact of the
+paper fixes it; it is a convention that the CUDA parity tests cover.
+"""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle as O
+import test_oracle_pins as P
+
+MUTANTS = {
+    "pivot_cap_drops_the_minus_one": (
+        "uint64_t up_p = orc_binom(p - 1, k - h - 1, &ovf);       /* line 5 */",
+        "uint64_t up_p = orc_binom(p, k - h - 1, &ovf);       /* line 5 */"),
+    "zero_cap_nodes_kept_in_plateaus": (
+        "/* line 1: sort by r; R6: nodes without capacity take no part */\n"
+        "    int ns = 0;\n    for (int i = 0; i < len; ++i) if (up[i] > 0) srt[ns++] = i;",
+        "/* line 1: sort by r; R6: nodes without capacity take no part */\n"
+        "    int ns = 0;\n    for (int i = 0; i < len; ++i) srt[ns++] = i;"),
+    "remainder_to_highest_id": (
+        "for (uint64_t j = 0; j < nC; ++j) { r[A[j]] += 1; up[A[j]] -= 1; }",
+        "for (uint64_t j = 0; j < nC; ++j) { r[A[na - 1 - j]] += 1; up[A[na - 1 - j]] -= 1; }"),
+    "hold_branch_keeps_handled_candidates": (
+        "for (int j = 0; j < ncur; ++j) if (cur[j] != w) cur[q++] = cur[j];",
+        "for (int j = 0; j < ncur; ++j) cur[q++] = cur[j];"),
+    "prefix_event_one_position_early": (
+        "acc[mh + 1] += prev;", "acc[mh] += prev;"),
+    "argmax_ties_to_smallest_prefix": (
+        "if (frac_cmp(a, (uint64_t)i, b, (uint64_t)best) >= 0) best = i;",
+        "if (frac_cmp(a, (uint64_t)i, b, (uint64_t)best) > 0) best = i;"),
+    "clique_listing_skips_a_candidate": (
+        "for (int64_t j = i + 1; j < nc; ++j)\n            if (is_adj(c->off, c->adj, v, cand[j]))",
+        "for (int64_t j = i + 2; j < nc; ++j)\n            if (is_adj(c->off, c->adj, v, cand[j]))"),
+    "binomial_off_by_one": (
+        "v = v * (u128)(a - b + i) / (u128)i;",
+        "v = v * (u128)(a - b + i + 1) / (u128)i;"),
+    "plateau_gap_ignored": (
+        "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
+        "if (nC / (uint64_t)na < w)"),
+}
+
+PINS = [
+    P.test_g1_triangles_and_densest_subgraph,
+    P.test_g1_sct_matches_example_2_2,
+    P.test_g1_example_3_1_pbupdate_steps,
+    P.test_g1_psctl_extracts_densest,
+    P.test_g1_converges_to_sct_cp_optimum,
+    lambda: P.test_sct_partitions_the_k_cliques(O.ORDER_PEEL),
+    P.test_pbupdate_is_an_optimal_integer_allocation,
+    P.test_fw_invariants_and_weak_duality,
+    P.test_prefix_counts_from_pairs_equal_explicit_list,
+    P.test_argmax_takes_the_largest_prefix_on_ties,
+    lambda: P.test_brute_force_small_graphs(3),
+]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path, monkeypatch):
+    old, new = MUTANTS[name]
+    src = open(O.SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", str(so),
+                           str(path), "-lm"])
+    real = O.lib()
+    mutant = ctypes.CDLL(str(so))
+    # copy the ctypes signatures of the real library onto the mutant
+    for attr in dir(real):
+        if attr.startswith("orc_"):
+            f, g = getattr(real, attr), getattr(mutant, attr)
+            g.argtypes, g.restype = f.argtypes, f.restype
+    monkeypatch.setattr(O, "_lib", mutant)
+    caught = []
+    for pin in PINS:
+        try:
+            pin()
+        except (AssertionError, OverflowError, ValueError):
+            caught.append(getattr(pin, "__name__", "pin"))
+    assert caught, f"no pin failed for planted mistake {name}"

@@ -1,0 +1,366 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Nothing here re-derives the oracle's own formulas: every check compares the
+oracle with something independent of it -- values printed in the paper for its
+worked example (tests/golden/g1_example.txt), networkx, brute force over all
+subsets, an explicit clique listing, or a closed-form optimality condition.
+"""
+from fractions import Fraction
+from itertools import combinations
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from conftest import load_golden
+
+G = load_golden("g1_example.txt")
+
+
+def _pairs_from_golden(lines):
+    out = []
+    for ln in lines:
+        a, b = ln.split("|")
+        out.append((tuple(sorted(int(x) for x in a.split())),
+                    tuple(sorted(int(x) for x in b.split()))))
+    return sorted(out)
+
+
+def _g1():
+    n, s, d = synth.g1()
+    edges = [tuple(int(x) for x in e.split("-")) for e in G["edges"][0].split()]
+    assert sorted(map(tuple, map(sorted, zip(s.tolist(), d.tolist())))) == sorted(
+        tuple(sorted(e)) for e in edges)
+    return n, s, d
+
+
+def _graph(n, s, d, kind=O.ORDER_PEEL):
+    off, adj = O.csr(n, s, d)
+    core, rnd, dg = O.peel(n, off, adj)
+    rank, vert = O.order(n, core, rnd, kind)
+    return off, adj, core, rnd, dg, rank, vert
+
+
+# ---------------------------------------------------------------------------
+# The paper's worked example G1
+# ---------------------------------------------------------------------------
+
+def test_g1_triangles_and_densest_subgraph():
+    """Sec. 1 Example 1.1: 9 triangles on 7 nodes; {u1..u6} at 4/3 > 9/7."""
+    n, s, d = _g1()
+    off, adj, *_ = _graph(n, s, d)
+    cl = O.list_cliques(n, off, adj, 3)
+    assert len(cl) == int(G["triangles"][0])
+    masks = [sum(1 << int(v) for v in c) for c in cl]
+    bm, num, den, union = O.brute_best(n, masks, [1] * len(masks))
+    want = [int(x) for x in G["densest"][0].split()]
+    assert bm == sum(1 << v for v in want) and union == bm
+    assert Fraction(num, den) == Fraction(G["densest_density"][0])
+    assert Fraction(len(cl), n) == Fraction(G["whole_density"][0])
+
+
+def test_g1_sct_matches_example_2_2():
+    """Example 2.2: the five SCT pairs of G1 (vertex order u0 < ... < u6)."""
+    n, s, d = _g1()
+    off, adj, core, rnd, dg, rank, vert = _graph(n, s, d, O.ORDER_CORE)
+    assert vert.tolist() == list(range(7))
+    sc = O.sct(n, off, adj, rank, vert, 3)
+    assert O.canonical_pairs(sc) == _pairs_from_golden(G["pair"])
+
+
+def test_g1_example_3_1_pbupdate_steps():
+    """Example 3.1: P4 then P3 from r = 0 (lines 16 and 13 of Alg. 3)."""
+    r = np.zeros(7, np.uint64)
+    for step in ("ex31_step1", "ex31_step2"):
+        (hold, piv), = _pairs_from_golden(G[step + "_pair"])
+        ids = np.array(list(hold) + list(piv), np.int32)
+        delta = O.pbupdate_alg3(ids, r[ids], len(hold), 3)
+        got = {int(i): int(x) for i, x in zip(ids, delta) if x}
+        want = dict(tuple(map(int, t.split(":"))) for t in G[step + "_delta"][0].split())
+        assert got == want
+        r[ids] += delta
+
+
+def test_g1_psctl_extracts_densest():
+    """Alg. 2 on G1 returns {u1..u6} with 8 triangles (density 4/3)."""
+    n, s, d = _g1()
+    for kind in (O.ORDER_PEEL, O.ORDER_CORE):
+        res = O.solve(n, s, d, 3, 100, order_kind=kind)
+        assert res["istar"] == 6
+        assert res["ids"].tolist() == [int(x) for x in G["densest"][0].split()]
+        assert res["count"] == int(G["densest_count"][0])
+        assert res["c_k"] == int(G["triangles"][0])
+
+
+def test_g1_converges_to_sct_cp_optimum():
+    """r_T / T tends to the SCT-CP optimum r* = (1, 4/3 x 6) of G1: the
+    first batch H(r*) = {u1..u6} at rho_3 = 4/3 (Lemma 2.3 / Thm 3.3), and u0
+    keeps the one triangle it cannot hand to a denser node."""
+    n, s, d = _g1()
+    off, adj, core, rnd, dg, rank, vert = _graph(n, s, d, O.ORDER_CORE)
+    sc = O.sct(n, off, adj, rank, vert, 3)
+    T = 3000
+    r = O.fw_sync(n, sc, 3, T) / T
+    assert abs(r[0] - 1.0) < 1e-3
+    assert np.all(np.abs(r[1:] - 4.0 / 3.0) < 1e-3)
+
+
+# ---------------------------------------------------------------------------
+# A1-A2 against networkx
+# ---------------------------------------------------------------------------
+
+def test_csr_and_core_numbers_against_networkx():
+    nx = pytest.importorskip("networkx")
+    for seed in range(5):
+        n, s, d, _ = synth.chung_lu(400, 8.0, 2.3, seed, plant_size=15, plant_prob=0.8)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        Gx = nx.Graph()
+        Gx.add_nodes_from(range(n))
+        Gx.add_edges_from((int(a), int(b)) for a, b in zip(s, d) if a != b)
+        assert len(adj) == 2 * Gx.number_of_edges()
+        for v in range(n):
+            assert adj[off[v]:off[v + 1]].tolist() == sorted(Gx.neighbors(v))
+        cn = nx.core_number(Gx)
+        assert [cn[v] for v in range(n)] == core.tolist()
+        assert dg == max(cn.values())
+        # every vertex has at most core(v) later neighbours in the peel order
+        for v in range(n):
+            later = np.sum(rank[adj[off[v]:off[v + 1]]] > rank[v])
+            assert later <= core[v]
+
+
+# ---------------------------------------------------------------------------
+# The SCT against the explicit clique list (Lemmas 2.4-2.6)
+# ---------------------------------------------------------------------------
+
+def _expand(sc, k):
+    """All k-cliques encoded by the pairs (Lemma 2.5)."""
+    out = []
+    po, nodes, h = sc["pair_off"], sc["nodes"], sc["h"]
+    for q in range(len(h)):
+        seg = nodes[po[q]:po[q + 1]].tolist()
+        hold, piv = seg[:h[q]], seg[h[q]:]
+        for extra in combinations(piv, k - len(hold)):
+            out.append(tuple(sorted(hold + list(extra))))
+    return out
+
+
+@pytest.mark.parametrize("kind", [O.ORDER_PEEL, O.ORDER_CORE])
+def test_sct_partitions_the_k_cliques(kind):
+    rng = random.Random(7)
+    for trial in range(12):
+        n = rng.randint(15, 45)
+        p = rng.uniform(0.15, 0.5)
+        n, s, d = synth.erdos_renyi(n, p, 100 + trial)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d, kind)
+        adjset = {(int(a), int(b)) for a, b in zip(np.repeat(np.arange(n), np.diff(off)), adj)}
+        for k in (2, 3, 4, 5):
+            sc = O.sct(n, off, adj, rank, vert, k)
+            listed = sorted(map(tuple, O.list_cliques(n, off, adj, k).tolist()))
+            enc = _expand(sc, k)
+            assert len(enc) == len(set(enc)), "pairs overlap"          # disjoint
+            assert sorted(enc) == listed                               # cover
+            po, nodes, h = sc["pair_off"], sc["nodes"], sc["h"]
+            total_cap = 0
+            for q in range(len(h)):
+                seg = nodes[po[q]:po[q + 1]].tolist()
+                hh, pp = h[q], len(seg) - h[q]
+                assert hh <= k <= len(seg)                             # Lemma 2.5
+                assert all((a, b) in adjset for a, b in combinations(seg, 2))  # V(P) clique
+                # Lemma 2.6 per node, counted on the expanded cliques
+                cl_p = [set(seg[:hh]) | set(e) for e in combinations(seg[hh:], k - hh)]
+                for i, u in enumerate(seg):
+                    cnt = sum(1 for c in cl_p if u in c)
+                    cap = O.binom(pp, k - hh) if i < hh else O.binom(pp - 1, k - hh - 1)
+                    assert cnt == cap
+                    total_cap += cap
+            assert total_cap == k * len(listed)                        # sum of caps = k c_k
+
+
+# ---------------------------------------------------------------------------
+# PBUpdate: Alg. 3, one-clique-at-a-time greedy and the closed-form level
+# ---------------------------------------------------------------------------
+
+def _random_pair(rng):
+    k = rng.randint(2, 7)
+    h = rng.randint(1, k)
+    p = rng.randint(max(0, k - h), 9)
+    ln = h + p
+    ids = rng.sample(range(1000), ln)
+    spread = rng.choice([0, 1, 2, 5, 50, 10 ** 6])
+    r = [rng.randint(0, spread) for _ in range(ln)]
+    if rng.random() < 0.3:
+        r = [x - x % 3 for x in r]   # many ties
+    return np.array(ids, np.int32), np.array(r, np.uint64), h, k
+
+
+def test_pbupdate_three_restatements_agree():
+    """Alg. 3 (with reading R6) equals the per-clique greedy and the closed
+    form of the water level on 20,000 random pairs."""
+    rng = random.Random(11)
+    for _ in range(20000):
+        ids, r, h, k = _random_pair(rng)
+        a = O.pbupdate_alg3(ids, r, h, k)
+        b = O.pbupdate_greedy(ids, r, h, k)
+        c = O.pbupdate_level(ids, r, h, k)
+        assert a.tolist() == b.tolist() == c.tolist()
+
+
+def test_pbupdate_is_an_optimal_integer_allocation():
+    """KKT check of an allocation minimising the sum of squares under C3-C4:
+    all n_C units are placed, caps hold, and no unit can move from a node to
+    a node with spare capacity that ends lower by 2 or more."""
+    rng = random.Random(12)
+    for _ in range(5000):
+        ids, r, h, k = _random_pair(rng)
+        ln, p = len(ids), len(ids) - h
+        nC = O.binom(p, k - h)
+        cap = [O.binom(p, k - h)] * h + [O.binom(p - 1, k - h - 1)] * p
+        dl = O.pbupdate_alg3(ids, r, h, k).astype(object)
+        assert sum(dl) == nC
+        fin = [int(r[i]) + int(dl[i]) for i in range(ln)]
+        for i in range(ln):
+            assert 0 <= dl[i] <= cap[i]
+            if dl[i] == 0:
+                continue
+            for j in range(ln):
+                if dl[j] < cap[j]:
+                    assert fin[i] - 1 <= fin[j]
+
+
+def test_pbupdate_continuous_is_the_exact_water_level():
+    """Continuous rule: all units placed, caps hold, and every node that
+    receives weight ends at one common level L that no node with spare
+    capacity lies below."""
+    rng = random.Random(13)
+    for _ in range(3000):
+        ids, r, h, k = _random_pair(rng)
+        rr = r.astype(np.float64) + np.array([rng.random() for _ in r])
+        dl = O.pbupdate_cont(ids, rr, h, k)
+        ln, p = len(ids), len(ids) - h
+        nC = O.binom(p, k - h)
+        cap = [float(O.binom(p, k - h))] * h + [float(O.binom(p - 1, k - h - 1))] * p
+        assert abs(dl.sum() - nC) <= 1e-9 * max(1.0, nC)
+        fin = rr + dl
+        recv = [i for i in range(ln) if dl[i] > 1e-9 and dl[i] < cap[i] - 1e-9]
+        if recv:
+            L = fin[recv[0]]
+            for i in recv:
+                assert abs(fin[i] - L) <= 1e-6 * max(1.0, L)
+            for j in range(ln):
+                if dl[j] < cap[j] - 1e-9:
+                    assert fin[j] >= L - 1e-6 * max(1.0, L)
+
+
+# ---------------------------------------------------------------------------
+# FW invariants (Lemma 3.1, Thms 3.5-3.6) and brute force (Def. 2.1, Thm 3.4)
+# ---------------------------------------------------------------------------
+
+def _planted(n, p, size, seed):
+    n, s, d = synth.erdos_renyi(n, p, seed)
+    rng = random.Random(seed)
+    nodes = rng.sample(range(n), size)
+    extra = [(a, b) for a, b in combinations(nodes, 2) if rng.random() < 0.9]
+    s = np.concatenate([s, np.array([a for a, _ in extra], np.int32)])
+    d = np.concatenate([d, np.array([b for _, b in extra], np.int32)])
+    return n, s, d
+
+
+def test_fw_invariants_and_weak_duality():
+    """sum_u r_t(u) = t c_k and r_t(u) <= t cnt_k(u) (Lemma 3.1); the best
+    rho'(V_i) never exceeds max_u r_t(u)/t (weak duality, Thms 3.5-3.6); the
+    extracted rho_k never exceeds the Alg. 1 bound max_u r^CP_t(u)/t."""
+    for seed in range(4):
+        n, s, d = _planted(40, 0.15, 10, 50 + seed)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        for k in (3, 4):
+            sc = O.sct(n, off, adj, rank, vert, k)
+            cl = O.list_cliques(n, off, adj, k)
+            ck = len(cl)
+            cnt = np.bincount(cl.reshape(-1), minlength=n) if ck else np.zeros(n, int)
+            rcp = O.fw_cliques(n, cl, k, 50)
+            for t in (1, 2, 3, 7, 20):
+                r = O.fw_sync(n, sc, k, t)
+                assert int(r.astype(object).sum()) == t * ck
+                assert np.all(r.astype(np.int64) <= t * cnt)
+                ordr = O.sort_desc(r)
+                lo, hi, flo, fhi = O.prefix_counts_pairs(n, ordr, sc, k)
+                best_rp = max(Fraction(int(flo[i]), i) for i in range(1, n + 1))
+                assert best_rp <= Fraction(int(r.max()), t)
+                i = O.argmax_density(lo, hi)
+                assert Fraction(int(lo[i]), i) <= Fraction(int(rcp.max()), 50)
+
+
+def test_prefix_counts_from_pairs_equal_explicit_list():
+    """C_k(V_i) from the SCT pairs (Lemma 2.5-2.6) equals the explicit count."""
+    rng = np.random.default_rng(3)
+    for seed in range(5):
+        n, s, d = _planted(50, 0.12, 12, 80 + seed)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        for k in (2, 3, 5):
+            sc = O.sct(n, off, adj, rank, vert, k)
+            cl = O.list_cliques(n, off, adj, k)
+            ordr = rng.permutation(n).astype(np.int32)
+            a, ah = O.prefix_counts_cliques(n, ordr, cl, k)
+            b, bh, _, _ = O.prefix_counts_pairs(n, ordr, sc, k)
+            assert a.tolist() == b.tolist() and ah.tolist() == bh.tolist()
+
+
+def test_argmax_takes_the_largest_prefix_on_ties():
+    lo = np.array([0, 1, 2, 3, 3, 5, 6], np.uint64)   # 1/1 = 2/2 = 3/3 = 6/6
+    hi = np.zeros(7, np.uint64)
+    assert O.argmax_density(lo, hi) == 6
+    lo = np.array([0, 0, 3, 3, 4], np.uint64)          # 3/2 > 3/3, 4/4
+    assert O.argmax_density(lo, np.zeros(5, np.uint64)) == 2
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_brute_force_small_graphs(k):
+    """n <= 14: the k-clique densest subgraph V* (Def. 2.1, maximal on ties)
+    by enumeration of all subsets; PSCTL after many iterations meets the
+    bound of Thm 3.4 and max_u r/T tends to max_S rho'(S) (Thms 3.5-3.6);
+    Alg. 1 (CP(G), Lemma 2.3) extracts V* itself."""
+    for seed in range(6):
+        n, s, d = _planted(12 + seed % 3, 0.25, 6, 200 + seed + 10 * k)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        cl = O.list_cliques(n, off, adj, k)
+        if len(cl) == 0:
+            continue
+        masks = [sum(1 << int(v) for v in c) for c in cl]
+        bm, num, den, union = O.brute_best(n, masks, [1] * len(masks))
+        assert union == bm                      # the maximal V* contains all maximisers
+        rho_star = Fraction(num, den)
+        sc = O.sct(n, off, adj, rank, vert, k)
+        pm, ph = sc["pair_off"], sc["h"]
+        pmasks, pw = [], []
+        for q in range(len(ph)):
+            seg = sc["nodes"][pm[q]:pm[q + 1]]
+            pmasks.append(sum(1 << int(v) for v in seg))
+            pw.append(O.binom(len(seg) - ph[q], k - ph[q]))
+        _, pn, pd, _ = O.brute_best(n, pmasks, pw)
+        rho_p = Fraction(pn, pd)
+        assert rho_p <= rho_star                # rho'(S) <= rho_k(S)
+        T = 4000
+        res_r = O.fw_sync(n, sc, k, T)
+        ordr = O.sort_desc(res_r)
+        lo, hi, _, _ = O.prefix_counts_pairs(n, ordr, sc, k)
+        i = O.argmax_density(lo, hi)
+        got = Fraction(int(lo[i]), i)
+        assert got > rho_star * (1 - Fraction(1, k * den))                # Thm 3.4
+        ub = Fraction(int(res_r.max()), T)
+        assert ub >= rho_p and float(ub) <= float(rho_p) * 1.02 + 1e-9     # Thm 3.5-3.6
+        rcp = O.fw_cliques(n, cl, k, T)
+        o2 = O.sort_desc(rcp)
+        lo2, hi2 = O.prefix_counts_cliques(n, o2, cl, k)
+        i2 = O.argmax_density(lo2, hi2)
+        assert sorted(o2[:i2].tolist()) == [v for v in range(n) if bm >> v & 1]
+
+
+def test_sequential_and_synchronous_reach_the_same_density():
+    """Both readings of Alg. 2's pair loop reach the paper's density on G1."""
+    n, s, d = _g1()
+    a = O.solve(n, s, d, 3, 50, mode="seq")
+    b = O.solve(n, s, d, 3, 50, mode="sync")
+    assert a["istar"] == b["istar"] == 6 and a["count"] == b["count"] == 8
