@@ -812,12 +812,12 @@ int orc_brute_best(int n, int64_t nitems, const uint32_t *masks, const uint64_t 
     u128 bn = 0; uint64_t bd = 1; uint32_t bm = 0, uni = 0;
     for (size_t S = 1; S < N; ++S) {
         uint64_t d = (uint64_t)__builtin_popcount((unsigned)S);
-        int c = frac_cmp(F[S], bd, bn, d);
+        int c = frac_cmp(F[S], d, bn, bd);
         if (c > 0 || (c == 0 && d > bd)) { bn = F[S]; bd = d; bm = (uint32_t)S; }
     }
     for (size_t S = 1; S < N; ++S) {
         uint64_t d = (uint64_t)__builtin_popcount((unsigned)S);
-        if (frac_cmp(F[S], bd, bn, d) == 0) uni |= (uint32_t)S;
+        if (frac_cmp(F[S], d, bn, bd) == 0) uni |= (uint32_t)S;
     }
     *best_mask = bm; *best_num = (uint64_t)bn; *best_den = bd; *union_of_maximisers = uni;
     free(F);
