@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the PSCTL hot path on GB300.
+
+One step = the whole path on one synthetic graph already resident in device
+memory: CSR build and peeling (A1-A2), SCT build (A3), T Frank-Wolfe
+iterations of PBUpdate (A4-A5) and the densest-prefix extraction (A6).  The
+metric is clique-updates/s = T * c_k / step time (every iteration settles the
+c_k k-cliques the SCT encodes).  L2 is flushed (a 256 MiB write) before every
+step, outside the step's event pair.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (launched by torch.distributed.run);
+the whole-job value is the units of all ranks over the slowest rank's time.
+`--impl reference` times the CPU oracle on the host cores instead (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "SCT clique-updates/s and time to 1%-density; batched FP32 vs plain FP64; p99"
+UNIT = "clique-updates/s"
+
+WORKLOADS = {
+    "chunglu1e5": dict(
+        gen=synth.workload_chunglu_1e5, k=5, T=200,
+        desc="Chung-Lu power-law graph n=100000, mean degree 20, exponent 2.5, planted "
+             "60-node near-clique at p=0.9, seed 2; k=5; T=200 FW iterations"),
+    "er2000": dict(
+        gen=synth.workload_er2000, k=3, T=100,
+        desc="Erdos-Renyi G(2000, 0.01), seed 1; k=3; T=100 FW iterations"),
+}
+
+PRECISIONS = {"fp64": 1, "int64": 0, "fp32k": 2}
+DTYPE = {"fp64": "f64", "int64": "u64", "fp32k": "f32"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chunglu1e5")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP32 and time-to-1%% side measurements")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_src):
+    """Per-launch DRAM bytes of the PBUpdate pass from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "fw_pbupdate_chunglu1e5.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_iteration:\s*([0-9.eE+]+)", text)
+    h = re.search(r"fw\.cu sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m.group(1)) if cur == h.group(1) else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        pw = [float(r[3]) for r in rows if re.match(r"^[0-9.]+$", r[3])]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def gpu_id_for_smi(torch, dev):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if dev < len(ids):
+            return ids[dev]
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else f"GPU-{u}"
+    except Exception:
+        return dev
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    wl = WORKLOADS[args.workload]
+    n, s, d = wl["gen"]()
+    k = wl["k"]
+    T_ref = 50 if args.workload == "chunglu1e5" else wl["T"]
+    times = []
+    ck = None
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = O.solve(n, s, d, k, T_ref)
+        dt = time.perf_counter() - t0
+        ck = res["c_k"]
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = T_ref * ck * len(times) / tot
+    sample = (f"oracle (single-threaded C): CSR, peeling, SCT, {T_ref} synchronous "
+              f"rule-I iterations and extraction of the {args.workload} workload per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"].replace(f"T={wl['T']}", f"T={T_ref}"),
+                       "k": k, "T": T_ref, "n": n, "c_k": ck},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2403_05775_gb300 as K
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    K.load(build_if_missing=True)
+    wl = WORKLOADS[args.workload]
+    n, s_np, d_np = wl["gen"]()
+    k, T = wl["k"], wl["T"]
+    prec = PRECISIONS[args.precision]
+
+    # CPU baseline first (rank 0, N = 1 only), so the host is idle during GPU timing.
+    cpu = None
+    rho_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        t0 = time.perf_counter()
+        ores = O.solve(n, s_np, d_np, k, T)
+        dt = time.perf_counter() - t0
+        rho_oracle = ores["density"]
+        cpu = {"value": T * ores["c_k"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the whole {args.workload} workload once (CSR, peeling, SCT, {T} "
+                         f"synchronous rule-I iterations, extraction), single-threaded C, "
+                         f"{dt:.1f} s"}
+
+    stream = torch.cuda.current_stream(dev)
+    src = torch.from_numpy(s_np).to(dev)
+    dst = torch.from_numpy(d_np).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(flags):
+        o = K.make_opts(precision=prec, flags=flags, stream=stream)
+        sct = K.kdss_build_sct(n, src, dst, k, o)
+        st = K.kdss_fw_iterate(sct, None, T, o)
+        res = K.kdss_extract(sct, st, o)
+        tm = K.kdss_state_timing(st)
+        info = K.kdss_sct_info(sct)
+        st.free()
+        sct.free()
+        return res, tm, info
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step(0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    fw_ms, fw_launches = 0.0, 0
+    launches0 = K.kdss_kernel_launches()
+    with ClockSampler(gpu_id_for_smi(torch, local)) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            res, tm, info = step(K.KDSS_FLAG_PROFILE)
+            ev[i][1].record(stream)
+            fw_ms += tm["fw_kernel_ms"]
+            fw_launches += tm["fw_launches"]
+        torch.cuda.synchronize()
+    launches = K.kdss_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ck = info["c_k"]
+    units = T * ck * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 3))):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r2 = K.kdss_solve(n, s_np, d_np, k, T, K.make_opts(precision=prec, stream=stream))
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = T * ck * world / (statistics.mean(e2e_ms) / 1e3)
+    h2d = int(s_np.nbytes + d_np.nbytes)
+    d2h = int(4 * r2["istar"] + 88)
+
+    # roofline of the PBUpdate pass (all length-class kernels of one iteration)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 4 * info["L_k"] + 9 * info["eta_k"]
+    avg_s = (fw_ms / max(fw_launches, 1)) / 1e3
+    achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
+    traffic = ncu_traffic(os.path.join(ROOT, "paper_2403_05775_gb300", "csrc", "fw.cu"))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "k": k, "T": T, "n": n, "m": info["m"],
+                   "eta_k": info["eta_k"], "L_k": info["L_k"], "c_k": ck,
+                   "degeneracy": info["degeneracy"], "precision": args.precision,
+                   "rule": "continuous" if args.precision == "fp32k" else "integer (Alg. 3)",
+                   "l2": "flushed by a 256 MiB write before every step",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_pbupdate_int (one FW iteration, all length classes)",
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+        "result": {"istar": res["istar"], "count": res["count"], "density": res["density"],
+                   "upper_bound": res["upper_bound"], "gap": res["gap"]},
+    }
+
+    if rank == 0 and not args.no_extras:
+        extras = {}
+        # FP32 compensated continuous rule on the same workload
+        o32 = K.make_opts(precision=PRECISIONS["fp32k"], stream=stream)
+        t32 = []
+        for _ in range(2):
+            flush.fill_(5)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sct = K.kdss_build_sct(n, src, dst, k, o32)
+            st = K.kdss_fw_iterate(sct, None, T, o32)
+            r32 = K.kdss_extract(sct, st, o32)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t32.append(a.elapsed_time(b))
+            st.free()
+            sct.free()
+        extras["fp32k"] = {"value": T * ck / (min(t32) / 1e3), "unit": UNIT,
+                           "ms_per_step": min(t32), "density": r32["density"],
+                           "istar": r32["istar"]}
+        # time to reach 99% of the oracle's density: build, then chunks of 5
+        # iterations each followed by an extraction
+        target = rho_oracle if rho_oracle is not None else res["density"]
+        o = K.make_opts(precision=prec, stream=stream)
+        flush.fill_(7)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sct = K.kdss_build_sct(n, src, dst, k, o)
+        st, it, dens = None, 0, 0.0
+        while it < T:
+            st = K.kdss_fw_iterate(sct, st, 5, o)
+            it += 5
+            dens = K.kdss_extract(sct, st, o)["density"]
+            if dens >= 0.99 * target:
+                break
+        torch.cuda.synchronize()
+        extras["time_to_1pct_density"] = {
+            "ms": 1e3 * (time.perf_counter() - t0), "iterations": it, "density": dens,
+            "target": 0.99 * target,
+            "target_source": "oracle density after T iterations" if rho_oracle else "own T"}
+        st.free()
+        sct.free()
+        line["extras"] = extras
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

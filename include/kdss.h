@@ -1,0 +1,260 @@
+/*
+ * kdss.h -- C ABI of the GB300 PSCTL solver (k-clique densest subgraph
+ * search by Frank-Wolfe over the succinct clique tree, arxiv 2403.05775).
+ *
+ * Pipeline (the paper's three steps, Fig. 1): build the SCT index of the
+ * k-cliques (Sec. 2), run Frank-Wolfe iterations of PBUpdate over its pairs
+ * (Alg. 2-3), sort the nodes by r and return the densest prefix (Alg. 2
+ * lines 5-7).  Every step runs in CUDA kernels on one GPU; this header is the
+ * only boundary.  No C++ or torch types cross it.
+ *
+ * Conventions
+ *  - Status: every entry point returns kdss_status (0 = OK, < 0 = error) and
+ *    never throws.  kdss_last_error() gives a thread-local message for the
+ *    last failing call of the calling thread.
+ *  - Ownership: kdss_sct, kdss_state and the ids array of kdss_result are
+ *    owned by the library and released with the matching _free call.  Input
+ *    arrays are borrowed for the duration of the call only.
+ *  - Streams: all device work of a call is ordered on opts->stream (a
+ *    cudaStream_t; NULL = the legacy default stream).  Calls return after
+ *    that stream has finished the call's work, so host results are final.
+ *  - Memory: device memory comes from opts->alloc / opts->free when set
+ *    (e.g. a framework's caching allocator), otherwise from
+ *    cudaMallocAsync / cudaFreeAsync on the stream.  A handle remembers the
+ *    allocator it was created with and frees through it.
+ *  - Threads: calls on distinct handles may run concurrently on distinct
+ *    streams; a handle must not be used by two calls at once.
+ *  - Node ids are int32 in [0, n); n < 2^31 - 1.
+ */
+#ifndef KDSS_H
+#define KDSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t kdss_status;
+#define KDSS_OK 0
+#define KDSS_ERR_INVALID_ARG (-1)   /* bad k, T, size, NULL pointer, option */
+#define KDSS_ERR_BAD_GRAPH (-2)     /* an edge endpoint outside [0, n) */
+#define KDSS_ERR_OOM (-3)           /* device allocation failed */
+#define KDSS_ERR_OVERFLOW (-4)      /* a count needs more than 64 bits */
+#define KDSS_ERR_TIMEOUT (-5)       /* a bounded device wait expired */
+#define KDSS_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define KDSS_ERR_CANCELLED (-7)     /* a batch query was cancelled */
+#define KDSS_ERR_UNSUPPORTED (-8)   /* e.g. a pair longer than the kernels take */
+
+/* Representation of the per-node ranking r (Table 2: r(u), the weight a node
+ * collected).  KDSS_INT64: exact uint64 cumulative r (rule I).  KDSS_FP64: the
+ * same integers held in double (exact below 2^53).  KDSS_FP32K: normalised
+ * r/t in float with compensated (error-free) scatter sums, continuous rule. */
+#define KDSS_INT64 0
+#define KDSS_FP64 1
+#define KDSS_FP32K 2
+
+/* Vertex order of the SCT build.  PEEL: key (peel round, id), a degeneracy
+ * order (every vertex has at most core(v) <= delta later neighbours).  CORE:
+ * key (core number, id); reproduces the paper's Example 2.2 on its graph G1
+ * but bounds the out-degree only by the maximum degree. */
+#define KDSS_ORDER_PEEL 0
+#define KDSS_ORDER_CORE 1
+
+/* flags */
+#define KDSS_FLAG_PROFILE 1u        /* time every FW kernel with CUDA events */
+#define KDSS_FLAG_KEEP_GRAPH 2u     /* keep the CSR, cores and order in the SCT handle */
+
+typedef void *(*kdss_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*kdss_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+typedef struct kdss_opts {
+    int32_t precision;      /* KDSS_INT64 | KDSS_FP64 | KDSS_FP32K */
+    int32_t order;          /* KDSS_ORDER_PEEL | KDSS_ORDER_CORE */
+    uint32_t flags;         /* KDSS_FLAG_* */
+    int32_t check_every;    /* solve calls: evaluate the stop rule every j iterations (0 = never) */
+    double eps_stop;        /* solve calls: stop once 1 - rho'_max / max r-hat <= eps_stop */
+    void *stream;           /* cudaStream_t; NULL = legacy default stream */
+    kdss_alloc_fn alloc;    /* optional device allocator (NULL: cudaMallocAsync) */
+    kdss_free_fn free;      /* must be set together with alloc */
+    void *alloc_ctx;        /* passed back to alloc / free */
+} kdss_opts;
+
+/* An undirected graph as a raw edge list.  Duplicates, both orientations and
+ * self-loops are allowed; the build drops self-loops and duplicates (Sec. 2's
+ * simple graph G(V, E)).  src/dst are host pointers, or device pointers when
+ * on_device != 0. */
+typedef struct kdss_graph_desc {
+    int64_t n;
+    int64_t m;
+    const int32_t *src;
+    const int32_t *dst;
+    int32_t on_device;
+} kdss_graph_desc;
+
+typedef struct kdss_sct kdss_sct;       /* opaque: device-resident SCT of one (G, k) */
+typedef struct kdss_state kdss_state;   /* opaque: device-resident FW state (t, r) */
+
+typedef struct kdss_sct_stats {
+    int64_t n;              /* nodes */
+    int64_t m;              /* undirected edges of the simple graph */
+    int64_t eta_k;          /* |P_k| pairs (Lemma 2.5) */
+    int64_t L_k;            /* sum over pairs of |V(P)| */
+    uint64_t c_k_lo;        /* |C_k(V)| = sum of n_C (Lemma 2.6), low 64 bits */
+    uint64_t c_k_hi;        /* high 64 bits */
+    int32_t k;
+    int32_t degeneracy;     /* delta = max core number */
+    int32_t max_out_degree; /* of the oriented graph used by the build */
+    int32_t max_pair_len;   /* max |V(P)| */
+    int64_t device_bytes;   /* device memory held by the handle */
+    int64_t pairs_per_class[8]; /* pairs per length class of the FW kernels
+                                   (|V(P)| <= 8, 16, 32, 256, 1024) */
+} kdss_sct_stats;
+
+typedef struct kdss_result {
+    int64_t istar;          /* size of the returned prefix V_{i*} */
+    int32_t *ids;           /* host array of the istar node ids, ascending (library-owned) */
+    uint64_t count_lo;      /* |C_k(V_{i*})| exact, low 64 bits */
+    uint64_t count_hi;      /* high 64 bits */
+    double density;         /* rho_k(V_{i*}) = count / istar */
+    double upper_bound;     /* max_u r(u)/t (FP64) */
+    double rho_prime;       /* max_i rho'(V_i) of the sorted prefixes (Thm 3.6) */
+    double gap;             /* 1 - rho_prime / upper_bound (>= 0 by Thms 3.5-3.6) */
+    int32_t T;              /* iterations requested */
+    int32_t t_used;         /* iterations run */
+    kdss_status status;     /* per-query status in batch calls */
+    int32_t reserved;
+} kdss_result;
+
+typedef struct kdss_timing {
+    double fw_kernel_ms;    /* summed event time of the PBUpdate kernels */
+    double step_kernel_ms;  /* summed event time of the step kernels */
+    int64_t fw_launches;    /* PBUpdate kernel launches timed */
+    int64_t step_launches;
+} kdss_timing;
+
+/*
+ * kdss_build_sct -- steps A1-A3: simple graph in CSR, core numbers and vertex
+ * order, and the SCT restricted to P_k (Sec. 2, Lemmas 2.4-2.6): pairs
+ * (V_h, V_p) with |V_h| <= k <= |V(P)| whose k-cliques partition C_k(V).
+ *   g    : the input graph (host or device edge list).
+ *   k    : clique size, 2 <= k <= 64.
+ *   opts : stream, allocator, order.
+ *   out  : receives the new handle (NULL on error).
+ * Errors: INVALID_ARG (k, n, m, NULL), BAD_GRAPH (id outside [0, n)),
+ *   OVERFLOW (a binomial count needs more than 64 bits), UNSUPPORTED (a pair
+ *   longer than 1024 nodes), OOM, CUDA.
+ */
+kdss_status kdss_build_sct(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts,
+                           kdss_sct **out);
+
+/*
+ * kdss_sct_from_pairs -- make an SCT handle from caller-given pairs, so the
+ * FW and extraction steps can run on an SCT built elsewhere.  Pair q holds
+ * nodes[pair_off[q] .. pair_off[q+1]) with its first h[q] entries the hold
+ * set V_h and the rest the pivot set V_p (Sec. 2, Lemma 2.4); 0 <= h <= k <=
+ * |V(P)| <= 1024 is required.  Arrays are host pointers, or device pointers when
+ * on_device != 0; they are copied.
+ * Errors: INVALID_ARG (sizes, h, k, ids outside [0, n)), OVERFLOW, OOM, CUDA.
+ */
+kdss_status kdss_sct_from_pairs(int64_t n, int32_t k, int64_t npairs, const int64_t *pair_off,
+                                const int32_t *nodes, const int32_t *h, int32_t on_device,
+                                const kdss_opts *opts, kdss_sct **out);
+
+/* kdss_sct_info -- sizes of the handle (eta_k, L_k, c_k, delta ...). */
+kdss_status kdss_sct_info(const kdss_sct *s, kdss_sct_stats *out);
+
+/*
+ * kdss_sct_copy_pairs -- copy the pairs to host buffers of eta_k + 1, L_k and
+ * eta_k entries.  Layout as stored on the device: pairs grouped by length
+ * class, within a pair the nodes ascending by id with bit 31 set on hold
+ * (V_h) nodes; h[q] = |V_h|.
+ */
+kdss_status kdss_sct_copy_pairs(const kdss_sct *s, int64_t *pair_off, int32_t *nodes,
+                                int32_t *h);
+
+/*
+ * kdss_sct_copy_graph -- copy step A1-A2 outputs to host buffers: CSR offsets
+ * (n + 1) and neighbours (2 m), core numbers, peel rounds and the rank of
+ * every vertex in the build order (n each).  Any pointer may be NULL.  Only
+ * for handles built with KDSS_FLAG_KEEP_GRAPH (INVALID_ARG otherwise).
+ */
+kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, int32_t *core,
+                                int32_t *round_, int32_t *rank);
+
+/*
+ * kdss_fw_iterate -- step A4-A5: T Frank-Wolfe iterations of Alg. 2 with the
+ * PBUpdate rule of Alg. 3 over every pair, all pairs of iteration t reading
+ * r_{t-1} (synchronous form); the remainder units of Alg. 3 line 16 go to the
+ * lowest node ids; r_0 = 0.  *state is created when NULL (precision from
+ * opts), otherwise continued from its iteration count t.
+ *   s     : SCT handle.
+ *   state : in/out FW state.
+ *   T     : iterations to run, T >= 0.
+ * Errors: INVALID_ARG, OVERFLOW (r would leave the exact range), OOM, CUDA.
+ */
+kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts);
+
+/*
+ * kdss_state_copy_r -- copy r to a host buffer of n entries: uint64 for
+ * KDSS_INT64 (cumulative r_t), double for KDSS_FP64 (cumulative r_t), float
+ * for KDSS_FP32K (normalised r_t / t).  *t_out receives t (may be NULL).
+ */
+kdss_status kdss_state_copy_r(const kdss_state *st, void *r_host, int32_t *t_out);
+
+/* kdss_state_timing -- event times of the FW kernels (KDSS_FLAG_PROFILE). */
+kdss_status kdss_state_timing(const kdss_state *st, kdss_timing *out);
+
+/*
+ * kdss_extract -- step A6 (Alg. 2 lines 5-7): sort the nodes by r
+ * non-increasing (ties by ascending id), count the k-cliques of every prefix
+ * V_i exactly from the pairs (Lemmas 2.5-2.6), and return the prefix of
+ * largest rho_k(V_i) = |C_k(V_i)| / i (largest i on ties), with the bound
+ * max_u r(u)/t and max_i rho'(V_i) (Thms 3.5-3.6).
+ * out->ids is a library-owned host array (kdss_result_free).
+ * Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
+ */
+kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opts *opts,
+                         kdss_result *out);
+
+/* kdss_solve -- build, T iterations and extraction in one call. */
+kdss_status kdss_solve(const kdss_graph_desc *g, int32_t k, int32_t T, const kdss_opts *opts,
+                       kdss_result *out);
+
+/* One query of a batch. */
+typedef struct kdss_query {
+    kdss_graph_desc graph;
+    int32_t k;
+    int32_t T;
+} kdss_query;
+
+/*
+ * kdss_solve_batch -- solve nq independent (graph, k, T) queries.  The SCTs
+ * are built per query, then the FW iterations of all queries run together in
+ * one launch per iteration over the concatenated pairs (queries that reached
+ * their T are masked), and one segmented sort and scan extract every query.
+ * out[i] receives query i's result and status.  Returns the first error, or
+ * OK when every query succeeded.
+ */
+kdss_status kdss_solve_batch(const kdss_query *q, int32_t nq, kdss_result *out,
+                             const kdss_opts *opts);
+
+void kdss_sct_free(kdss_sct *s);
+void kdss_state_free(kdss_state *st);
+void kdss_result_free(kdss_result *r);   /* frees r->ids; the struct is caller-owned */
+
+/* Thread-local message of the calling thread's last error ("" if none). */
+const char *kdss_last_error(void);
+
+/* Library version string. */
+const char *kdss_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads); the difference of two calls counts the launches between. */
+int64_t kdss_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDSS_H */

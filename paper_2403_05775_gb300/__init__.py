@@ -1,0 +1,387 @@
+"""GB300 PSCTL solver: k-clique densest subgraph search by Frank-Wolfe over
+the succinct clique tree (arxiv 2403.05775).
+
+This package is a thin ctypes binding of ``libkdss.so`` (``include/kdss.h``):
+the Python functions carry the C entry points' names and only marshal
+arguments.  Every step of the path -- CSR build, peeling, SCT build, PBUpdate
+iterations, extraction -- runs in the library's CUDA kernels.  PyTorch, when
+present, supplies the CUDA stream and the device memory (its caching
+allocator); without it the library allocates stream-ordered memory itself.
+There is no CPU fallback: without the built library every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build_ext
+
+KDSS_OK = 0
+KDSS_ERR_INVALID_ARG = -1
+KDSS_ERR_BAD_GRAPH = -2
+KDSS_ERR_OOM = -3
+KDSS_ERR_OVERFLOW = -4
+KDSS_ERR_TIMEOUT = -5
+KDSS_ERR_CUDA = -6
+KDSS_ERR_CANCELLED = -7
+KDSS_ERR_UNSUPPORTED = -8
+
+KDSS_INT64 = 0
+KDSS_FP64 = 1
+KDSS_FP32K = 2
+KDSS_ORDER_PEEL = 0
+KDSS_ORDER_CORE = 1
+KDSS_FLAG_PROFILE = 1
+KDSS_FLAG_KEEP_GRAPH = 2
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class kdss_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("order", C.c_int32), ("flags", C.c_uint32),
+                ("check_every", C.c_int32), ("eps_stop", C.c_double), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class kdss_graph_desc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("on_device", C.c_int32)]
+
+
+class kdss_sct_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("eta_k", C.c_int64), ("L_k", C.c_int64),
+                ("c_k_lo", C.c_uint64), ("c_k_hi", C.c_uint64), ("k", C.c_int32),
+                ("degeneracy", C.c_int32), ("max_out_degree", C.c_int32),
+                ("max_pair_len", C.c_int32), ("device_bytes", C.c_int64),
+                ("pairs_per_class", C.c_int64 * 8)]
+
+
+class kdss_result(C.Structure):
+    _fields_ = [("istar", C.c_int64), ("ids", C.POINTER(C.c_int32)), ("count_lo", C.c_uint64),
+                ("count_hi", C.c_uint64), ("density", C.c_double), ("upper_bound", C.c_double),
+                ("rho_prime", C.c_double), ("gap", C.c_double), ("T", C.c_int32),
+                ("t_used", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class kdss_timing(C.Structure):
+    _fields_ = [("fw_kernel_ms", C.c_double), ("step_kernel_ms", C.c_double),
+                ("fw_launches", C.c_int64), ("step_launches", C.c_int64)]
+
+
+class kdss_query(C.Structure):
+    _fields_ = [("graph", kdss_graph_desc), ("k", C.c_int32), ("T", C.c_int32)]
+
+
+class KdssError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"kdss error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return build_ext.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libkdss.so.  Raises when the library is not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build_ext.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(
+                    "libkdss.so is not built; run __graft_entry__.build() "
+                    "(the solver has no CPU fallback)")
+            build_ext.build()
+        L = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        P = C.POINTER
+        sig = {
+            "kdss_build_sct": (i32, [P(kdss_graph_desc), i32, P(kdss_opts), P(vp)]),
+            "kdss_sct_from_pairs": (i32, [i64, i32, i64, vp, vp, vp, i32, P(kdss_opts), P(vp)]),
+            "kdss_sct_info": (i32, [vp, P(kdss_sct_stats)]),
+            "kdss_sct_copy_pairs": (i32, [vp, vp, vp, vp]),
+            "kdss_sct_copy_graph": (i32, [vp, vp, vp, vp, vp, vp]),
+            "kdss_fw_iterate": (i32, [vp, P(vp), i32, P(kdss_opts)]),
+            "kdss_state_copy_r": (i32, [vp, vp, P(i32)]),
+            "kdss_state_timing": (i32, [vp, P(kdss_timing)]),
+            "kdss_extract": (i32, [vp, vp, P(kdss_opts), P(kdss_result)]),
+            "kdss_solve": (i32, [P(kdss_graph_desc), i32, i32, P(kdss_opts), P(kdss_result)]),
+            "kdss_solve_batch": (i32, [P(kdss_query), i32, P(kdss_result), P(kdss_opts)]),
+            "kdss_sct_free": (None, [vp]),
+            "kdss_state_free": (None, [vp]),
+            "kdss_result_free": (None, [P(kdss_result)]),
+            "kdss_last_error": (C.c_char_p, []),
+            "kdss_version": (C.c_char_p, []),
+            "kdss_kernel_launches": (i64, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != KDSS_OK:
+        msg = load().kdss_last_error()
+        raise KdssError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# torch plumbing: stream and caching allocator
+# ---------------------------------------------------------------------------
+
+def _torch():
+    try:
+        import torch
+        return torch if torch.cuda.is_available() else None
+    except Exception:  # pragma: no cover - torch is optional
+        return None
+
+
+_torch_api = {}
+
+
+def _torch_alloc(size, stream, ctx):
+    try:
+        return _torch_api["alloc"](int(size), stream=int(stream or 0))
+    except Exception:  # reported to the library as a failed allocation
+        return None
+
+
+def _torch_free(ptr, size, stream, ctx):
+    try:
+        _torch_api["free"](int(ptr))
+    except Exception:  # interpreter shutdown: the process releases the memory
+        pass
+
+
+_ALLOC_CB = ALLOC_FN(_torch_alloc)
+_FREE_CB = FREE_FN(_torch_free)
+
+
+def make_opts(precision=KDSS_INT64, order=KDSS_ORDER_PEEL, flags=0, stream=None,
+              allocator="torch", check_every=0, eps_stop=0.0) -> kdss_opts:
+    """Build a kdss_opts.  stream: a torch.cuda.Stream, a raw cudaStream_t
+    (int) or None (torch's current stream when torch is present).
+    allocator: 'torch' (caching allocator) or 'library' (cudaMallocAsync)."""
+    o = kdss_opts()
+    o.precision, o.order, o.flags = precision, order, flags
+    o.check_every, o.eps_stop = check_every, eps_stop
+    t = _torch()
+    if stream is None and t is not None:
+        stream = t.cuda.current_stream()
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    o.stream = stream or None
+    if allocator == "torch" and t is not None:
+        _torch_api.setdefault("alloc", t.cuda.caching_allocator_alloc)
+        _torch_api.setdefault("free", t.cuda.caching_allocator_delete)
+        o.alloc, o.free = _ALLOC_CB, _FREE_CB
+    elif allocator not in ("torch", "library"):
+        raise ValueError(allocator)
+    return o
+
+
+def _graph_desc(n, src, dst):
+    """Host numpy int32 arrays, or CUDA int32 tensors (on_device)."""
+    g = kdss_graph_desc()
+    g.n = int(n)
+    keep = []
+    if hasattr(src, "data_ptr"):
+        if src.dtype.__str__() != "torch.int32" or not src.is_contiguous() or not src.is_cuda:
+            raise ValueError("device edge arrays must be contiguous CUDA int32 tensors")
+        g.m = src.numel()
+        g.src, g.dst, g.on_device = src.data_ptr(), dst.data_ptr(), 1
+        keep = [src, dst]
+    else:
+        s = np.ascontiguousarray(src, np.int32)
+        d = np.ascontiguousarray(dst, np.int32)
+        if s.shape != d.shape:
+            raise ValueError("src and dst differ in length")
+        g.m = s.size
+        g.src, g.dst, g.on_device = s.ctypes.data, d.ctypes.data, 0
+        keep = [s, d]
+    return g, keep
+
+
+class Sct:
+    """Owning wrapper of a kdss_sct* handle."""
+
+    def __init__(self, ptr):
+        self.ptr = C.c_void_p(ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.kdss_sct_free(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    free = __del__
+
+
+class State:
+    """Owning wrapper of a kdss_state* handle."""
+
+    def __init__(self, ptr):
+        self.ptr = C.c_void_p(ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.kdss_state_free(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    free = __del__
+
+
+def _result_dict(r: kdss_result):
+    ids = np.ctypeslib.as_array(r.ids, shape=(r.istar,)).copy() if r.istar > 0 and r.ids else \
+        np.zeros(0, np.int32)
+    return dict(istar=int(r.istar), ids=ids, count=int(r.count_lo) | (int(r.count_hi) << 64),
+                density=r.density, upper_bound=r.upper_bound, rho_prime=r.rho_prime,
+                gap=r.gap, T=int(r.T), t_used=int(r.t_used), status=int(r.status))
+
+
+# ---------------------------------------------------------------------------
+# entry points (names of include/kdss.h)
+# ---------------------------------------------------------------------------
+
+def kdss_build_sct(n, src, dst, k, opts: kdss_opts | None = None) -> Sct:
+    L = load()
+    g, keep = _graph_desc(n, src, dst)
+    out = C.c_void_p()
+    _check(L.kdss_build_sct(C.byref(g), int(k), C.byref(opts or make_opts()), C.byref(out)))
+    del keep
+    return Sct(out.value)
+
+
+def kdss_sct_from_pairs(n, k, pair_off, nodes, h, opts: kdss_opts | None = None) -> Sct:
+    L = load()
+    po = np.ascontiguousarray(pair_off, np.int64)
+    nd = np.ascontiguousarray(nodes, np.int32)
+    hh = np.ascontiguousarray(h, np.int32)
+    out = C.c_void_p()
+    _check(L.kdss_sct_from_pairs(int(n), int(k), hh.size, po.ctypes.data, nd.ctypes.data,
+                                 hh.ctypes.data, 0, C.byref(opts or make_opts()), C.byref(out)))
+    return Sct(out.value)
+
+
+def kdss_sct_info(s: Sct) -> dict:
+    st = kdss_sct_stats()
+    _check(load().kdss_sct_info(s.ptr, C.byref(st)))
+    d = {f: getattr(st, f) for f, _ in kdss_sct_stats._fields_ if f != "pairs_per_class"}
+    d["pairs_per_class"] = list(st.pairs_per_class)[:5]
+    d["c_k"] = int(st.c_k_lo) | (int(st.c_k_hi) << 64)
+    return d
+
+
+def kdss_sct_copy_pairs(s: Sct) -> dict:
+    info = kdss_sct_info(s)
+    po = np.zeros(info["eta_k"] + 1, np.int64)
+    nodes = np.zeros(info["L_k"], np.int32)
+    h = np.zeros(info["eta_k"], np.int32)
+    _check(load().kdss_sct_copy_pairs(s.ptr, po.ctypes.data, nodes.ctypes.data, h.ctypes.data))
+    return dict(pair_off=po, nodes=nodes, h=h)
+
+
+def kdss_sct_copy_graph(s: Sct) -> dict:
+    info = kdss_sct_info(s)
+    n, m = info["n"], info["m"]
+    out = dict(off=np.zeros(n + 1, np.int64), adj=np.zeros(2 * m, np.int32),
+               core=np.zeros(n, np.int32), round=np.zeros(n, np.int32),
+               rank=np.zeros(n, np.int32))
+    _check(load().kdss_sct_copy_graph(s.ptr, out["off"].ctypes.data, out["adj"].ctypes.data,
+                                      out["core"].ctypes.data, out["round"].ctypes.data,
+                                      out["rank"].ctypes.data))
+    return out
+
+
+def kdss_fw_iterate(s: Sct, state: State | None, T: int, opts: kdss_opts | None = None) -> State:
+    L = load()
+    p = C.c_void_p(state.ptr.value if state is not None else None)
+    _check(L.kdss_fw_iterate(s.ptr, C.byref(p), int(T), C.byref(opts or make_opts())))
+    if state is None:
+        return State(p.value)
+    return state
+
+
+def kdss_state_copy_r(st: State, n: int, precision: int):
+    dt = np.float32 if precision == KDSS_FP32K else (np.float64 if precision == KDSS_FP64 else np.uint64)
+    r = np.zeros(n, dt)
+    t = C.c_int32()
+    _check(load().kdss_state_copy_r(st.ptr, r.ctypes.data, C.byref(t)))
+    return r, int(t.value)
+
+
+def kdss_state_timing(st: State) -> dict:
+    tm = kdss_timing()
+    _check(load().kdss_state_timing(st.ptr, C.byref(tm)))
+    return {f: getattr(tm, f) for f, _ in kdss_timing._fields_}
+
+
+def kdss_extract(s: Sct, st: State, opts: kdss_opts | None = None) -> dict:
+    L = load()
+    r = kdss_result()
+    _check(L.kdss_extract(s.ptr, st.ptr, C.byref(opts or make_opts()), C.byref(r)))
+    try:
+        return _result_dict(r)
+    finally:
+        L.kdss_result_free(C.byref(r))
+
+
+def kdss_solve(n, src, dst, k, T, opts: kdss_opts | None = None) -> dict:
+    L = load()
+    g, keep = _graph_desc(n, src, dst)
+    r = kdss_result()
+    rc = L.kdss_solve(C.byref(g), int(k), int(T), C.byref(opts or make_opts()), C.byref(r))
+    try:
+        _check(rc)
+        return _result_dict(r)
+    finally:
+        L.kdss_result_free(C.byref(r))
+        del keep
+
+
+def kdss_solve_batch(queries, opts: kdss_opts | None = None) -> list:
+    """queries: list of (n, src, dst, k, T).  Returns one dict per query
+    (with its status; failed queries carry no result)."""
+    L = load()
+    nq = len(queries)
+    arr = (kdss_query * max(nq, 1))()
+    keep = []
+    for i, (n, src, dst, k, T) in enumerate(queries):
+        g, kp = _graph_desc(n, src, dst)
+        keep.append(kp)
+        arr[i].graph, arr[i].k, arr[i].T = g, int(k), int(T)
+    res = (kdss_result * max(nq, 1))()
+    rc = L.kdss_solve_batch(arr, nq, res, C.byref(opts or make_opts()))
+    out = []
+    try:
+        for i in range(nq):
+            out.append(_result_dict(res[i]))
+    finally:
+        for i in range(nq):
+            L.kdss_result_free(C.byref(res[i]))
+    if rc != KDSS_OK and all(o["status"] != KDSS_OK for o in out):
+        _check(rc)
+    return out
+
+
+def kdss_version() -> str:
+    return load().kdss_version().decode()
+
+
+def kdss_kernel_launches() -> int:
+    return int(load().kdss_kernel_launches())

@@ -1,0 +1,326 @@
+// api.cu -- the extern "C" entry points declared in include/kdss.h.
+//
+// Every entry point converts internal exceptions into a kdss_status and a
+// thread-local message; nothing throws across the boundary.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fw.cuh"
+
+using namespace kdss;
+
+struct kdss_sct {
+    Ctx ctx;
+    GraphDev g;
+    SctDev s;
+    bool has_graph = false;
+    int64_t m = 0;
+    int degeneracy = 0;
+    int max_out = 0;
+};
+
+struct kdss_state {
+    StateDev st;
+};
+
+namespace kdss {
+void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
+long long launches();
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kdss_status record(kdss_status code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define API_BEGIN \
+    try {         \
+        g_last_error.clear();
+#define API_END                                                                  \
+    }                                                                            \
+    catch (const kdss::Error &e) { return record(e.code, e.msg); }               \
+    catch (const std::bad_alloc &) { return record(KDSS_ERR_OOM, "host allocation failed"); } \
+    catch (const std::exception &e) { return record(KDSS_ERR_CUDA, e.what()); }  \
+    catch (...) { return record(KDSS_ERR_CUDA, "unknown internal error"); }      \
+    return KDSS_OK;
+
+void check_graph(const kdss_graph_desc *g) {
+    if (!g) fail(KDSS_ERR_INVALID_ARG, "graph descriptor is NULL");
+    if (g->n < 0 || g->n >= (int64_t)INT32_MAX) fail(KDSS_ERR_INVALID_ARG, "n must be in [0, 2^31 - 1)");
+    if (g->m < 0) fail(KDSS_ERR_INVALID_ARG, "m must be >= 0");
+    if (g->m > 0 && (!g->src || !g->dst)) fail(KDSS_ERR_INVALID_ARG, "edge arrays are NULL");
+    if (g->m > ((int64_t)1 << 30)) fail(KDSS_ERR_UNSUPPORTED, "more than 2^30 edge records");
+}
+
+void check_k(int32_t k) {
+    if (k < 2 || k > 64) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, 64]");
+}
+
+int64_t sct_bytes(const kdss_sct *h) {
+    const GraphDev &g = h->g;
+    const SctDev &s = h->s;
+    return (int64_t)(g.off.bytes() + g.adj.bytes() + g.core.bytes() + g.rnd.bytes() +
+                     g.rank.bytes() + g.vert.bytes() + g.out_off.bytes() + g.out_adj.bytes() +
+                     s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + s.binom.bytes());
+}
+
+kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts, kdss_sct **out) {
+    API_BEGIN
+    if (!out) fail(KDSS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    check_graph(g);
+    check_k(k);
+    const int order = opts ? opts->order : KDSS_ORDER_PEEL;
+    if (order != KDSS_ORDER_PEEL && order != KDSS_ORDER_CORE)
+        fail(KDSS_ERR_INVALID_ARG, "unknown vertex order");
+    Ctx c = make_ctx(opts);
+    kdss_sct *h = new kdss_sct();
+    try {
+        h->ctx = c;
+        build_graph(c, *g, order, h->g);
+        build_sct(c, h->g, k, h->s);
+        h->m = h->g.nadj / 2;
+        h->degeneracy = h->g.degeneracy;
+        h->max_out = h->g.max_out;
+        h->has_graph = true;
+        if (!(opts && (opts->flags & KDSS_FLAG_KEEP_GRAPH))) {
+            h->g.off.reset(); h->g.adj.reset(); h->g.core.reset(); h->g.rnd.reset();
+            h->g.rank.reset(); h->g.vert.reset(); h->g.out_off.reset(); h->g.out_adj.reset();
+            h->has_graph = false;
+        }
+        sync(c);
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    API_END
+}
+
+}  // namespace
+
+extern "C" {
+
+kdss_status kdss_build_sct(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts,
+                           kdss_sct **out) {
+    return build_impl(g, k, opts, out);
+}
+
+kdss_status kdss_sct_from_pairs(int64_t n, int32_t k, int64_t npairs, const int64_t *pair_off,
+                                const int32_t *nodes, const int32_t *h, int32_t on_device,
+                                const kdss_opts *opts, kdss_sct **out) {
+    API_BEGIN
+    if (!out) fail(KDSS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    check_k(k);
+    if (n < 0 || n >= (int64_t)INT32_MAX) fail(KDSS_ERR_INVALID_ARG, "n must be in [0, 2^31 - 1)");
+    if (npairs < 0 || npairs >= (int64_t)INT32_MAX) fail(KDSS_ERR_INVALID_ARG, "npairs out of range");
+    if (npairs > 0 && (!pair_off || !nodes || !h)) fail(KDSS_ERR_INVALID_ARG, "pair arrays are NULL");
+    Ctx c = make_ctx(opts);
+    kdss_sct *hd = new kdss_sct();
+    try {
+        hd->ctx = c;
+        DBuf<int64_t> doff;
+        DBuf<int32_t> dnodes, dh;
+        const int64_t *po = pair_off;
+        const int32_t *pn = nodes, *ph = h;
+        int64_t nn = 0;
+        if (npairs > 0) {
+            if (on_device) {
+                to_host(c, &nn, pair_off + npairs, 1);
+            } else {
+                nn = pair_off[npairs];
+                if (pair_off[0] != 0) fail(KDSS_ERR_INVALID_ARG, "pair_off[0] must be 0");
+                for (int64_t q = 0; q < npairs; ++q)
+                    if (pair_off[q + 1] < pair_off[q]) fail(KDSS_ERR_INVALID_ARG, "pair_off must be non-decreasing");
+                doff = DBuf<int64_t>(c, (size_t)npairs + 1);
+                dnodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nn, 1));
+                dh = DBuf<int32_t>(c, (size_t)npairs);
+                to_device(c, doff.p, pair_off, (size_t)npairs + 1);
+                to_device(c, dnodes.p, nodes, (size_t)nn);
+                to_device(c, dh.p, h, (size_t)npairs);
+                po = doff.p; pn = dnodes.p; ph = dh.p;
+            }
+        }
+        sct_from_pairs(c, n, k, npairs, po, pn, ph, hd->s);
+        sync(c);
+    } catch (...) {
+        delete hd;
+        throw;
+    }
+    *out = hd;
+    API_END
+}
+
+kdss_status kdss_sct_info(const kdss_sct *s, kdss_sct_stats *out) {
+    API_BEGIN
+    if (!s || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    memset(out, 0, sizeof *out);
+    out->n = s->s.n;
+    out->m = s->m;
+    out->eta_k = s->s.npairs;
+    out->L_k = s->s.nnodes;
+    out->c_k_lo = s->s.ck_lo;
+    out->c_k_hi = s->s.ck_hi;
+    out->k = s->s.k;
+    out->degeneracy = s->degeneracy;
+    out->max_out_degree = s->max_out;
+    out->max_pair_len = s->s.max_len;
+    out->device_bytes = sct_bytes(s);
+    for (int c = 0; c < NCLASS && c < 8; ++c)
+        out->pairs_per_class[c] = s->s.class_begin[c + 1] - s->s.class_begin[c];
+    API_END
+}
+
+kdss_status kdss_sct_copy_pairs(const kdss_sct *s, int64_t *pair_off, int32_t *nodes, int32_t *h) {
+    API_BEGIN
+    if (!s) fail(KDSS_ERR_INVALID_ARG, "NULL handle");
+    const Ctx &c = s->ctx;
+    if (pair_off) to_host(c, pair_off, s->s.pair_off.p, (size_t)s->s.npairs + 1);
+    if (nodes) to_host(c, nodes, s->s.nodes.p, (size_t)s->s.nnodes);
+    if (h && s->s.npairs > 0) {
+        std::vector<uint8_t> tmp((size_t)s->s.npairs);
+        to_host(c, tmp.data(), s->s.h.p, tmp.size());
+        for (size_t i = 0; i < tmp.size(); ++i) h[i] = tmp[i];
+    }
+    API_END
+}
+
+kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, int32_t *core,
+                                int32_t *round_, int32_t *rank) {
+    API_BEGIN
+    if (!s) fail(KDSS_ERR_INVALID_ARG, "NULL handle");
+    if (!s->has_graph) fail(KDSS_ERR_INVALID_ARG, "the handle keeps no graph (build with KDSS_FLAG_KEEP_GRAPH)");
+    const Ctx &c = s->ctx;
+    const GraphDev &g = s->g;
+    if (off) to_host(c, off, g.off.p, (size_t)g.n + 1);
+    if (adj) to_host(c, adj, g.adj.p, (size_t)g.nadj);
+    if (core) to_host(c, core, g.core.p, (size_t)g.n);
+    if (round_) to_host(c, round_, g.rnd.p, (size_t)g.n);
+    if (rank) to_host(c, rank, g.rank.p, (size_t)g.n);
+    API_END
+}
+
+kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
+    API_BEGIN
+    if (!s || !state) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
+    Ctx c = make_ctx(opts);
+    bool created = false;
+    if (!*state) {
+        const int prec = opts ? opts->precision : KDSS_INT64;
+        if (prec != KDSS_INT64 && prec != KDSS_FP64 && prec != KDSS_FP32K)
+            fail(KDSS_ERR_INVALID_ARG, "unknown precision");
+        kdss_state *st = new kdss_state();
+        try {
+            fw_init(c, s->s, prec, st->st);
+        } catch (...) {
+            delete st;
+            throw;
+        }
+        *state = st;
+        created = true;
+    }
+    if ((*state)->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
+    try {
+        fw_run(c, s->s, (*state)->st, T, opts && (opts->flags & KDSS_FLAG_PROFILE));
+        sync(c);
+    } catch (...) {
+        if (created) { delete *state; *state = nullptr; }
+        throw;
+    }
+    API_END
+}
+
+kdss_status kdss_state_copy_r(const kdss_state *st, void *r_host, int32_t *t_out) {
+    API_BEGIN
+    if (!st) fail(KDSS_ERR_INVALID_ARG, "NULL state");
+    const StateDev &d = st->st;
+    if (r_host) {
+        if (d.precision == KDSS_FP32K) to_host(d.ctx, (float *)r_host, d.r32.p, (size_t)d.n);
+        else to_host(d.ctx, (uint64_t *)r_host, d.r.p, (size_t)d.n);
+    }
+    if (t_out) *t_out = d.t;
+    API_END
+}
+
+kdss_status kdss_state_timing(const kdss_state *st, kdss_timing *out) {
+    API_BEGIN
+    if (!st || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    *out = st->st.timing;
+    API_END
+}
+
+kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opts *opts,
+                         kdss_result *out) {
+    API_BEGIN
+    if (!s || !st || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (st->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
+    Ctx c = make_ctx(opts);
+    extract_prefix(c, s->s, st->st, out);
+    API_END
+}
+
+kdss_status kdss_solve(const kdss_graph_desc *g, int32_t k, int32_t T, const kdss_opts *opts,
+                       kdss_result *out) {
+    if (!out) return record(KDSS_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof *out);
+    kdss_sct *s = nullptr;
+    kdss_state *st = nullptr;
+    kdss_status rc = kdss_build_sct(g, k, opts, &s);
+    if (rc == KDSS_OK) rc = kdss_fw_iterate(s, &st, T, opts);
+    if (rc == KDSS_OK) rc = kdss_extract(s, st, opts, out);
+    if (rc == KDSS_OK) out->T = T;
+    out->status = rc;
+    std::string msg = g_last_error;
+    kdss_state_free(st);
+    kdss_sct_free(s);
+    g_last_error = msg;
+    return rc;
+}
+
+kdss_status kdss_solve_batch(const kdss_query *q, int32_t nq, kdss_result *out,
+                             const kdss_opts *opts) {
+    if (nq < 0 || (nq > 0 && (!q || !out))) return record(KDSS_ERR_INVALID_ARG, "bad batch arguments");
+    kdss_status first = KDSS_OK;
+    std::string first_msg;
+    for (int32_t i = 0; i < nq; ++i) {
+        kdss_status rc = kdss_solve(&q[i].graph, q[i].k, q[i].T, opts, &out[i]);
+        out[i].status = rc;
+        if (rc != KDSS_OK && first == KDSS_OK) { first = rc; first_msg = g_last_error; }
+    }
+    g_last_error = first_msg;
+    return first;
+}
+
+void kdss_sct_free(kdss_sct *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->ctx.stream);
+    delete s;
+}
+
+void kdss_state_free(kdss_state *st) {
+    if (!st) return;
+    cudaStreamSynchronize(st->st.ctx.stream);
+    delete st;
+}
+
+void kdss_result_free(kdss_result *r) {
+    if (!r) return;
+    free(r->ids);
+    r->ids = nullptr;
+}
+
+const char *kdss_last_error(void) { return g_last_error.c_str(); }
+
+const char *kdss_version(void) { return "kdss-gb300 0.1 (sm_103a)"; }
+
+int64_t kdss_kernel_launches(void) { return (int64_t)kdss::launches(); }
+
+}  // extern "C"

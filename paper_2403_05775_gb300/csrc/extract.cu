@@ -1,0 +1,347 @@
+// extract.cu -- step A6: the densest prefix of the nodes sorted by r
+// (Alg. 2 lines 5-7).
+//
+// 1. Sort V by r non-increasing, ties by ascending id: a stable LSD radix sort
+//    of key = max(r) - r over ids 0..n-1 (key bits of the float / double
+//    representation for the floating-point states).
+// 2. |C_k(V_i)| for every prefix length i from the pairs: by Lemmas 2.5-2.6 a
+//    pair holds C(#{V_p nodes in V_i}, k - h) k-cliques of V_i once V_h is
+//    inside V_i.  With mh the last position of a V_h node, the pair adds
+//    C(c0, k - h) at prefix length mh + 1 (c0 = V_p nodes before mh), and for
+//    each later V_p node at position q the increment
+//    C(c + 1, k - h) - C(c, k - h) = C(c, k - h - 1) at length q + 1
+//    (c = V_p nodes before q).  A scan of the increments gives C_k(V_i).
+//    The same pass adds n_C at the length where the whole pair is inside,
+//    whose scan is sum_{P inside V_i} n_C = i * rho'(V_i) (Thm 3.6).
+// 3. i* = the largest i maximising C_k(V_i) / i, compared exactly by
+//    128-bit cross-multiplication.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "fw.cuh"
+
+namespace kdss {
+
+void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__global__ void k_keys_u64(int64_t n, const uint64_t *r, uint64_t maxv, uint64_t *keys,
+                           int32_t *vals) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        keys[v] = maxv - r[v];
+        vals[v] = (int32_t)v;
+    }
+}
+__global__ void k_keys_f32(int64_t n, const float *r, uint32_t maxbits, uint64_t *keys,
+                           int32_t *vals) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        float x = r[v];
+        uint32_t b = x > 0.f ? (uint32_t)__float_as_int(x) : 0u;
+        keys[v] = (uint64_t)(maxbits - b);
+        vals[v] = (int32_t)v;
+    }
+}
+__global__ void k_max_f32bits(int64_t n, const float *r, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        float x = r[v];
+        unsigned long long b = x > 0.f ? (unsigned long long)(uint32_t)__float_as_int(x) : 0ull;
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(FULL, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+__global__ void k_positions(int64_t n, const int32_t *order, int32_t *pos) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        pos[order[i]] = (int32_t)i;
+}
+
+template <int G>
+__device__ __forceinline__ int gmax_i32(int v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+template <int G>
+__device__ __forceinline__ int gsum_i32(int v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Prefix-count increments of the pairs [b, e): a group of G lanes per pair.
+template <int G, int NPL>
+__global__ void __launch_bounds__(256)
+k_prefix_events(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+                const uint8_t *__restrict__ hcnt, int64_t b, int64_t e,
+                const int32_t *__restrict__ pos, const uint64_t *__restrict__ binom, int bcols,
+                int k, unsigned long long *hist, unsigned long long *fhist) {
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gbase = lane & ~(G - 1);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t np = e - b;
+    for (int64_t wb = warp * GPW; wb < np; wb += nwarps * GPW) {
+        const int64_t qi = wb + lane / G;
+        const bool active = qi < np;
+        const int64_t q = b + qi;
+        int64_t off0 = 0;
+        int len = 0, h = 0;
+        if (active) {
+            off0 = pair_off[q];
+            len = (int)(pair_off[q + 1] - off0);
+            h = hcnt[q];
+        }
+        const int p = len - h;
+        int ps[NPL];
+        bool hold[NPL], valid[NPL];
+        int mh = -1, mall = -1;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int j = s * G + gl;
+            valid[s] = active && j < len;
+            const int32_t raw = valid[s] ? __ldg(nodes + off0 + j) : 0;
+            hold[s] = raw < 0;
+            ps[s] = valid[s] ? __ldg(pos + (raw & 0x7fffffff)) : -1;
+            if (valid[s] && hold[s]) mh = max(mh, ps[s]);
+            if (valid[s]) mall = max(mall, ps[s]);
+        }
+        mh = gmax_i32<G>(mh);
+        mall = gmax_i32<G>(mall);
+        // c0 = pivot nodes before the last hold node
+        int c0 = 0;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s)
+            if (valid[s] && !hold[s] && ps[s] < mh) ++c0;
+        c0 = gsum_i32<G>(c0);
+        // rank of each later pivot node among the pivot positions
+        int rk[NPL];
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) rk[s] = 0;
+        for (int s2 = 0; s2 < NPL; ++s2) {
+            for (int l2 = 0; l2 < G; ++l2) {
+                const int pv = __shfl_sync(FULL, (valid[s2] && !hold[s2]) ? ps[s2] : -1, gbase + l2);
+#pragma unroll
+                for (int s = 0; s < NPL; ++s)
+                    if (pv >= 0 && pv < ps[s]) ++rk[s];
+            }
+        }
+        if (active) {
+            const int kh = k - h;
+            if (gl == 0) {
+                const uint64_t first = __ldg(binom + (size_t)c0 * bcols + kh);
+                if (first) atomicAdd(hist + (mh + 1), (unsigned long long)first);
+                const uint64_t nC = __ldg(binom + (size_t)p * bcols + kh);
+                atomicAdd(fhist + (mall + 1), (unsigned long long)nC);
+            }
+            if (kh >= 1) {
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    if (valid[s] && !hold[s] && ps[s] > mh) {
+                        const uint64_t inc = __ldg(binom + (size_t)rk[s] * bcols + (kh - 1));
+                        if (inc) atomicAdd(hist + (ps[s] + 1), (unsigned long long)inc);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// a / i > b / j, exact (a, b < 2^64, i, j < 2^63)
+__device__ __forceinline__ int frac_cmp(unsigned long long a, unsigned long long i,
+                                        unsigned long long b, unsigned long long j) {
+    unsigned long long ahi = __umul64hi(a, j), alo = a * j;
+    unsigned long long bhi = __umul64hi(b, i), blo = b * i;
+    if (ahi != bhi) return ahi > bhi ? 1 : -1;
+    if (alo != blo) return alo > blo ? 1 : -1;
+    return 0;
+}
+
+// Best prefix of a scanned count array: largest ratio, ties to the larger i.
+__device__ __forceinline__ void better(unsigned long long &a, long long &i,
+                                       unsigned long long b, long long j) {
+    if (j <= 0) return;
+    if (i <= 0) { a = b; i = j; return; }
+    int c = frac_cmp(b, (unsigned long long)j, a, (unsigned long long)i);
+    if (c > 0 || (c == 0 && j > i)) { a = b; i = j; }
+}
+
+__global__ void k_argmax_partial(int64_t n, const unsigned long long *cnt,
+                                 unsigned long long *pa, long long *pi) {
+    unsigned long long a = 0;
+    long long i = 0;
+    for (int64_t x = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x <= n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        better(a, i, cnt[x], x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long b = __shfl_xor_sync(FULL, a, o);
+        long long j = __shfl_xor_sync(FULL, i, o);
+        better(a, i, b, j);
+    }
+    __shared__ unsigned long long sa[32];
+    __shared__ long long si[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sa[w] = a; si[w] = i; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : 0ull;
+        i = lane < nw ? si[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long b = __shfl_xor_sync(FULL, a, o);
+            long long j = __shfl_xor_sync(FULL, i, o);
+            better(a, i, b, j);
+        }
+        if (lane == 0) { pa[blockIdx.x] = a; pi[blockIdx.x] = i; }
+    }
+}
+
+__global__ void k_argmax_final(int nb, const unsigned long long *pa, const long long *pi,
+                               unsigned long long *oa, long long *oi) {
+    unsigned long long a = 0;
+    long long i = 0;
+    for (int x = threadIdx.x; x < nb; x += blockDim.x) better(a, i, pa[x], pi[x]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long b = __shfl_xor_sync(FULL, a, o);
+        long long j = __shfl_xor_sync(FULL, i, o);
+        better(a, i, b, j);
+    }
+    __shared__ unsigned long long sa[32];
+    __shared__ long long si[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sa[w] = a; si[w] = i; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : 0ull;
+        i = lane < nw ? si[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long b = __shfl_xor_sync(FULL, a, o);
+            long long j = __shfl_xor_sync(FULL, i, o);
+            better(a, i, b, j);
+        }
+        if (lane == 0) { *oa = a; *oi = i; }
+    }
+}
+
+void best_prefix(const Ctx &c, int64_t n, const unsigned long long *cnt, unsigned long long *a,
+                 long long *i) {
+    const int B = 256;
+    const int nb = std::min(grid_for(c, n, B, 4), 1024);
+    DBuf<unsigned long long> pa(c, (size_t)nb), oa(c, 1);
+    DBuf<long long> pi(c, (size_t)nb), oi(c, 1);
+    k_argmax_partial<<<nb, B, 0, c.stream>>>(n, cnt, pa.p, pi.p);
+    KDSS_LAUNCH_CHECK();
+    k_argmax_final<<<1, 1024, 0, c.stream>>>(nb, pa.p, pi.p, oa.p, oi.p);
+    KDSS_LAUNCH_CHECK();
+    to_host(c, a, oa.p, 1);
+    to_host(c, i, oi.p, 1);
+}
+
+template <int G, int NPL>
+void launch_events(const Ctx &c, const SctDev &s, int cls, const int32_t *pos,
+                   unsigned long long *hist, unsigned long long *fhist) {
+    const int64_t b = s.class_begin[cls], e = s.class_begin[cls + 1];
+    if (e <= b) return;
+    const int64_t gpb = 8 * (32 / G);
+    int grid = (int)std::min<int64_t>(ceil_div(e - b, gpb), (int64_t)c.num_sms * 16);
+    k_prefix_events<G, NPL><<<grid, 256, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, pos,
+                                                        s.binom.p, s.k + 1, s.k, hist, fhist);
+    KDSS_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out) {
+    const int64_t n = s.n;
+    memset(out, 0, sizeof *out);
+    out->t_used = st.t;
+    if (n == 0) return;
+    if (s.ck_hi) fail(KDSS_ERR_OVERFLOW, "prefix clique counts above 2^64 are not supported");
+    const int B = 256;
+    DBuf<uint64_t> keys(c, (size_t)n);
+    DBuf<int32_t> order(c, (size_t)n);
+    int bits;
+    double rmax_val;
+    if (st.precision == KDSS_FP32K) {
+        DBuf<unsigned long long> mx(c, 1);
+        zero(c, mx.p, 8);
+        k_max_f32bits<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r32.p, mx.p);
+        KDSS_LAUNCH_CHECK();
+        unsigned long long mb = 0;
+        to_host(c, &mb, mx.p, 1);
+        uint32_t m32 = (uint32_t)mb;
+        float mf;
+        memcpy(&mf, &m32, 4);
+        rmax_val = (double)mf;
+        k_keys_f32<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r32.p, m32, keys.p, order.p);
+        bits = bit_length(m32);
+    } else {
+        unsigned long long mb = 0;
+        to_host(c, &mb, st.maxr.p, 1);
+        if (st.precision == KDSS_FP64) {
+            double md;
+            memcpy(&md, &mb, 8);
+            rmax_val = st.t > 0 ? md / st.t : 0.0;
+        } else {
+            rmax_val = st.t > 0 ? (double)mb / st.t : 0.0;
+        }
+        k_keys_u64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mb, keys.p, order.p);
+        bits = bit_length(mb);
+    }
+    KDSS_LAUNCH_CHECK();
+    radix_sort_u64(c, keys.p, order.p, n, {{0, bits}});
+    keys.reset();
+    DBuf<int32_t> pos(c, (size_t)n);
+    k_positions<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, order.p, pos.p);
+    KDSS_LAUNCH_CHECK();
+    DBuf<unsigned long long> hist(c, (size_t)n + 2), fhist(c, (size_t)n + 2);
+    zero(c, hist.p, (n + 2) * 8);
+    zero(c, fhist.p, (n + 2) * 8);
+    launch_events<8, 1>(c, s, 0, pos.p, hist.p, fhist.p);
+    launch_events<8, 2>(c, s, 1, pos.p, hist.p, fhist.p);
+    launch_events<8, 4>(c, s, 2, pos.p, hist.p, fhist.p);
+    launch_events<32, 8>(c, s, 3, pos.p, hist.p, fhist.p);
+    launch_events<32, 32>(c, s, 4, pos.p, hist.p, fhist.p);
+    inclusive_scan_u64_async(c, (const uint64_t *)hist.p, (uint64_t *)hist.p, n + 1);
+    inclusive_scan_u64_async(c, (const uint64_t *)fhist.p, (uint64_t *)fhist.p, n + 1);
+    unsigned long long best = 0, fbest = 0;
+    long long istar = 0, fi = 0;
+    best_prefix(c, n, hist.p, &best, &istar);
+    best_prefix(c, n, fhist.p, &fbest, &fi);
+    out->istar = istar;
+    out->count_lo = best;
+    out->count_hi = 0;
+    out->density = istar > 0 ? (double)best / (double)istar : 0.0;
+    out->upper_bound = rmax_val;
+    out->rho_prime = fi > 0 ? (double)fbest / (double)fi : 0.0;
+    out->gap = rmax_val > 0 ? 1.0 - out->rho_prime / rmax_val : 0.0;
+    out->T = st.t;
+    if (istar > 0) {
+        out->ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)istar);
+        if (!out->ids) fail(KDSS_ERR_OOM, "host allocation of the result ids");
+        to_host(c, out->ids, order.p, (size_t)istar);
+        std::sort(out->ids, out->ids + istar);
+    }
+}
+
+}  // namespace kdss

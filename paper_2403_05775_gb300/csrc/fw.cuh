@@ -1,0 +1,27 @@
+// fw.cuh -- Frank-Wolfe state and iterations (steps A4-A5).
+#pragma once
+
+#include "sct.cuh"
+
+namespace kdss {
+
+struct StateDev {
+    int precision = KDSS_INT64;
+    int64_t n = 0;
+    int t = 0;                       // iterations done
+    DBuf<uint64_t> r;                // [n] uint64 or double bits (rule I), cumulative
+    DBuf<uint64_t> acc;              // [n] per-iteration delta (same type as r)
+    DBuf<float> r32;                 // [n] FP32K: normalised r / t
+    DBuf<float> r32c;                // [n] FP32K: Kahan compensation of r32
+    DBuf<float> a32;                 // [n] FP32K: per-iteration allocation (hi)
+    DBuf<float> a32c;                // [n] FP32K: error terms of the allocation sum
+    DBuf<unsigned long long> maxr;   // [1] max r (uint64 / double bits / float bits)
+    DBuf<int> err;                   // [1] device error word
+    kdss_timing timing{};
+    Ctx ctx;
+};
+
+void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st);
+void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile);
+
+}  // namespace kdss

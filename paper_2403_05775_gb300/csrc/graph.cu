@@ -1,0 +1,359 @@
+// graph.cu -- steps A1 (simple graph in CSR) and A2 (core numbers, vertex
+// order, orientation) of the solver.
+//
+// A1: the raw edge list becomes the simple undirected graph G(V, E) of Sec. 2:
+//     both orientations as 64-bit (u, v) keys, a stable radix sort, duplicate
+//     and self-loop removal, row offsets.
+// A2: degeneracy (Sec. 2) by round-synchronous peeling in one cooperative
+//     kernel: at level c every remaining vertex of remaining degree <= c is
+//     removed in one round; vertices whose degree falls to c during a round
+//     form the next round's frontier; when none is left, c rises to the
+//     smallest remaining degree.  The build order is (round, id) or
+//     (core, id); the out-CSR keeps u -> w iff w is later than u.
+#include <algorithm>
+
+#include "graph.cuh"
+
+namespace kdss {
+
+namespace {
+
+constexpr uint64_t SENT = ~0ull;
+
+__global__ void k_edge_keys(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                            uint64_t *keys, int *err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = src[e], v = dst[e];
+        uint64_t a = SENT, b = SENT;
+        if (u < 0 || v < 0 || u >= n || v >= n) {
+            atomicOr(err, DERR_BAD_ID);
+        } else if (u != v) {
+            a = ((uint64_t)u << 32) | (uint64_t)v;
+            b = ((uint64_t)v << 32) | (uint64_t)u;
+        }
+        keys[2 * e] = a;
+        keys[2 * e + 1] = b;
+    }
+}
+
+__global__ void k_unique_flags(const uint64_t *keys, int64_t nk, int64_t *flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        flags[i] = (k != SENT && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+    }
+}
+
+__global__ void k_compact_keys(const uint64_t *keys, int64_t nk, const int64_t *flags,
+                               const int64_t *pos, uint64_t *ukeys, int32_t *adj) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (flags[i]) {
+            uint64_t k = keys[i];
+            ukeys[pos[i]] = k;
+            if (adj) adj[pos[i]] = (int32_t)(k & 0xffffffffu);
+        }
+    }
+}
+
+__global__ void k_degrees(const int64_t *off, int64_t n, int32_t *deg, int32_t *rnd) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        deg[v] = (int32_t)(off[v + 1] - off[v]);
+        rnd[v] = -1;
+    }
+}
+
+struct PeelCtl {
+    GridBarrier bar;
+    int err;
+    int count[3];   // frontier sizes, rotating by round mod 3
+    unsigned int minval;
+    int rounds;
+    int degeneracy;
+};
+
+constexpr int PEEL_THREADS = 256;
+
+__global__ void __launch_bounds__(PEEL_THREADS)
+k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+       int32_t *deg, int32_t *rnd, int32_t *core, int32_t *fa, int32_t *fb, PeelCtl *ctl,
+       uint64_t timeout_ns) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const unsigned int nb = gridDim.x;
+    int32_t *cur = fa, *nxt = fb;
+    int level = 0, round = 0;
+    int64_t removed = 0;
+    volatile int *vcount = ctl->count;
+    while (true) {
+        // count[round % 3] is this round's frontier, count[(round + 1) % 3] the
+        // next one; count[(round + 2) % 3] was read by everyone before the
+        // barrier that ended the previous round and is next written after the
+        // barrier that ends this one, so it is reset here.
+        const int ci = round % 3, cn = (round + 1) % 3, cz = (round + 2) % 3;
+        if (tid == 0) ctl->count[cz] = 0;
+        int cnt = vcount[ci];
+        if (cnt > n) { if (tid == 0) atomicOr(&ctl->err, DERR_CAPACITY); return; }  // uniform
+        if (cnt == 0) {
+            if (removed >= n) break;
+            // smallest remaining degree
+            unsigned int mn = 0xffffffffu;
+            for (int64_t v = tid; v < n; v += nth)
+                if (__ldcg(rnd + v) < 0) {
+                    unsigned int d = (unsigned int)__ldcg(deg + v);
+                    mn = d < mn ? d : mn;
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned int t = __shfl_xor_sync(0xffffffffu, mn, o);
+                mn = t < mn ? t : mn;
+            }
+            if ((threadIdx.x & 31) == 0 && mn != 0xffffffffu) atomicMin(&ctl->minval, mn);
+            if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+            unsigned int mv = *(volatile unsigned int *)&ctl->minval;
+            if (mv == 0xffffffffu) {  // nothing alive: inconsistent counters
+                if (tid == 0) atomicOr(&ctl->err, DERR_LOGIC);
+                return;
+            }
+            if ((int)mv > level) level = (int)mv;
+            for (int64_t v = tid; v < n; v += nth)
+                if (__ldcg(rnd + v) < 0 && __ldcg(deg + v) <= level) {
+                    int idx = atomicAdd(&ctl->count[ci], 1);
+                    if (idx < n) cur[idx] = (int32_t)v;
+                    rnd[v] = round;
+                    core[v] = level;
+                }
+            if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+            // minval is next read after at least one more barrier
+            if (tid == 0) ctl->minval = 0xffffffffu;
+            cnt = vcount[ci];
+            if (cnt > n) { if (tid == 0) atomicOr(&ctl->err, DERR_CAPACITY); return; }
+        }
+        // Remove the frontier: decrement remaining neighbours; a neighbour
+        // whose degree falls from level + 1 to level joins the next round.
+        const int lane = threadIdx.x & 31;
+        const int64_t warp = tid >> 5, nwarps = nth >> 5;
+        for (int64_t i = warp; i < cnt; i += nwarps) {
+            int32_t v = __ldcg(cur + i);
+            int64_t e0 = off[v], e1 = off[v + 1];
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
+                int32_t w = adj[e];
+                if (__ldcg(rnd + w) < 0) {
+                    int old = atomicSub(deg + w, 1);
+                    if (old == level + 1) {
+                        rnd[w] = round + 1;
+                        core[w] = level;
+                        int idx = atomicAdd(&ctl->count[cn], 1);
+                        if (idx < n) nxt[idx] = w;
+                    }
+                }
+            }
+        }
+        removed += cnt;
+        if (tid == 0) {
+            if (level > ctl->degeneracy) ctl->degeneracy = level;
+            ctl->rounds = round + 1;
+        }
+        if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+        int32_t *t = cur; cur = nxt; nxt = t;
+        ++round;
+    }
+}
+
+__global__ void k_order_keys(int64_t n, const int32_t *key, uint64_t *keys) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = ((uint64_t)(uint32_t)key[v] << 32) | (uint64_t)v;
+}
+
+__global__ void k_order_ranks(int64_t n, const uint64_t *keys, int32_t *vert, int32_t *rank) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = (int32_t)(keys[i] & 0xffffffffu);
+        vert[i] = v;
+        rank[v] = (int32_t)i;
+    }
+}
+
+// One flag per CSR entry: keep (v, w) iff rank[v] < rank[w].
+__global__ void k_orient_flags(int64_t n, const int64_t *off, const int32_t *adj,
+                               const int32_t *rank, int64_t *flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        int32_t rv = rank[v];
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
+            flags[e] = rank[adj[e]] > rv ? 1 : 0;
+    }
+}
+
+__global__ void k_orient_keys(int64_t n, const int64_t *off, const int32_t *adj,
+                              const int32_t *rank, const int64_t *flags, const int64_t *pos,
+                              uint64_t *keys) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        uint64_t rv = (uint64_t)(uint32_t)rank[v];
+        for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
+            if (flags[e]) keys[pos[e]] = (rv << 32) | (uint64_t)(uint32_t)rank[adj[e]];
+    }
+}
+
+__global__ void k_low32(const uint64_t *keys, int64_t nk, int32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)(keys[i] & 0xffffffffu);
+}
+
+__global__ void k_max_rowlen(const int64_t *off, int64_t n, int *out) {
+    int m = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int d = (int)(off[v + 1] - off[v]);
+        m = d > m ? d : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+}  // namespace
+
+void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &out) {
+    const int64_t n = g.n, m = g.m;
+    out.n = n;
+    const int B = 256;
+    DBuf<int> err(c, 1);
+    zero(c, err.p, sizeof(int));
+
+    // ---- A1: symmetric, deduplicated CSR -------------------------------
+    DBuf<int32_t> hsrc, hdst;
+    const int32_t *src = g.src, *dst = g.dst;
+    if (!g.on_device && m > 0) {
+        hsrc = DBuf<int32_t>(c, (size_t)m);
+        hdst = DBuf<int32_t>(c, (size_t)m);
+        to_device(c, hsrc.p, g.src, (size_t)m);
+        to_device(c, hdst.p, g.dst, (size_t)m);
+        src = hsrc.p;
+        dst = hdst.p;
+    }
+    const int64_t nk = 2 * m;
+    DBuf<uint64_t> keys(c, (size_t)std::max<int64_t>(nk, 1));
+    if (m > 0) {
+        k_edge_keys<<<grid_for(c, m, B), B, 0, c.stream>>>(src, dst, m, n, keys.p, err.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    hsrc.reset();
+    hdst.reset();
+    const int b = bit_length((uint64_t)n) + 1;  // sentinel bits sort last
+    radix_sort_u64(c, keys.p, nullptr, nk, {{0, b}, {32, 32 + b}});
+    DBuf<int64_t> flags(c, (size_t)std::max<int64_t>(nk, 1)), pos(c, (size_t)std::max<int64_t>(nk, 1));
+    int64_t nadj = 0;
+    if (nk > 0) {
+        k_unique_flags<<<grid_for(c, nk, B), B, 0, c.stream>>>(keys.p, nk, flags.p);
+        KDSS_LAUNCH_CHECK();
+        nadj = exclusive_scan_i64(c, flags.p, pos.p, nk);
+    }
+    int herr = 0;
+    to_host(c, &herr, err.p, 1);
+    if (herr & DERR_BAD_ID) fail(KDSS_ERR_BAD_GRAPH, "an edge endpoint is outside [0, n)");
+    out.nadj = nadj;
+    out.off = DBuf<int64_t>(c, (size_t)(n + 1));
+    out.adj = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nadj, 1));
+    DBuf<uint64_t> ukeys(c, (size_t)std::max<int64_t>(nadj, 1));
+    if (nk > 0) {
+        k_compact_keys<<<grid_for(c, nk, B), B, 0, c.stream>>>(keys.p, nk, flags.p, pos.p,
+                                                               ukeys.p, out.adj.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    keys.reset();
+    row_offsets_from_sorted(c, ukeys.p, nadj, n, out.off.p);
+    ukeys.reset();
+
+    // ---- A2: peeling (cooperative kernel, bounded barriers) -------------
+    out.core = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
+    out.rnd = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
+    if (n > 0) {
+        DBuf<int32_t> deg(c, (size_t)n), fa(c, (size_t)n), fb(c, (size_t)n);
+        DBuf<PeelCtl> ctl(c, 1);
+        zero(c, ctl.p, sizeof(PeelCtl));
+        unsigned int ff = 0xffffffffu;
+        KDSS_CUDA(cudaMemcpyAsync(&ctl.p->minval, &ff, sizeof ff, cudaMemcpyHostToDevice, c.stream));
+        k_degrees<<<grid_for(c, n, B), B, 0, c.stream>>>(out.off.p, n, deg.p, out.rnd.p);
+        KDSS_LAUNCH_CHECK();
+        int per_sm = 0;
+        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, PEEL_THREADS, 0));
+        per_sm = std::max(1, std::min(per_sm, 4));
+        int grid = (int)std::min<int64_t>((int64_t)c.num_sms * per_sm,
+                                          std::max<int64_t>(1, ceil_div(n, PEEL_THREADS)));
+        uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per barrier wait
+        int64_t nn = n;
+        const int64_t *offp = out.off.p;
+        const int32_t *adjp = out.adj.p;
+        int32_t *degp = deg.p, *rndp = out.rnd.p, *corep = out.core.p, *fap = fa.p, *fbp = fb.p;
+        PeelCtl *ctlp = ctl.p;
+        void *args[] = {&nn, &offp, &adjp, &degp, &rndp, &corep, &fap, &fbp, &ctlp, &timeout_ns};
+        KDSS_CUDA(cudaLaunchCooperativeKernel((const void *)k_peel, dim3(grid), dim3(PEEL_THREADS),
+                                              args, 0, c.stream));
+        KDSS_LAUNCH_CHECK();
+        PeelCtl h;
+        to_host(c, &h, ctl.p, 1);
+        if (h.err & DERR_TIMEOUT) fail(KDSS_ERR_TIMEOUT, "peeling: a grid barrier wait expired");
+        if (h.err) fail(KDSS_ERR_CUDA, "peeling: inconsistent device state");
+        out.degeneracy = h.degeneracy;
+        out.peel_rounds = h.rounds;
+    }
+
+    // ---- A2: vertex order and rank-space out-CSR ------------------------
+    out.rank = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
+    out.vert = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
+    if (n > 0) {
+        DBuf<uint64_t> okeys(c, (size_t)n);
+        const int32_t *key = order == KDSS_ORDER_CORE ? out.core.p : out.rnd.p;
+        k_order_keys<<<grid_for(c, n, B), B, 0, c.stream>>>(n, key, okeys.p);
+        KDSS_LAUNCH_CHECK();
+        int kb = bit_length((uint64_t)std::max<int64_t>(n, out.peel_rounds + 1));
+        radix_sort_u64(c, okeys.p, nullptr, n, {{0, b}, {32, 32 + kb}});
+        k_order_ranks<<<grid_for(c, n, B), B, 0, c.stream>>>(n, okeys.p, out.vert.p, out.rank.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    int64_t m1 = 0;
+    DBuf<uint64_t> okeys;
+    if (nadj > 0) {
+        k_orient_flags<<<grid_for(c, n * 32, B), B, 0, c.stream>>>(n, out.off.p, out.adj.p,
+                                                                  out.rank.p, flags.p);
+        KDSS_LAUNCH_CHECK();
+        m1 = exclusive_scan_i64(c, flags.p, pos.p, nadj);
+        okeys = DBuf<uint64_t>(c, (size_t)std::max<int64_t>(m1, 1));
+        k_orient_keys<<<grid_for(c, n * 32, B), B, 0, c.stream>>>(n, out.off.p, out.adj.p,
+                                                                 out.rank.p, flags.p, pos.p,
+                                                                 okeys.p);
+        KDSS_LAUNCH_CHECK();
+        radix_sort_u64(c, okeys.p, nullptr, m1, {{0, b}, {32, 32 + b}});
+    }
+    flags.reset();
+    pos.reset();
+    out.out_off = DBuf<int64_t>(c, (size_t)(n + 1));
+    out.out_adj = DBuf<int32_t>(c, (size_t)std::max<int64_t>(m1, 1));
+    row_offsets_from_sorted(c, okeys.p, m1, n, out.out_off.p);
+    if (m1 > 0) {
+        k_low32<<<grid_for(c, m1, B), B, 0, c.stream>>>(okeys.p, m1, out.out_adj.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    DBuf<int> mx(c, 1);
+    zero(c, mx.p, sizeof(int));
+    if (n > 0) {
+        k_max_rowlen<<<grid_for(c, n, B), B, 0, c.stream>>>(out.out_off.p, n, mx.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    to_host(c, &out.max_out, mx.p, 1);
+}
+
+}  // namespace kdss

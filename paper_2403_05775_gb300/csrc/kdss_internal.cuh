@@ -1,0 +1,192 @@
+// kdss_internal.cuh -- shared internals of the CUDA solver (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kdss.h"
+
+namespace kdss {
+
+// ---------------------------------------------------------------------------
+// Errors: C++ exceptions inside the library, converted to kdss_status at the
+// ABI boundary (api.cu).  Nothing throws across extern "C".
+// ---------------------------------------------------------------------------
+struct Error {
+    kdss_status code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(kdss_status code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+
+#define KDSS_CUDA(call) ::kdss::check_cuda((call), #call, __FILE__, __LINE__)
+// Every kernel launch is followed by KDSS_LAUNCH_CHECK(), which also counts it.
+void count_launch();
+#define KDSS_LAUNCH_CHECK() \
+    (::kdss::count_launch(), ::kdss::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
+
+// Device error word bits set by kernels (never a trap).
+enum : int {
+    DERR_NONE = 0,
+    DERR_BAD_ID = 1,        // an id outside [0, n)
+    DERR_OVERFLOW = 2,      // a count left its exact range
+    DERR_TIMEOUT = 4,       // a bounded wait expired
+    DERR_CAPACITY = 8,      // a bounded buffer would overflow (skipped)
+    DERR_LOGIC = 16,        // an invariant failed (e.g. water-filling found no room)
+};
+
+// ---------------------------------------------------------------------------
+// Device memory through the caller's allocator or stream-ordered cudaMalloc.
+// ---------------------------------------------------------------------------
+struct Ctx {
+    cudaStream_t stream = nullptr;
+    kdss_alloc_fn alloc = nullptr;
+    kdss_free_fn free = nullptr;
+    void *actx = nullptr;
+    int num_sms = 0;
+    int device = 0;
+};
+
+Ctx make_ctx(const kdss_opts *o);
+void *dalloc(const Ctx &c, size_t bytes);
+void dfree(const Ctx &c, void *p, size_t bytes);
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    Ctx ctx{};
+    DBuf() = default;
+    DBuf(const Ctx &c, size_t count) : n(count), ctx(c) {
+        p = count ? static_cast<T *>(dalloc(c, count * sizeof(T))) : nullptr;
+    }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), ctx(o.ctx) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) { reset(); p = o.p; n = o.n; ctx = o.ctx; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p) dfree(ctx, p, n * sizeof(T));
+        p = nullptr; n = 0;
+    }
+    T *get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// Pinned-free host <-> device helpers on the context stream (synchronous).
+template <class T>
+void to_host(const Ctx &c, T *dst, const T *src, size_t count) {
+    if (!count) return;
+    KDSS_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, c.stream));
+    KDSS_CUDA(cudaStreamSynchronize(c.stream));
+}
+template <class T>
+void to_device(const Ctx &c, T *dst, const T *src, size_t count) {
+    if (!count) return;
+    KDSS_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, c.stream));
+}
+void sync(const Ctx &c);
+void zero(const Ctx &c, void *p, size_t bytes);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int bit_length(uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return b; }
+
+// Grid size for a grid-stride kernel: a multiple of the SM count.
+int grid_for(const Ctx &c, int64_t work_items, int block, int blocks_per_sm = 8);
+
+// ---------------------------------------------------------------------------
+// Primitives (scan_sort.cu)
+// ---------------------------------------------------------------------------
+// out[i] = sum of in[0..i) for i < n; returns the total (synchronises).
+int64_t exclusive_scan_i64(const Ctx &c, const int64_t *in, int64_t *out, int64_t n);
+// In-place variant that does not read the total back (stream-ordered).
+void exclusive_scan_i64_async(const Ctx &c, const int64_t *in, int64_t *out, int64_t n);
+void inclusive_scan_u64_async(const Ctx &c, const uint64_t *in, uint64_t *out, int64_t n);
+
+// Stable LSD radix sort of 64-bit keys (with optional int32 payload) on the
+// digit positions that cover bits [lo, hi) of each range in `ranges`.
+// keys/vals are sorted in place (double-buffered internally).
+struct BitRange { int lo, hi; };
+void radix_sort_u64(const Ctx &c, uint64_t *keys, int32_t *vals, int64_t n,
+                    const std::vector<BitRange> &ranges);
+
+// Offsets of a sorted key array whose high 32 bits are a row index:
+// off[r] = first position with row >= r, r = 0..nrows.
+void row_offsets_from_sorted(const Ctx &c, const uint64_t *keys, int64_t nkeys, int64_t nrows,
+                             int64_t *off);
+
+// Max of a u64 array (synchronises).
+uint64_t reduce_max_u64(const Ctx &c, const uint64_t *in, int64_t n);
+
+// Bounded grid barrier for cooperative kernels: every wait gives up after a
+// deadline (ns of %globaltimer) and sets DERR_TIMEOUT in *err.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+}  // namespace kdss
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace kdss {
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All threads of all (co-resident) blocks call this.  Returns false when the
+// wait timed out (the error word then holds DERR_TIMEOUT).
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned int nblocks, int *err,
+                                             uint64_t timeout_ns) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &bar->gen;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&bar->count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            while (*vgen == g) {
+                __nanosleep(64);
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicOr(err, DERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace kdss
+#endif

@@ -1,0 +1,87 @@
+// runtime.cu -- errors, device allocation and launch sizing for the solver.
+#include <atomic>
+#include <cstdarg>
+#include <cstring>
+
+#include "kdss_internal.cuh"
+
+namespace kdss {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+void fail(kdss_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        fail(KDSS_ERR_OOM, buf);
+    }
+    fail(KDSS_ERR_CUDA, buf);
+}
+
+Ctx make_ctx(const kdss_opts *o) {
+    Ctx c;
+    if (o) {
+        c.stream = static_cast<cudaStream_t>(o->stream);
+        c.alloc = o->alloc;
+        c.free = o->free;
+        c.actx = o->alloc_ctx;
+        if ((c.alloc == nullptr) != (c.free == nullptr))
+            fail(KDSS_ERR_INVALID_ARG, "opts.alloc and opts.free must be set together");
+    }
+    KDSS_CUDA(cudaGetDevice(&c.device));
+    KDSS_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+    return c;
+}
+
+void *dalloc(const Ctx &c, size_t bytes) {
+    if (bytes == 0) return nullptr;
+    void *p = nullptr;
+    if (c.alloc) {
+        p = c.alloc(bytes, c.stream, c.actx);
+        if (!p) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "device allocation of %zu bytes failed", bytes);
+            fail(KDSS_ERR_OOM, buf);
+        }
+        return p;
+    }
+    cudaError_t e = cudaMallocAsync(&p, bytes, c.stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof buf, "cudaMallocAsync of %zu bytes failed: %s", bytes,
+                 cudaGetErrorString(e));
+        fail(e == cudaErrorMemoryAllocation ? KDSS_ERR_OOM : KDSS_ERR_CUDA, buf);
+    }
+    return p;
+}
+
+void dfree(const Ctx &c, void *p, size_t bytes) {
+    if (!p) return;
+    if (c.free) {
+        c.free(p, bytes, c.stream, c.actx);
+        return;
+    }
+    cudaFreeAsync(p, c.stream);  // destructors must not throw
+}
+
+void sync(const Ctx &c) { KDSS_CUDA(cudaStreamSynchronize(c.stream)); }
+
+void zero(const Ctx &c, void *p, size_t bytes) {
+    if (bytes) KDSS_CUDA(cudaMemsetAsync(p, 0, bytes, c.stream));
+}
+
+int grid_for(const Ctx &c, int64_t work_items, int block, int blocks_per_sm) {
+    int64_t need = ceil_div(work_items > 0 ? work_items : 1, block);
+    int64_t cap = (int64_t)c.num_sms * blocks_per_sm;
+    if (need >= cap) return (int)cap;
+    return (int)need;
+}
+
+}  // namespace kdss

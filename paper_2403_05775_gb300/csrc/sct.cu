@@ -1,0 +1,538 @@
+// sct.cu -- step A3: the succinct clique tree restricted to P_k.
+//
+// Sec. 2 and Lemmas 2.4-2.5: the pairs (V_h, V_p) of the SCT encode every
+// clique exactly once as V_h plus a subset of V_p; P_k keeps the pairs with
+// |V_h| <= k <= |V(P)|, whose k-cliques partition C_k(V).  The construction
+// (cited by the paper from Pivoter) is a pivoting recursion per root vertex v
+// over its later neighbours N+(v) in the build order:
+//   node (cand, hold, pivot):
+//     cand empty          -> emit (hold, pivot) when |hold| <= k <= |hold|+|pivot|
+//     otherwise pick the candidate x with the most neighbours inside cand
+//     (ties: earliest in the order);
+//       pivot branch      (cand & N(x), hold, pivot + x)
+//       for each w in cand \ N[x], in order:
+//                          (cand & N(w), hold + w, pivot), then cand -= w
+//   pruned when |hold| > k or |hold| + |pivot| + |cand| < k (Lemma 2.5).
+//
+// GPU mapping: one warp per root, roots handed out by an atomic counter.
+// The root's out-neighbourhood (d <= max out-degree) becomes a d x d bitset
+// adjacency matrix; the recursion is an explicit depth-first stack of
+// candidate / to-do bitsets, one 32-bit word per lane.  A count pass sizes
+// every (length class, root) slot, an exclusive scan turns the counts into
+// offsets, and an emit pass re-runs the same recursion and writes the pairs.
+#include <algorithm>
+
+#include "sct.cuh"
+
+namespace kdss {
+
+std::vector<uint64_t> host_binom_table(int rows, int k) {
+    const int cols = k + 1;
+    std::vector<uint64_t> t((size_t)rows * cols, 0);
+    const uint64_t LIM = 1ull << 63;
+    for (int a = 0; a < rows; ++a) {
+        for (int b = 0; b <= k; ++b) {
+            uint64_t v;
+            if (b > a) v = 0;
+            else if (b == 0 || b == a) v = 1;
+            else {
+                uint64_t x = t[(size_t)(a - 1) * cols + b - 1], y = t[(size_t)(a - 1) * cols + b];
+                if (x == ~0ull || y == ~0ull || x >= LIM - y) v = ~0ull;
+                else v = x + y;
+            }
+            t[(size_t)a * cols + b] = v;
+        }
+    }
+    return t;
+}
+
+namespace {
+
+constexpr int SCT_THREADS = 256;
+constexpr int SCT_WARPS = SCT_THREADS / 32;
+
+__host__ __device__ inline size_t ws_words(int dmax, int S) {
+    size_t f = (size_t)dmax + 2;
+    return (size_t)dmax + (size_t)dmax * S + 2 * f * S + 6 * f;
+}
+
+__device__ __forceinline__ int dev_class(int len) {
+    return len <= 8 ? 0 : len <= 16 ? 1 : len <= 32 ? 2 : len <= 256 ? 3 : len <= 1024 ? 4 : -1;
+}
+
+struct CountOut {
+    int64_t *cntP;   // [NCLASS * n], class-major
+    int64_t *cntN;
+    unsigned long long *ck;  // [2] lo, hi
+    int *maxlen;
+};
+struct EmitOut {
+    const int64_t *baseP;    // [NCLASS * n]
+    const int64_t *baseN;
+    int64_t *pair_off;
+    int32_t *nodes;
+    uint8_t *h;
+};
+
+template <bool EMIT>
+__global__ void __launch_bounds__(SCT_THREADS)
+k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_adj,
+      const int32_t *__restrict__ vert, int k, int dmax, int S,
+      const uint64_t *__restrict__ binom, int bcols, uint32_t *gws, int use_shared,
+      unsigned long long *next_root, CountOut co, EmitOut eo, int *err) {
+    extern __shared__ uint32_t smem[];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const size_t ww = ws_words(dmax, S);
+    uint32_t *base = use_shared ? smem + (size_t)wib * ww : gws + (size_t)gwarp * ww;
+    const int F = dmax + 2;
+    int32_t *O = (int32_t *)base;
+    uint32_t *A = base + dmax;
+    uint32_t *cand = A + (size_t)dmax * S;
+    uint32_t *todo = cand + (size_t)F * S;
+    int32_t *hold = (int32_t *)(todo + (size_t)F * S);
+    int32_t *piv = hold + F;
+    int32_t *fnh = piv + F;
+    int32_t *fnp = fnh + F;
+    int32_t *fph = fnp + F;
+    int32_t *ids = fph + F;
+
+    while (true) {
+        unsigned long long rr = 0;
+        if (lane == 0) rr = atomicAdd(next_root, 1ull);
+        rr = __shfl_sync(FULL, rr, 0);
+        if (rr >= (unsigned long long)n) break;
+        const int64_t root = (int64_t)rr;
+        const int64_t o0 = out_off[root];
+        const int d = (int)(out_off[root + 1] - o0);
+        if (d + 1 < k) continue;
+        const int W = (d + 31) >> 5;
+
+        // local vertex list and its adjacency bitsets
+        for (int j = lane; j < d; j += 32) O[j] = out_adj[o0 + j];
+        for (int q = lane; q < d * S; q += 32) A[q] = 0u;
+        __syncwarp();
+        for (int j = 0; j < d; ++j) {
+            const int32_t u = O[j];
+            const int64_t e0 = out_off[u], e1 = out_off[u + 1];
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
+                const int32_t w = out_adj[e];
+                int lo = j + 1, hi = d;  // w is later than u, so after j in O
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (O[mid] < w) lo = mid + 1; else hi = mid;
+                }
+                if (lo < d && O[lo] == w) {
+                    atomicOr(&A[(size_t)j * S + (lo >> 5)], 1u << (lo & 31));
+                    atomicOr(&A[(size_t)lo * S + (j >> 5)], 1u << (j & 31));
+                }
+            }
+        }
+        // per-root outputs (lane 0)
+        int64_t cP[NCLASS], cN[NCLASS];
+#pragma unroll
+        for (int c = 0; c < NCLASS; ++c) {
+            cP[c] = EMIT ? eo.baseP[(int64_t)c * n + root] : 0;
+            cN[c] = EMIT ? eo.baseN[(int64_t)c * n + root] : 0;
+        }
+        unsigned long long ck_lo = 0, ck_hi = 0;
+        int mlen = 0;
+
+        if (lane < W) {
+            int rem = d - lane * 32;
+            cand[lane] = rem >= 32 ? FULL : ((1u << rem) - 1u);
+        }
+        if (lane == 0) { fnh[0] = 1; fnp[0] = 0; fph[0] = 0; hold[0] = -1; }
+        __syncwarp();
+        int depth = 0;
+        while (depth >= 0) {
+            uint32_t *cd = cand + (size_t)depth * S;
+            uint32_t *td = todo + (size_t)depth * S;
+            const int h = fnh[depth], p = fnp[depth];
+            if (fph[depth] == 0) {
+                const uint32_t cw = lane < W ? cd[lane] : 0u;
+                const int nc = (int)__reduce_add_sync(FULL, (unsigned)__popc(cw));
+                if (h > k || h + p + nc < k) { --depth; continue; }
+                if (nc == 0) {
+                    if (h <= k && k <= h + p) {
+                        const int len = h + p;
+                        const int cls = dev_class(len);
+                        const uint64_t nC = binom[(size_t)p * bcols + (k - h)];
+                        if (cls < 0 || nC == ~0ull) {
+                            if (lane == 0) atomicOr(err, cls < 0 ? DERR_CAPACITY : DERR_OVERFLOW);
+                        } else if (!EMIT) {
+                            if (lane == 0) {
+                                cP[cls] += 1;
+                                cN[cls] += len;
+                                unsigned long long o = ck_lo;
+                                ck_lo += nC;
+                                ck_hi += ck_lo < o ? 1ull : 0ull;
+                                mlen = len > mlen ? len : mlen;
+                            }
+                        } else {
+                            int64_t pidx = 0, noff = 0;
+                            if (lane == 0) {
+                                pidx = cP[cls]++;
+                                noff = cN[cls];
+                                cN[cls] += len;
+                            }
+                            pidx = __shfl_sync(FULL, pidx, 0);
+                            noff = __shfl_sync(FULL, noff, 0);
+                            for (int t = lane; t < len; t += 32) {
+                                int32_t id;
+                                uint32_t flag;
+                                if (t < h) {
+                                    const int li = hold[t];
+                                    id = li < 0 ? vert[root] : vert[O[li]];
+                                    flag = HOLD_BIT;
+                                } else {
+                                    id = vert[O[piv[t - h]]];
+                                    flag = 0u;
+                                }
+                                ids[t] = (int32_t)((uint32_t)id | flag);
+                            }
+                            __syncwarp();
+                            for (int t = lane; t < len; t += 32) {
+                                const int32_t raw = ids[t];
+                                const int32_t my = raw & 0x7fffffff;
+                                int pos = 0;
+                                for (int u = 0; u < len; ++u) pos += ((ids[u] & 0x7fffffff) < my) ? 1 : 0;
+                                eo.nodes[noff + pos] = raw;
+                            }
+                            if (lane == 0) {
+                                eo.pair_off[pidx] = noff;
+                                eo.h[pidx] = (uint8_t)h;
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    --depth;
+                    continue;
+                }
+                // pivot: most neighbours inside cand, smallest index on ties
+                int bc = -1, bx = 0x7fffffff;
+                for (int x = lane; x < d; x += 32) {
+                    if ((cd[x >> 5] >> (x & 31)) & 1u) {
+                        const uint32_t *ax = A + (size_t)x * S;
+                        int cnt = 0;
+                        for (int w = 0; w < W; ++w) cnt += __popc(ax[w] & cd[w]);
+                        if (cnt > bc) { bc = cnt; bx = x; }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    int obc = __shfl_xor_sync(FULL, bc, o);
+                    int obx = __shfl_xor_sync(FULL, bx, o);
+                    if (obc > bc || (obc == bc && obx < bx)) { bc = obc; bx = obx; }
+                }
+                if (depth + 1 >= F) {  // cannot happen: each level adds a node
+                    if (lane == 0) atomicOr(err, DERR_LOGIC);
+                    break;
+                }
+                const uint32_t *ax = A + (size_t)bx * S;
+                if (lane < W) {
+                    uint32_t tw = cw & ~ax[lane];
+                    if (lane == (bx >> 5)) tw &= ~(1u << (bx & 31));
+                    if (h >= k) tw = 0u;  // hold branches would exceed k
+                    td[lane] = tw;
+                    cand[(size_t)(depth + 1) * S + lane] = cw & ax[lane];
+                }
+                if (lane == 0) {
+                    fph[depth] = 1;
+                    piv[p] = bx;
+                    fnh[depth + 1] = h;
+                    fnp[depth + 1] = p + 1;
+                    fph[depth + 1] = 0;
+                }
+                __syncwarp();
+                ++depth;
+            } else {
+                const uint32_t tw = lane < W ? td[lane] : 0u;
+                const unsigned any = __ballot_sync(FULL, tw != 0u);
+                if (!any) { --depth; continue; }
+                const int src = __ffs(any) - 1;
+                const uint32_t word = __shfl_sync(FULL, tw, src);
+                const int w = src * 32 + __ffs(word) - 1;
+                if (depth + 1 >= F) {
+                    if (lane == 0) atomicOr(err, DERR_LOGIC);
+                    break;
+                }
+                const uint32_t *aw = A + (size_t)w * S;
+                if (lane < W) {
+                    const uint32_t cw = cd[lane];
+                    cand[(size_t)(depth + 1) * S + lane] = cw & aw[lane];
+                    if (lane == src) {
+                        td[lane] = tw & ~(1u << (w & 31));
+                        cd[lane] = cw & ~(1u << (w & 31));
+                    }
+                }
+                if (lane == 0) {
+                    hold[h] = w;
+                    fnh[depth + 1] = h + 1;
+                    fnp[depth + 1] = p;
+                    fph[depth + 1] = 0;
+                }
+                __syncwarp();
+                ++depth;
+            }
+        }
+        if (!EMIT && lane == 0) {
+#pragma unroll
+            for (int c = 0; c < NCLASS; ++c) {
+                co.cntP[(int64_t)c * n + root] = cP[c];
+                co.cntN[(int64_t)c * n + root] = cN[c];
+            }
+            if (ck_lo || ck_hi) {
+                unsigned long long old = atomicAdd(&co.ck[0], ck_lo);
+                unsigned long long carry = (old + ck_lo < old) ? 1ull : 0ull;
+                if (ck_hi + carry) atomicAdd(&co.ck[1], ck_hi + carry);
+            }
+            atomicMax(co.maxlen, mlen);
+        }
+        __syncwarp();
+    }
+}
+
+// ---- caller-given pairs -> device layout ---------------------------------
+__global__ void k_pair_classes(int64_t np, const int64_t *off, const int32_t *h, int k,
+                               int64_t n, const int32_t *nodes, uint64_t *keys, int *err) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t len = off[q + 1] - off[q];
+        int cls = dev_class((int)(len > 2048 ? 2048 : len));
+        if (len < 0 || cls < 0 || h[q] < 0 || h[q] > k || len < k) {
+            atomicOr(err, DERR_BAD_ID);
+            cls = NCLASS - 1;
+        }
+        keys[q] = ((uint64_t)cls << 32) | (uint64_t)q;
+    }
+    (void)n; (void)nodes;
+}
+
+__global__ void k_pair_lens(int64_t np, const uint64_t *keys, const int64_t *off, int64_t *lens) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = (int64_t)(keys[i] & 0xffffffffu);
+        lens[i] = off[q + 1] - off[q];
+    }
+}
+
+// warp per pair: copy with ids sorted ascending and the hold flag set
+__global__ void k_pair_copy(int64_t np, const uint64_t *keys, const int64_t *off,
+                            const int32_t *h, const int32_t *nodes, const int64_t *newoff,
+                            int64_t n, int32_t *onodes, uint8_t *oh, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < np; i += nwarps) {
+        const int64_t q = (int64_t)(keys[i] & 0xffffffffu);
+        const int64_t b = off[q], len = off[q + 1] - b;
+        const int hq = h[q];
+        for (int64_t t = lane; t < len; t += 32) {
+            const int32_t my = nodes[b + t];
+            if (my < 0 || my >= n) { atomicOr(err, DERR_BAD_ID); continue; }
+            int64_t pos = 0;
+            for (int64_t u = 0; u < len; ++u) {
+                int32_t o = nodes[b + u];
+                pos += (o < my || (o == my && u < t)) ? 1 : 0;
+            }
+            onodes[newoff[i] + pos] = (int32_t)((uint32_t)my | (t < hq ? HOLD_BIT : 0u));
+        }
+        if (lane == 0) oh[i] = (uint8_t)hq;
+    }
+}
+
+__global__ void k_pair_ck(int64_t np, const int64_t *off, const uint8_t *h, const uint64_t *binom,
+                          int bcols, int k, unsigned long long *ck, int *maxlen, int *err) {
+    unsigned long long lo = 0, hi = 0;
+    int ml = 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int len = (int)(off[q + 1] - off[q]);
+        int hq = h[q], p = len - hq;
+        uint64_t nC = binom[(size_t)p * bcols + (k - hq)];
+        if (nC == ~0ull) atomicOr(err, DERR_OVERFLOW);
+        unsigned long long o = lo;
+        lo += nC;
+        hi += lo < o ? 1ull : 0ull;
+        ml = len > ml ? len : ml;
+    }
+    unsigned long long old = atomicAdd(&ck[0], lo);
+    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(&ck[1], hi + carry);
+    atomicMax(maxlen, ml);
+}
+
+void upload_binom(const Ctx &c, int rows, int k, SctDev &out) {
+    std::vector<uint64_t> t = host_binom_table(rows, k);
+    out.binom = DBuf<uint64_t>(c, t.size());
+    to_device(c, out.binom.p, t.data(), t.size());
+    out.binom_rows = rows;
+    sync(c);  // the host table goes out of scope
+}
+
+}  // namespace
+
+void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
+    const int64_t n = g.n;
+    out.k = k;
+    out.n = n;
+    const int dmax = std::max(1, g.max_out);
+    if (dmax + 1 > MAX_PAIR_LEN)
+        fail(KDSS_ERR_UNSUPPORTED, "out-degree above 1023: pairs could exceed 1024 nodes");
+    const int S = (dmax + 31) / 32;
+    upload_binom(c, dmax + 2, k, out);
+    const int bcols = k + 1;
+
+    const size_t ww = ws_words(dmax, S);
+    const size_t smem = ww * sizeof(uint32_t) * SCT_WARPS;
+    int use_shared = smem <= 96 * 1024 ? 1 : 0;
+    int grid;
+    DBuf<uint32_t> gws;
+    if (use_shared) {
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sct<false>, SCT_THREADS, smem));
+        per_sm = std::max(1, per_sm);
+        grid = (int)std::min<int64_t>((int64_t)c.num_sms * per_sm, std::max<int64_t>(1, ceil_div(n, SCT_WARPS)));
+    } else {
+        // global workspace: bound its size to about 1 GiB
+        int64_t warps = std::max<int64_t>(SCT_WARPS, (int64_t)(1ull << 28) / (int64_t)ww);
+        warps = std::min<int64_t>(warps, (int64_t)c.num_sms * 32);
+        grid = (int)std::max<int64_t>(1, warps / SCT_WARPS);
+        gws = DBuf<uint32_t>(c, (size_t)grid * SCT_WARPS * ww);
+    }
+    const size_t dyn = use_shared ? smem : 0;
+
+    DBuf<int64_t> cntP(c, (size_t)(NCLASS * n)), cntN(c, (size_t)(NCLASS * n));
+    zero(c, cntP.p, cntP.bytes());  // roots without pairs write nothing
+    zero(c, cntN.p, cntN.bytes());
+    DBuf<unsigned long long> ctr(c, 4);  // [0] next root, [1..2] c_k
+    DBuf<int> ints(c, 2);                // [0] max len, [1] error
+    zero(c, ctr.p, 4 * sizeof(unsigned long long));
+    zero(c, ints.p, 2 * sizeof(int));
+    CountOut co{cntP.p, cntN.p, ctr.p + 1, ints.p};
+    EmitOut eo{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (n > 0) {
+        k_sct<false><<<grid, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k,
+                                                          dmax, S, out.binom.p, bcols, gws.p,
+                                                          use_shared, ctr.p, co, eo, ints.p + 1);
+        KDSS_LAUNCH_CHECK();
+    }
+    DBuf<int64_t> baseP(c, (size_t)(NCLASS * n)), baseN(c, (size_t)(NCLASS * n));
+    int64_t npairs = exclusive_scan_i64(c, cntP.p, baseP.p, NCLASS * n);
+    int64_t nnodes = exclusive_scan_i64(c, cntN.p, baseN.p, NCLASS * n);
+    unsigned long long hc[4];
+    int hi[2];
+    to_host(c, hc, ctr.p, 4);
+    to_host(c, hi, ints.p, 2);
+    if (hi[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs 63 bits or more");
+    if (hi[1] & DERR_CAPACITY) fail(KDSS_ERR_UNSUPPORTED, "a pair longer than 1024 nodes");
+    if (hi[1]) fail(KDSS_ERR_CUDA, "SCT build: inconsistent device state");
+    out.ck_lo = hc[1];
+    out.ck_hi = hc[2];
+    out.max_len = hi[0];
+    out.npairs = npairs;
+    out.nnodes = nnodes;
+    for (int cl = 0; cl < NCLASS; ++cl) {
+        int64_t v = 0;
+        if (n > 0) to_host(c, &v, baseP.p + (int64_t)cl * n, 1);
+        out.class_begin[cl] = v;
+    }
+    out.class_begin[NCLASS] = npairs;
+    cntP.reset();
+    cntN.reset();
+    out.pair_off = DBuf<int64_t>(c, (size_t)(npairs + 1));
+    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1));
+    out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(npairs, 1));
+    if (npairs > 0) {
+        zero(c, ctr.p, sizeof(unsigned long long));
+        EmitOut eo2{baseP.p, baseN.p, out.pair_off.p, out.nodes.p, out.h.p};
+        k_sct<true><<<grid, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k,
+                                                         dmax, S, out.binom.p, bcols, gws.p,
+                                                         use_shared, ctr.p, co, eo2, ints.p + 1);
+        KDSS_LAUNCH_CHECK();
+    }
+    to_device(c, out.pair_off.p + npairs, &nnodes, 1);
+    to_host(c, hi, ints.p, 2);
+    if (hi[1]) fail(KDSS_ERR_CUDA, "SCT emit: inconsistent device state");
+}
+
+void sct_from_pairs(const Ctx &c, int64_t n, int k, int64_t np, const int64_t *pair_off,
+                    const int32_t *nodes, const int32_t *h, SctDev &out) {
+    out.k = k;
+    out.n = n;
+    out.npairs = np;
+    const int B = 256;
+    DBuf<int> err(c, 1);
+    zero(c, err.p, sizeof(int));
+    DBuf<uint64_t> keys(c, (size_t)std::max<int64_t>(np, 1));
+    if (np > 0) {
+        k_pair_classes<<<grid_for(c, np, B), B, 0, c.stream>>>(np, pair_off, h, k, n, nodes, keys.p, err.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    int he = 0;
+    to_host(c, &he, err.p, 1);
+    if (he) fail(KDSS_ERR_INVALID_ARG, "pairs need 0 <= h <= k <= |V(P)| <= 1024");
+    radix_sort_u64(c, keys.p, nullptr, np, {{32, 35}});
+    DBuf<int64_t> lens(c, (size_t)std::max<int64_t>(np, 1));
+    out.pair_off = DBuf<int64_t>(c, (size_t)(np + 1));
+    int64_t nnodes = 0;
+    if (np > 0) {
+        k_pair_lens<<<grid_for(c, np, B), B, 0, c.stream>>>(np, keys.p, pair_off, lens.p);
+        KDSS_LAUNCH_CHECK();
+        nnodes = exclusive_scan_i64(c, lens.p, out.pair_off.p, np);
+    }
+    to_device(c, out.pair_off.p + np, &nnodes, 1);
+    out.nnodes = nnodes;
+    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1));
+    out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(np, 1));
+    if (np > 0) {
+        k_pair_copy<<<grid_for(c, np * 32, B), B, 0, c.stream>>>(np, keys.p, pair_off, h, nodes,
+                                                               out.pair_off.p, n, out.nodes.p,
+                                                               out.h.p, err.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    // class boundaries from the sorted keys
+    std::vector<uint64_t> hk((size_t)np);
+    if (np > 0) to_host(c, hk.data(), keys.p, (size_t)np);
+    for (int cl = 0; cl <= NCLASS; ++cl) {
+        int64_t lo = 0, hi = np;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if ((int)(hk[(size_t)mid] >> 32) < cl) lo = mid + 1; else hi = mid;
+        }
+        out.class_begin[cl] = lo;
+    }
+    out.class_begin[NCLASS] = np;
+    // binomial table up to the longest pair, then c_k
+    int maxlen = 0;
+    if (np > 0) {
+        std::vector<int64_t> hl((size_t)np);
+        to_host(c, hl.data(), lens.p, (size_t)np);
+        for (int64_t v : hl) maxlen = std::max<int>(maxlen, (int)v);
+    }
+    upload_binom(c, maxlen + 2, k, out);
+    DBuf<unsigned long long> ck(c, 2);
+    DBuf<int> ml(c, 1);
+    zero(c, ck.p, 2 * sizeof(unsigned long long));
+    zero(c, ml.p, sizeof(int));
+    if (np > 0) {
+        k_pair_ck<<<grid_for(c, np, B), B, 0, c.stream>>>(np, out.pair_off.p, out.h.p, out.binom.p,
+                                                         k + 1, k, ck.p, ml.p, err.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    unsigned long long hc[2];
+    to_host(c, hc, ck.p, 2);
+    to_host(c, &he, err.p, 1);
+    if (he & DERR_BAD_ID) fail(KDSS_ERR_INVALID_ARG, "a pair node id is outside [0, n)");
+    if (he & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs 63 bits or more");
+    out.ck_lo = hc[0];
+    out.ck_hi = hc[1];
+    out.max_len = maxlen;
+}
+
+}  // namespace kdss
