@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chunglu1e5")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--allocator", choices=["library", "torch"], default="library",
+                    help="device memory: the library's stream-ordered pool or torch's caching "
+                         "allocator (through callbacks)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP32 and time-to-1%% side measurements")
     return ap.parse_args()
@@ -239,7 +242,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(flags):
-        o = K.make_opts(precision=prec, flags=flags, stream=stream)
+        o = K.make_opts(precision=prec, flags=flags, stream=stream, allocator=args.allocator)
         sct = K.kdss_build_sct(n, src, dst, k, o)
         st = K.kdss_fw_iterate(sct, None, T, o)
         res = K.kdss_extract(sct, st, o)
@@ -290,7 +293,8 @@ def main():
         flush.fill_(3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r2 = K.kdss_solve(n, s_np, d_np, k, T, K.make_opts(precision=prec, stream=stream))
+        r2 = K.kdss_solve(n, s_np, d_np, k, T, K.make_opts(precision=prec, stream=stream,
+                                                           allocator=args.allocator))
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_value = T * ck * world / (statistics.mean(e2e_ms) / 1e3)
@@ -314,6 +318,7 @@ def main():
                    "degeneracy": info["degeneracy"], "precision": args.precision,
                    "rule": "continuous" if args.precision == "fp32k" else "integer (Alg. 3)",
                    "l2": "flushed by a 256 MiB write before every step",
+                   "allocator": args.allocator,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
@@ -332,7 +337,7 @@ def main():
     if rank == 0 and not args.no_extras:
         extras = {}
         # FP32 compensated continuous rule on the same workload
-        o32 = K.make_opts(precision=PRECISIONS["fp32k"], stream=stream)
+        o32 = K.make_opts(precision=PRECISIONS["fp32k"], stream=stream, allocator=args.allocator)
         t32 = []
         for _ in range(2):
             flush.fill_(5)
@@ -352,7 +357,7 @@ def main():
         # time to reach 99% of the oracle's density: build, then chunks of 5
         # iterations each followed by an extraction
         target = rho_oracle if rho_oracle is not None else res["density"]
-        o = K.make_opts(precision=prec, stream=stream)
+        o = K.make_opts(precision=prec, stream=stream, allocator=args.allocator)
         flush.fill_(7)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -27,7 +27,6 @@ struct kdss_state {
 
 namespace kdss {
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
-long long launches();
 }
 
 namespace {

@@ -62,6 +62,13 @@ __device__ __forceinline__ int gsum_i32(int v) {
     return v;
 }
 
+// 1 / s for iteration t = *t_done + 1 of the continuous rule, s = max(t - 1, 1)
+// (the step-size schedule is evaluated in FP64).
+__device__ __forceinline__ float inv_sigma_of(const int *t_done) {
+    const int t = *t_done + 1;
+    return (float)(1.0 / (double)(t - 1 > 1 ? t - 1 : 1));
+}
+
 template <class RT>
 __device__ __forceinline__ uint64_t load_r(const RT *r, int32_t id);
 template <>
@@ -72,12 +79,111 @@ template <>
 __device__ __forceinline__ uint64_t load_r<double>(const double *r, int32_t id) {
     return (uint64_t)__ldg(r + id);
 }
-__device__ __forceinline__ void add_acc(uint64_t *acc, int32_t id, uint64_t d) {
-    atomicAdd((unsigned long long *)(acc + id), (unsigned long long)d);
+// ---------------------------------------------------------------------------
+// Block-local aggregation of the scatter-adds.  Most pairs hand their units
+// to a few low-r nodes (on a power-law graph with a planted dense region,
+// under 2,000 distinct receivers for 1.6e5 pairs, the busiest node getting
+// tens of thousands of adds per iteration), and same-address global atomics
+// serialise.  Each block takes a contiguous chunk of pairs (consecutive pairs
+// share their root and usually their receiver), adds into a shared-memory
+// open-addressing table, and flushes one global atomic per distinct node.
+// A crowded table falls back to direct global atomics.
+// ---------------------------------------------------------------------------
+constexpr int AGG_BITS = 10;
+constexpr int AGG_SLOTS = 1 << AGG_BITS;
+constexpr int AGG_PROBES = 16;
+
+template <class V>
+struct AggTable {
+    int32_t key[AGG_SLOTS];
+    V val[AGG_SLOTS];
+    V comp[sizeof(V) == 4 ? AGG_SLOTS : 1];  // FP32: TwoSum error terms
+};
+
+__device__ __forceinline__ unsigned agg_hash(int32_t id) {
+    return ((uint32_t)id * 2654435761u) >> (32 - AGG_BITS);
 }
-__device__ __forceinline__ void add_acc(double *acc, int32_t id, uint64_t d) {
-    atomicAdd(acc + id, (double)d);
+
+template <class V>
+__device__ __forceinline__ void agg_init(AggTable<V> &t) {
+    for (int i = threadIdx.x; i < AGG_SLOTS; i += blockDim.x) {
+        t.key[i] = -1;
+        t.val[i] = V(0);
+        if (sizeof(V) == 4) t.comp[i] = V(0);
+    }
+    __syncthreads();
 }
+
+__device__ __forceinline__ void gadd(unsigned long long *g, int32_t id, unsigned long long x) {
+    atomicAdd(g + id, x);
+}
+__device__ __forceinline__ void gadd(double *g, int32_t id, double x) { atomicAdd(g + id, x); }
+// compensated FP32 add: the exact rounding error of the stored sum goes to gc
+__device__ __forceinline__ void gadd_f32(float *g, float *gc, int32_t id, float x) {
+    const float old = atomicAdd(g + id, x);
+    const float sum = old + x;
+    const float bp = sum - old;
+    const float e = (old - (sum - bp)) + (x - bp);
+    if (e != 0.f) atomicAdd(gc + id, e);
+}
+
+// slot of id in the table (inserting it), or -1 when the probe limit is hit
+template <class V>
+__device__ __forceinline__ int agg_slot(AggTable<V> &t, int32_t id) {
+    unsigned sl = agg_hash(id);
+    for (int pr = 0; pr < AGG_PROBES; ++pr) {
+        const int32_t k = ((volatile int32_t *)t.key)[sl];
+        if (k == id) return (int)sl;
+        if (k == -1) {
+            const int32_t old = atomicCAS(&t.key[sl], -1, id);
+            if (old == -1 || old == id) return (int)sl;
+        }
+        sl = (sl + 1) & (AGG_SLOTS - 1);
+    }
+    return -1;
+}
+
+template <class V>
+__device__ __forceinline__ void agg_add(AggTable<V> &t, int32_t id, V x, V *gacc) {
+    const int sl = agg_slot(t, id);
+    if (sl >= 0) atomicAdd(&t.val[sl], x);
+    else gadd(gacc, id, x);
+}
+
+__device__ __forceinline__ void agg_add_f32(AggTable<float> &t, int32_t id, float x, float *g,
+                                            float *gc) {
+    const int sl = agg_slot(t, id);
+    if (sl < 0) { gadd_f32(g, gc, id, x); return; }
+    const float old = atomicAdd(&t.val[sl], x);
+    const float sum = old + x;
+    const float bp = sum - old;
+    const float e = (old - (sum - bp)) + (x - bp);
+    if (e != 0.f) atomicAdd(&t.comp[sl], e);
+}
+
+template <class V>
+__device__ __forceinline__ void agg_flush(AggTable<V> &t, V *gacc) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < AGG_SLOTS; i += blockDim.x) {
+        const int32_t id = t.key[i];
+        if (id >= 0 && t.val[i] != V(0)) gadd(gacc, id, t.val[i]);
+    }
+}
+
+__device__ __forceinline__ void agg_flush_f32(AggTable<float> &t, float *g, float *gc) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < AGG_SLOTS; i += blockDim.x) {
+        const int32_t id = t.key[i];
+        if (id < 0) continue;
+        if (t.val[i] != 0.f) gadd_f32(g, gc, id, t.val[i]);
+        if (t.comp[i] != 0.f) atomicAdd(gc + id, t.comp[i]);
+    }
+}
+
+// Accumulator value type of the integer rule for each storage type.
+template <class RT> struct AccV;
+template <> struct AccV<uint64_t> { using T = unsigned long long; };
+template <> struct AccV<double> { using T = double; };
 
 // Rule I (integer) PBUpdate over the pairs [p_begin, p_end).
 template <int G, int NPL, class RT>
@@ -85,7 +191,7 @@ __global__ void __launch_bounds__(FW_THREADS)
 k_pbupdate_int(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
                const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
                const RT *__restrict__ r, RT *acc, const uint64_t *__restrict__ binom, int bcols,
-               int k, int *err) {
+               int k, const int32_t *list, const int *list_count, int *err) {
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -93,11 +199,24 @@ k_pbupdate_int(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
     const unsigned lowmask = (G == 32) ? FULL : ((1u << G) - 1u);
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t np = p_end - p_begin;
-    for (int64_t wb = warp * GPW; wb < np; wb += nwarps * GPW) {
+    // pairs [p_begin, p_end), or p_begin + list[i] for i < *list_count; each
+    // block takes one contiguous chunk
+    int64_t np = p_end - p_begin;
+    if (list) {
+        const int lc = *list_count;
+        np = lc < np ? lc : np;
+    }
+    using AV = typename AccV<RT>::T;
+    __shared__ AggTable<AV> tbl;
+    agg_init(tbl);
+    const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
+    const int64_t cb = blockIdx.x * chunk, ce = cb + chunk < np ? cb + chunk : np;
+    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    (void)warp; (void)nwarps;
+    for (int64_t wb = cb + wib * GPW; wb < ce; wb += wpb * GPW) {
         const int64_t qi = wb + lane / G;
-        const bool active = qi < np;
-        const int64_t q = p_begin + qi;
+        const bool active = qi < ce;
+        const int64_t q = p_begin + (list ? (active ? (int64_t)list[qi] : 0) : qi);
         int64_t off0 = 0;
         int len = 0, h = 0;
         if (active) {
@@ -189,9 +308,361 @@ k_pbupdate_int(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int j = s * G + gl;
-            if (active && j < len && cur[s] > r0[s]) add_acc(acc, id[s], cur[s] - r0[s]);
+            if (active && j < len && cur[s] > r0[s])
+                agg_add(tbl, id[s], (AV)(cur[s] - r0[s]), (AV *)acc);
         }
     }
+    agg_flush(tbl, (AV *)acc);
+}
+
+// Warp-segmented aggregation of scatter-adds: lanes holding the same node id
+// in consecutive lanes (consecutive pairs usually hand their units to the
+// same low-r node) are summed by a segmented scan, and the last lane of each
+// run issues one atomic.  Lanes with id < 0 take no part.  Full-warp
+// shuffles only; every lane of the warp must call it.
+template <class V>
+__device__ __forceinline__ void warp_seg_add(int32_t id, V x, V *gacc) {
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int32_t prev = __shfl_up_sync(FULL_, id, 1);
+    const bool head = lane == 0 || prev != id;
+    const unsigned heads = __ballot_sync(FULL_, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = __shfl_up_sync(FULL_, x, o);
+        if (lane - o >= start) x += y;
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && id >= 0 && x != V(0)) atomicAdd(gacc + id, x);
+}
+
+// First step of Alg. 3 for pairs of at most 32 nodes.  A warp takes 32
+// consecutive pairs: their node ids are read with coalesced loads and their
+// r values gathered in parallel into shared memory (bit 63 marks V_h nodes);
+// then lane i streams pair i from shared memory, finding the lowest level m1
+// among the nodes that can receive, the set A of nodes at m1 (slot mask) and
+// the next level m2.  With w = floor(n_C/|A|) and R = n_C - w|A|, the walk of
+// Alg. 3 ends on this plateau exactly when no node of A reaches its cap and
+// the plateau does not reach m2: w < min(cap, m2 - m1) (w <= when R = 0).
+// Then every node of A takes w and the R lowest ids one more (lines 10-17).
+// The other pairs (several plateaus or a cap inside the fill) are appended
+// to `slow`.
+constexpr int FA_WARPS = 4;
+constexpr int FA_CAP = 32 * 32;
+constexpr uint64_t VHOLD = 1ull << 63;
+
+template <class RT>
+__global__ void __launch_bounds__(FA_WARPS * 32)
+k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+          const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
+          const RT *__restrict__ r, RT *acc, const uint64_t *__restrict__ binom, int bcols,
+          int k, int32_t *slow, int *slow_count, int *err) {
+    __shared__ uint64_t sval[FA_WARPS][FA_CAP];
+    using AV = typename AccV<RT>::T;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t np = p_end - p_begin;
+    const int64_t ntile = (np + 31) >> 5;
+    uint64_t *sv = sval[wib];
+    for (int64_t tile = blockIdx.x * (int64_t)FA_WARPS + wib; tile < ntile;
+         tile += (int64_t)gridDim.x * FA_WARPS) {
+        const int64_t qi = tile * 32 + lane;
+        const bool valid = qi < np;
+        const int64_t q = p_begin + (valid ? qi : np - 1);
+        const int64_t myb = pair_off[q], mye = pair_off[q + 1];
+        const int64_t B = __shfl_sync(0xffffffffu, myb, 0);
+        const int64_t lastq = p_begin + ((tile * 32 + 31 < np) ? tile * 32 + 31 : np - 1);
+        const int64_t E = pair_off[lastq + 1];
+        const int cnt = (int)(E - B);  // <= 1024 for pairs of <= 32 nodes
+        if (cnt > FA_CAP) {             // not a range of short pairs (uniform)
+            if (lane == 0) atomicOr(err, DERR_CAPACITY);
+            continue;
+        }
+        // stage: coalesced ids, parallel gathers
+#pragma unroll 4
+        for (int i = lane; i < cnt; i += 32) {
+            const int32_t raw = __ldg(nodes + B + i);
+            const uint64_t v = load_r<RT>(r, raw & 0x7fffffff);
+            sv[i] = raw < 0 ? (v | VHOLD) : v;
+        }
+        __syncwarp();
+        uint32_t rmask = 0;     // receivers (slot bits)
+        uint64_t w = 0, R = 0;
+        int o = 0;
+        if (valid) {
+            o = (int)(myb - B);
+            const int len = (int)(mye - myb);
+            const int h = hcnt[q];
+            const int p = len - h;
+            const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
+            const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                                       ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+            uint64_t m1 = ~0ull, m2 = ~0ull;
+            uint32_t mask1 = 0, holdm = 0;
+            for (int s = 0; s < len; ++s) {
+                const uint64_t e = sv[o + s];
+                const bool hold = (e & VHOLD) != 0;
+                if (hold) holdm |= 1u << s;
+                if (hold ? nC == 0 : cap_p == 0) continue;  // zero cap: never receives
+                const uint64_t v = e & ~VHOLD;
+                if (v < m1) { m2 = m1; m1 = v; mask1 = 1u << s; }
+                else if (v == m1) mask1 |= 1u << s;
+                else if (v < m2) m2 = v;
+            }
+            if (mask1) {
+                const uint64_t na = (uint64_t)__popc(mask1);
+                const uint64_t mu = (mask1 & ~holdm) ? cap_p : nC;
+                const uint64_t gap = m2 == ~0ull ? ~0ull : m2 - m1;
+                w = nC / na;
+                R = nC - w * na;
+                const uint64_t lim = mu < gap ? mu : gap;
+                if (!(R == 0 ? w > lim : w >= lim)) {
+                    rmask = mask1;  // settled by the first step
+                } else {
+                    const int slot = atomicAdd(slow_count, 1);
+                    if (slot < np) slow[slot] = (int32_t)qi;
+                }
+            }
+        }
+        // scatter the allocation, one receiver per lane per round
+        uint64_t rank = 0;
+        while (__any_sync(0xffffffffu, rmask != 0)) {
+            int32_t rid = -1;
+            AV amount = AV(0);
+            if (rmask) {
+                const int sl = __ffs(rmask) - 1;
+                rmask &= rmask - 1;
+                const uint64_t dl = w + (rank < R ? 1ull : 0ull);
+                ++rank;
+                if (dl) {
+                    rid = __ldg(nodes + B + o + sl) & 0x7fffffff;
+                    amount = (AV)dl;
+                }
+            }
+            warp_seg_add<AV>(rid, amount, (AV *)acc);
+        }
+        __syncwarp();  // sv is rewritten by the next tile
+    }
+}
+
+// The pairs the first-step kernel left (several plateaus or a cap inside the
+// fill), one warp per pair of at most 32 nodes, in closed form.  The
+// allocation of Alg. 3 is the integer water level: with
+// g(L) = sum_i min(cap_i, max(0, L - r_i)), L* is the largest L with
+// g(L) <= n_C, node i gets min(cap_i, max(0, L* - r_i)) and the
+// n_C - g(L*) lowest ids among the nodes with r_i <= L* < r_i + cap_i one more.
+// g is piecewise linear with breakpoints r_i and r_i + cap_i; lane j
+// evaluates g and its right slope s at its own two breakpoints (a pass over
+// the pair in shared memory), the largest breakpoint b with g(b) <= n_C wins
+// a warp reduction, and L* = b + floor((n_C - g(b)) / s(b)) lies before the
+// next breakpoint.  Remainder ranks come from a ballot (lanes are in id order).
+constexpr int SB_WARPS = 8;
+
+template <class RT>
+__global__ void __launch_bounds__(SB_WARPS * 32)
+k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+          const uint8_t *__restrict__ hcnt, int64_t p_begin, const RT *__restrict__ r,
+          RT *acc, const uint64_t *__restrict__ binom, int bcols, int k,
+          const int32_t *__restrict__ list, const int *list_count, int64_t list_cap, int *err) {
+    __shared__ uint64_t sr[SB_WARPS][32];
+    __shared__ uint64_t sc[SB_WARPS][32];
+    using AV = typename AccV<RT>::T;
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int64_t np = *list_count;
+    np = np < list_cap ? np : list_cap;
+    for (int64_t li = blockIdx.x * (int64_t)SB_WARPS + wib; li < np;
+         li += (int64_t)gridDim.x * SB_WARPS) {
+        const int64_t q = p_begin + list[li];
+        const int64_t off0 = pair_off[q];
+        const int len = (int)(pair_off[q + 1] - off0);
+        if (len > 32) {  // uniform: not a short pair
+            if (lane == 0) atomicOr(err, DERR_CAPACITY);
+            continue;
+        }
+        const int h = hcnt[q];
+        const int p = len - h;
+        const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
+        const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                                   ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+        int32_t id = -1;
+        uint64_t rj = 0, cj = 0;
+        if (lane < len) {
+            const int32_t raw = __ldg(nodes + off0 + lane);
+            id = raw & 0x7fffffff;
+            rj = load_r<RT>(r, id);
+            cj = raw < 0 ? nC : cap_p;
+        }
+        // levels relative to the lowest node that can receive: 32-bit when
+        // the spread and n_C fit in 31 bits (the usual case)
+        uint64_t base = cj > 0 ? rj : ~0ull, top = cj > 0 ? rj : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t ob = __shfl_xor_sync(FULL_, base, o), ot = __shfl_xor_sync(FULL_, top, o);
+            base = ob < base ? ob : base;
+            top = ot > top ? ot : top;
+        }
+        if (top - base < (1ull << 31) && nC < (1ull << 31)) {
+            // (level, cap) of every node as one 64-bit word; a zero cap adds
+            // nothing below (min(d, 0) = 0), so no special case
+            uint2 *sp = (uint2 *)sr[wib];
+            const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
+            sp[lane] = make_uint2(rl, cl);
+            __syncwarp();
+            const uint32_t b1 = rl, b2 = rl + cl, lim = (uint32_t)nC + 1u, nC32 = (uint32_t)nC;
+            uint32_t g1 = 0, g2 = 0;
+#pragma unroll 4
+            for (int i = 0; i < len; ++i) {
+                const uint2 e = sp[i];
+                if (b1 > e.x) g1 = min(g1 + min(b1 - e.x, e.y), lim);
+                if (b2 > e.x) g2 = min(g2 + min(b2 - e.x, e.y), lim);
+            }
+            uint32_t key = 0, bg = 0;
+            int hv = 0;
+            if (cl > 0) {
+                if (g1 <= nC32) { key = b1; bg = g1; hv = 1; }
+                if (g2 <= nC32) { key = b2; bg = g2; hv = 1; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint32_t ok = __shfl_xor_sync(FULL_, key, o);
+                const int oh = __shfl_xor_sync(FULL_, hv, o);
+                const uint32_t og = __shfl_xor_sync(FULL_, bg, o);
+                if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; }
+            }
+            // right slope of g at the winning breakpoint
+            const int bs = __popc(__ballot_sync(FULL_, cl > 0 && key >= rl && key - rl < cl));
+            if (!hv || bs <= 0) {
+                if (lane == 0) atomicOr(err, DERR_LOGIC);
+                continue;
+            }
+            const uint32_t L = key + (nC32 - bg) / (uint32_t)bs;
+            uint32_t dj = 0;
+            bool elig = false;
+            if (cl > 0) {
+                if (L > rl) dj = min(L - rl, cl);
+                elig = rl <= L && L - rl < cl;
+            }
+            uint32_t tot = __reduce_add_sync(FULL_, dj);
+            const uint32_t R = nC32 - tot;
+            const unsigned eb = __ballot_sync(FULL_, elig);
+            if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+            if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+            __syncwarp();
+            continue;
+        }
+        sr[wib][lane] = rj;
+        sc[wib][lane] = cj;
+        __syncwarp();
+        // g and right slope at my breakpoints rj and rj + cj
+        const uint64_t b1 = rj, b2 = rj + cj, lim = nC + 1;
+        uint64_t g1 = 0, g2 = 0;
+        int s1 = 0, s2 = 0;
+        for (int i = 0; i < len; ++i) {
+            const uint64_t ri = sr[wib][i], ci = sc[wib][i];
+            if (ci == 0) continue;
+            if (b1 > ri) { const uint64_t d = b1 - ri; g1 += d < ci ? d : ci; }
+            if (b2 > ri) { const uint64_t d = b2 - ri; g2 += d < ci ? d : ci; }
+            g1 = g1 < lim ? g1 : lim;
+            g2 = g2 < lim ? g2 : lim;
+            s1 += (ri <= b1 && b1 - ri < ci) ? 1 : 0;
+            s2 += (ri <= b2 && b2 - ri < ci) ? 1 : 0;
+        }
+        // best breakpoint of this lane: the larger one with g <= n_C
+        uint64_t bb = 0, bg = 0;
+        int bs = 0;
+        bool have = false;
+        if (cj > 0) {
+            if (g1 <= nC) { bb = b1; bg = g1; bs = s1; have = true; }
+            if (g2 <= nC) { bb = b2; bg = g2; bs = s2; have = true; }
+        }
+        unsigned long long key = have ? (unsigned long long)bb : 0ull;
+        int hv = have ? 1 : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(FULL_, key, o);
+            const int oh = __shfl_xor_sync(FULL_, hv, o);
+            const uint64_t og = __shfl_xor_sync(FULL_, bg, o);
+            const int os = __shfl_xor_sync(FULL_, bs, o);
+            if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; bs = os; }
+        }
+        if (!hv || bs <= 0) {  // no room below n_C: invariant broken
+            if (lane == 0) atomicOr(err, DERR_LOGIC);
+            continue;
+        }
+        const uint64_t L = key + (nC - bg) / (uint64_t)bs;
+        uint64_t dj = 0;
+        bool elig = false;
+        if (cj > 0) {
+            if (L > rj) { const uint64_t d = L - rj; dj = d < cj ? d : cj; }
+            elig = rj <= L && L - rj < cj;
+        }
+        uint64_t tot = dj;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL_, tot, o);
+        const uint64_t R = nC - tot;
+        const unsigned eb = __ballot_sync(FULL_, elig);
+        if (elig && (uint64_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+        if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+        __syncwarp();
+    }
+}
+
+// The same first step for the continuous rule on the normalised iterate:
+// the plateau A takes n_C/s each when that stays within its caps and below
+// m2; otherwise the pair goes to the full walk.
+__global__ void __launch_bounds__(FW_THREADS)
+k_pb_fast_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+              const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
+              const float *__restrict__ r, float *acc, float *accc,
+              const uint64_t *__restrict__ binom, int bcols, int k, const int *t_done,
+              int32_t *slow, int *slow_count) {
+    const int64_t np = p_end - p_begin;
+    const float INF = __int_as_float(0x7f800000);
+    const float inv_sigma = inv_sigma_of(t_done);
+    __shared__ AggTable<float> tbl;
+    agg_init(tbl);
+    const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
+    const int64_t cb = blockIdx.x * chunk, ce = cb + chunk < np ? cb + chunk : np;
+    for (int64_t qi = cb + threadIdx.x; qi < ce; qi += blockDim.x) {
+        const int64_t q = p_begin + qi;
+        const int64_t off0 = pair_off[q];
+        const int len = (int)(pair_off[q + 1] - off0);
+        const int h = hcnt[q];
+        const int p = len - h;
+        const float nC = (float)__ldg(binom + (size_t)p * bcols + (k - h)) * inv_sigma;
+        const float cap_p = (p >= 1 && k - h - 1 >= 0)
+                                ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                                : 0.f;
+        float m1 = INF, m2 = INF;
+        uint32_t mask1 = 0, holdm = 0;
+        for (int s = 0; s < len; ++s) {
+            const int32_t raw = __ldg(nodes + off0 + s);
+            const bool hold = raw < 0;
+            if (hold) holdm |= 1u << s;
+            if (hold ? !(nC > 0.f) : !(cap_p > 0.f)) continue;
+            const float v = __ldg(r + (raw & 0x7fffffff));
+            if (v < m1) { m2 = m1; m1 = v; mask1 = 1u << s; }
+            else if (v == m1) mask1 |= 1u << s;
+            else if (v < m2) m2 = v;
+        }
+        if (!mask1) continue;
+        const float na = (float)__popc(mask1);
+        const float mu = (mask1 & ~holdm) ? cap_p : nC;
+        const float share = nC / na;
+        if (!(share <= mu && share <= m2 - m1)) {
+            const int slot = atomicAdd(slow_count, 1);
+            if (slot < np) slow[slot] = (int32_t)qi;
+            continue;
+        }
+        uint32_t bits = mask1;
+        while (bits) {
+            const int sl = __ffs(bits) - 1;
+            bits &= bits - 1;
+            agg_add_f32(tbl, __ldg(nodes + off0 + sl) & 0x7fffffff, share, acc, accc);
+        }
+    }
+    agg_flush_f32(tbl, acc, accc);
 }
 
 // Rule C (continuous) PBUpdate on the normalised iterate, FP32.
@@ -200,18 +671,31 @@ __global__ void __launch_bounds__(FW_THREADS)
 k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
                const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
                const float *__restrict__ r, float *acc, float *accc,
-               const uint64_t *__restrict__ binom, int bcols, int k, float inv_sigma, int *err) {
+               const uint64_t *__restrict__ binom, int bcols, int k, const int *t_done,
+               const int32_t *list, const int *list_count, int *err) {
     constexpr int GPW = 32 / G;
+    const float inv_sigma = inv_sigma_of(t_done);
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t np = p_end - p_begin;
+    // pairs [p_begin, p_end), or p_begin + list[i] for i < *list_count
+    int64_t np = p_end - p_begin;
+    if (list) {
+        const int lc = *list_count;
+        np = lc < np ? lc : np;
+    }
     const float INF = __int_as_float(0x7f800000);
-    for (int64_t wb = warp * GPW; wb < np; wb += nwarps * GPW) {
+    __shared__ AggTable<float> tbl;
+    agg_init(tbl);
+    const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
+    const int64_t cb = blockIdx.x * chunk, ce = cb + chunk < np ? cb + chunk : np;
+    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    (void)warp; (void)nwarps;
+    for (int64_t wb = cb + wib * GPW; wb < ce; wb += wpb * GPW) {
         const int64_t qi = wb + lane / G;
-        const bool active = qi < np;
-        const int64_t q = p_begin + qi;
+        const bool active = qi < ce;
+        const int64_t q = p_begin + (list ? (active ? (int64_t)list[qi] : 0) : qi);
         int64_t off0 = 0;
         int len = 0, h = 0;
         if (active) {
@@ -241,13 +725,21 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
             cur[s] = r0[s];
         }
         float rem = active ? nC : 0.f;
-        float lev;
+        // Work relative to the pair's lowest active level, so that the
+        // allocation (final level - start) is not a difference of two large
+        // values of r.
+        float lev = 0.f;
         {
             float m = INF;
 #pragma unroll
             for (int s = 0; s < NPL; ++s)
                 if (up[s] > 0.f) m = fminf(m, cur[s]);
-            lev = gmin_f32<G>(m);
+            const float base = gmin_f32<G>(m);
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                r0[s] = (r0[s] == INF || base == INF) ? INF : r0[s] - base;
+                cur[s] = r0[s];
+            }
         }
         int guard = 0;
         const int guard_max = 4 * G * NPL + 8;
@@ -288,22 +780,17 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int j = s * G + gl;
-            if (active && j < len && cur[s] > r0[s]) {
-                const float x = cur[s] - r0[s];
-                const float old = atomicAdd(acc + id[s], x);
-                // TwoSum: exact rounding error of the sum the atomic stored
-                const float sum = old + x;
-                const float bp = sum - old;
-                const float e = (old - (sum - bp)) + (x - bp);
-                if (e != 0.f) atomicAdd(accc + id[s], e);
-            }
+            if (active && j < len && cur[s] > r0[s])
+                agg_add_f32(tbl, id[s], cur[s] - r0[s], acc, accc);
         }
     }
+    agg_flush_f32(tbl, acc, accc);
 }
 
 // r_t = r_{t-1} + delta (rule I); running max of r for the bound.
 template <class RT>
-__global__ void k_step_int(int64_t n, RT *r, RT *acc, unsigned long long *maxr) {
+__global__ void k_step_int(int64_t n, RT *r, RT *acc, unsigned long long *maxr, int *slow_count) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *slow_count = 0;  // next iteration's list
     unsigned long long m = 0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -323,9 +810,14 @@ __global__ void k_step_int(int64_t n, RT *r, RT *acc, unsigned long long *maxr) 
     if ((threadIdx.x & 31) == 0 && m) atomicMax(maxr, m);
 }
 
-// rhat_t = rhat_{t-1} + (s * a - rhat_{t-1}) / t with Kahan compensation.
-__global__ void k_step_f32(int64_t n, float *r, float *rc, float *a, float *ac, float sigma,
-                           float inv_t) {
+// rhat_t = rhat_{t-1} + (s * a - rhat_{t-1}) / t with Kahan compensation,
+// t = *t_done + 1; the last block to finish advances *t_done.
+__global__ void k_step_f32(int64_t n, float *r, float *rc, float *a, float *ac, int *t_done,
+                           unsigned int *blocks_done, int *slow_count) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *slow_count = 0;  // next iteration's list
+    const int t = *t_done + 1;
+    const float sigma = (float)(t - 1 > 1 ? t - 1 : 1);
+    const float inv_t = (float)(1.0 / (double)t);
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const float delta = sigma * (a[v] + ac[v]);
@@ -337,50 +829,79 @@ __global__ void k_step_f32(int64_t n, float *r, float *rc, float *a, float *ac, 
         a[v] = 0.f;
         ac[v] = 0.f;
     }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        *blocks_done = 0u;
+        *t_done = t;
+        __threadfence();
+    }
 }
 
+// One iteration's PBUpdate launches.  Pairs of at most 32 nodes (classes
+// 0-2, stored contiguously) take the fast first-step kernel, the pairs it
+// leaves take the group walk (8 lanes x 4 slots); longer pairs take the
+// 32-lane group walk directly.
 template <class RT>
-void launch_int_class(const Ctx &c, const SctDev &s, int cls, RT *r, RT *acc, int *err) {
-    const int64_t b = s.class_begin[cls], e = s.class_begin[cls + 1];
-    if (e <= b) return;
-    const int64_t np = e - b;
+void launch_pbupdate_int(const Ctx &c, const SctDev &s, RT *r, RT *acc, int32_t *slow,
+                         int *slow_count, int *err) {
     const int bc = s.k + 1;
-    auto go = [&](auto kern, int G) {
+    const int64_t b = s.class_begin[0], e = s.class_begin[3];
+    auto go = [&](auto kern, int G, int64_t pb, int64_t pe, const int32_t *list, const int *lc) {
         const int64_t groups_per_block = (FW_THREADS / 32) * (32 / G);
-        int grid = (int)std::min<int64_t>(ceil_div(np, groups_per_block), (int64_t)c.num_sms * 16);
-        kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, r, acc,
-                                                s.binom.p, bc, s.k, err);
+        int grid = (int)std::min<int64_t>(ceil_div(pe - pb, groups_per_block), (int64_t)c.num_sms * 4);
+        kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, pb, pe, r, acc,
+                                                s.binom.p, bc, s.k, list, lc, err);
         KDSS_LAUNCH_CHECK();
     };
-    switch (cls) {
-        case 0: go(k_pbupdate_int<8, 1, RT>, 8); break;
-        case 1: go(k_pbupdate_int<8, 2, RT>, 8); break;
-        case 2: go(k_pbupdate_int<8, 4, RT>, 8); break;
-        case 3: go(k_pbupdate_int<32, 8, RT>, 32); break;
-        default: go(k_pbupdate_int<32, 32, RT>, 32); break;
+    if (e > b) {
+        const int64_t tiles = ceil_div(e - b, 32);
+        int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
+        k_pb_fast<RT><<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, r,
+                                                            acc, s.binom.p, bc, s.k, slow, slow_count,
+                                                            err);
+        KDSS_LAUNCH_CHECK();
+        int sgrid = (int)std::min<int64_t>(ceil_div(e - b, SB_WARPS), (int64_t)c.num_sms * 8);
+        k_pb_slow<RT><<<sgrid, SB_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, r,
+                                                             acc, s.binom.p, bc, s.k, slow, slow_count,
+                                                             e - b, err);
+        KDSS_LAUNCH_CHECK();
     }
+    if (s.class_begin[4] > s.class_begin[3])
+        go(k_pbupdate_int<32, 8, RT>, 32, s.class_begin[3], s.class_begin[4], nullptr, nullptr);
+    if (s.class_begin[5] > s.class_begin[4])
+        go(k_pbupdate_int<32, 32, RT>, 32, s.class_begin[4], s.class_begin[5], nullptr, nullptr);
 }
 
-void launch_f32_class(const Ctx &c, const SctDev &s, int cls, StateDev &st, float inv_sigma) {
-    const int64_t b = s.class_begin[cls], e = s.class_begin[cls + 1];
-    if (e <= b) return;
-    const int64_t np = e - b;
+void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
     const int bc = s.k + 1;
-    auto go = [&](auto kern, int G) {
+    const int64_t b = s.class_begin[0], e = s.class_begin[3];
+    auto go = [&](auto kern, int G, int64_t pb, int64_t pe, const int32_t *list, const int *lc) {
         const int64_t groups_per_block = (FW_THREADS / 32) * (32 / G);
-        int grid = (int)std::min<int64_t>(ceil_div(np, groups_per_block), (int64_t)c.num_sms * 16);
-        kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, st.r32.p,
+        int grid = (int)std::min<int64_t>(ceil_div(pe - pb, groups_per_block), (int64_t)c.num_sms * 4);
+        kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, pb, pe, st.r32.p,
                                                 st.a32.p, st.a32c.p, s.binom.p, bc, s.k,
-                                                inv_sigma, st.err.p);
+                                                st.dev_t.p, list, lc, st.err.p);
         KDSS_LAUNCH_CHECK();
     };
-    switch (cls) {
-        case 0: go(k_pbupdate_f32<8, 1>, 8); break;
-        case 1: go(k_pbupdate_f32<8, 2>, 8); break;
-        case 2: go(k_pbupdate_f32<8, 4>, 8); break;
-        case 3: go(k_pbupdate_f32<32, 8>, 32); break;
-        default: go(k_pbupdate_f32<32, 32>, 32); break;
+    if (e > b) {
+        int grid = (int)std::min<int64_t>(ceil_div(e - b, FW_THREADS), (int64_t)c.num_sms * 8);
+        k_pb_fast_f32<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
+                                                         st.r32.p, st.a32.p, st.a32c.p, s.binom.p,
+                                                         bc, s.k, st.dev_t.p, st.ovf_list.p,
+                                                         st.ovf_count.p);
+        KDSS_LAUNCH_CHECK();
+        go(k_pbupdate_f32<8, 4>, 8, b, e, st.ovf_list.p, st.ovf_count.p);
     }
+    if (s.class_begin[4] > s.class_begin[3])
+        go(k_pbupdate_f32<32, 8>, 32, s.class_begin[3], s.class_begin[4], nullptr, nullptr);
+    if (s.class_begin[5] > s.class_begin[4])
+        go(k_pbupdate_f32<32, 32>, 32, s.class_begin[4], s.class_begin[5], nullptr, nullptr);
 }
 
 struct EventPair {
@@ -412,13 +933,95 @@ void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st) {
     }
     st.maxr = DBuf<unsigned long long>(c, 1);
     st.err = DBuf<int>(c, 1);
+    st.dev_t = DBuf<int>(c, 2);  // [0] iterations done, [1] blocks-done counter
+    zero(c, st.dev_t.p, 2 * sizeof(int));
+    const int64_t short_pairs = std::max<int64_t>(1, s.class_begin[3] - s.class_begin[0]);
+    st.ovf_list = DBuf<int32_t>(c, (size_t)short_pairs);
+    st.ovf_count = DBuf<int>(c, 1);
+    zero(c, st.ovf_count.p, sizeof(int));
     zero(c, st.maxr.p, 8);
     zero(c, st.err.p, 4);
 }
 
+namespace {
+
+void enqueue_pbupdate(const Ctx &c, const SctDev &s, StateDev &st) {
+    if (st.precision == KDSS_FP32K) {
+        launch_pbupdate_f32(c, s, st);
+    } else if (st.precision == KDSS_FP64) {
+        launch_pbupdate_int<double>(c, s, (double *)st.r.p, (double *)st.acc.p, st.ovf_list.p,
+                                    st.ovf_count.p, st.err.p);
+    } else {
+        launch_pbupdate_int<uint64_t>(c, s, st.r.p, st.acc.p, st.ovf_list.p, st.ovf_count.p,
+                                      st.err.p);
+    }
+}
+
+void enqueue_step(const Ctx &c, const SctDev &s, StateDev &st) {
+    const int64_t n = s.n;
+    if (n <= 0) return;
+    const int B = 256;
+    const int sgrid = grid_for(c, n, B, 4);
+    if (st.precision == KDSS_FP32K) {
+        k_step_f32<<<sgrid, B, 0, c.stream>>>(n, st.r32.p, st.r32c.p, st.a32.p, st.a32c.p,
+                                             st.dev_t.p, (unsigned int *)(st.dev_t.p + 1),
+                                             st.ovf_count.p);
+    } else if (st.precision == KDSS_FP64) {
+        k_step_int<double><<<sgrid, B, 0, c.stream>>>(n, (double *)st.r.p, (double *)st.acc.p,
+                                                      st.maxr.p, st.ovf_count.p);
+    } else {
+        k_step_int<uint64_t><<<sgrid, B, 0, c.stream>>>(n, st.r.p, st.acc.p, st.maxr.p,
+                                                        st.ovf_count.p);
+    }
+    KDSS_LAUNCH_CHECK();
+}
+
+// Capture `fn` on a private stream into an executable graph; returns the
+// number of kernels it holds.
+template <class F>
+long long capture(const Ctx &c, cudaGraphExec_t *exec, F fn) {
+    cudaStream_t cap = nullptr;
+    KDSS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    Ctx cc = c;
+    cc.stream = cap;
+    const long long before = launches();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        try {
+            fn(cc);
+        } catch (...) {
+            cudaStreamEndCapture(cap, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            throw;
+        }
+        e = cudaStreamEndCapture(cap, &g);
+    }
+    const long long nk = launches() - before;
+    add_launches(-nk);  // captured, not run
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    check_cuda(e, "FW graph capture", __FILE__, __LINE__);
+    return nk;
+}
+
+}  // namespace
+
+StateDev::~StateDev() {
+    release_graphs();
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+void StateDev::release_graphs() {
+    for (cudaGraphExec_t *g : {&g_iter, &g_pb, &g_step})
+        if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
+    graph_sct = nullptr;
+}
+
 void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
     if (T <= 0) return;
-    const int64_t n = s.n;
     // exactness of the cumulative r: r_t(u) <= t * c_k
     if (st.precision != KDSS_FP32K) {
         const long double lim = st.precision == KDSS_INT64 ? 9.2e18L : 9.007199254740992e15L;
@@ -426,59 +1029,52 @@ void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
         if ((long double)(st.t + T) * ck >= lim)
             fail(KDSS_ERR_OVERFLOW, "T * c_k leaves the exact range of r");
     }
-    std::vector<EventPair> ev;
-    if (profile) ev.resize((size_t)T * 2);
-    auto rec = [&](cudaEvent_t &e) {
-        KDSS_CUDA(cudaEventCreate(&e));
-        KDSS_CUDA(cudaEventRecord(e, c.stream));
-    };
-    const int B = 256;
-    const int sgrid = grid_for(c, n, B, 4);
-    for (int it = 0; it < T; ++it) {
-        const int t = st.t + 1;  // iteration number, 1-based
-        if (profile) rec(ev[2 * it].a);
-        if (st.precision == KDSS_FP32K) {
-            const float inv_sigma = (float)(1.0 / (double)std::max(t - 1, 1));
-            for (int cl = 0; cl < NCLASS; ++cl) launch_f32_class(c, s, cl, st, inv_sigma);
-        } else if (st.precision == KDSS_FP64) {
-            for (int cl = 0; cl < NCLASS; ++cl)
-                launch_int_class<double>(c, s, cl, (double *)st.r.p, (double *)st.acc.p, st.err.p);
-        } else {
-            for (int cl = 0; cl < NCLASS; ++cl)
-                launch_int_class<uint64_t>(c, s, cl, st.r.p, st.acc.p, st.err.p);
-        }
-        if (profile) { rec(ev[2 * it].b); rec(ev[2 * it + 1].a); }
-        if (n > 0) {
-            if (st.precision == KDSS_FP32K) {
-                const double sigma = (double)std::max(t - 1, 1);
-                k_step_f32<<<sgrid, B, 0, c.stream>>>(n, st.r32.p, st.r32c.p, st.a32.p, st.a32c.p,
-                                                     (float)sigma, (float)(1.0 / (double)t));
-            } else if (st.precision == KDSS_FP64) {
-                k_step_int<double><<<sgrid, B, 0, c.stream>>>(n, (double *)st.r.p, (double *)st.acc.p,
-                                                              st.maxr.p);
-            } else {
-                k_step_int<uint64_t><<<sgrid, B, 0, c.stream>>>(n, st.r.p, st.acc.p, st.maxr.p);
-            }
-            KDSS_LAUNCH_CHECK();
-        }
-        if (profile) rec(ev[2 * it + 1].b);
-        st.t = t;
+    // One iteration as CUDA graphs (PBUpdate, step, and both), captured once
+    // per (state, SCT) and replayed T times on the caller's stream.
+    if (st.graph_sct != &s) {
+        st.release_graphs();
+        st.nk_pb = capture(c, &st.g_pb, [&](const Ctx &cc) { enqueue_pbupdate(cc, s, st); });
+        st.nk_step = capture(c, &st.g_step, [&](const Ctx &cc) { enqueue_step(cc, s, st); });
+        capture(c, &st.g_iter, [&](const Ctx &cc) {
+            enqueue_pbupdate(cc, s, st);
+            enqueue_step(cc, s, st);
+        });
+        st.graph_sct = &s;
     }
+    // event pool kept in the state (creating events per call costs host time)
+    if (profile) {
+        while (st.events.size() < (size_t)T * 4) {
+            cudaEvent_t e;
+            KDSS_CUDA(cudaEventCreate(&e));
+            st.events.push_back(e);
+        }
+    }
+    std::vector<cudaEvent_t> &ev = st.events;
+    for (int it = 0; it < T; ++it) {
+        if (profile) {
+            KDSS_CUDA(cudaEventRecord(ev[4 * it], c.stream));
+            KDSS_CUDA(cudaGraphLaunch(st.g_pb, c.stream));
+            KDSS_CUDA(cudaEventRecord(ev[4 * it + 1], c.stream));
+            KDSS_CUDA(cudaEventRecord(ev[4 * it + 2], c.stream));
+            KDSS_CUDA(cudaGraphLaunch(st.g_step, c.stream));
+            KDSS_CUDA(cudaEventRecord(ev[4 * it + 3], c.stream));
+        } else {
+            KDSS_CUDA(cudaGraphLaunch(st.g_iter, c.stream));
+        }
+        add_launches(st.nk_pb + st.nk_step);
+    }
+    st.t += T;
     int herr = 0;
     to_host(c, &herr, st.err.p, 1);
     if (profile) {
         for (int it = 0; it < T; ++it) {
             float a = 0.f, b2 = 0.f;
-            KDSS_CUDA(cudaEventElapsedTime(&a, ev[2 * it].a, ev[2 * it].b));
-            KDSS_CUDA(cudaEventElapsedTime(&b2, ev[2 * it + 1].a, ev[2 * it + 1].b));
+            KDSS_CUDA(cudaEventElapsedTime(&a, ev[4 * it], ev[4 * it + 1]));
+            KDSS_CUDA(cudaEventElapsedTime(&b2, ev[4 * it + 2], ev[4 * it + 3]));
             st.timing.fw_kernel_ms += a;
             st.timing.step_kernel_ms += b2;
             st.timing.fw_launches += 1;
             st.timing.step_launches += 1;
-        }
-        for (auto &e : ev) {
-            cudaEventDestroy(e.a);
-            cudaEventDestroy(e.b);
         }
     }
     if (herr) fail(KDSS_ERR_CUDA, "FW iteration: water-filling invariant failed on the device");

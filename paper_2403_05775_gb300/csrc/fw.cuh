@@ -17,8 +17,21 @@ struct StateDev {
     DBuf<float> a32c;                // [n] FP32K: error terms of the allocation sum
     DBuf<unsigned long long> maxr;   // [1] max r (uint64 / double bits / float bits)
     DBuf<int> err;                   // [1] device error word
+    DBuf<int32_t> ovf_list;          // pairs of <= 32 nodes left to the full walk
+    DBuf<int> ovf_count;             // their number (reset by the step kernel)
+    DBuf<int> dev_t;                 // [0] iterations done (FP32 schedule), [1] scratch
     kdss_timing timing{};
     Ctx ctx;
+    // one FW iteration as CUDA graphs, bound to the SCT they were captured for
+    const SctDev *graph_sct = nullptr;
+    cudaGraphExec_t g_iter = nullptr, g_pb = nullptr, g_step = nullptr;
+    long long nk_pb = 0, nk_step = 0;
+    std::vector<cudaEvent_t> events;  // timing events (KDSS_FLAG_PROFILE)
+    StateDev() = default;
+    StateDev(const StateDev &) = delete;
+    StateDev &operator=(const StateDev &) = delete;
+    ~StateDev();
+    void release_graphs();
 };
 
 void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st);

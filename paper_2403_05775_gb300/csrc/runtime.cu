@@ -10,6 +10,7 @@ namespace kdss {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 
 void fail(kdss_status code, const std::string &msg) { throw Error{code, msg}; }
 
@@ -36,6 +37,22 @@ Ctx make_ctx(const kdss_opts *o) {
     }
     KDSS_CUDA(cudaGetDevice(&c.device));
     KDSS_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+    if (!c.alloc) {
+        // Without a caller allocator the library draws from the device's
+        // stream-ordered pool; let the pool keep freed memory for reuse
+        // instead of returning it at every synchronisation (a setting of this
+        // process's pool only).
+        static thread_local int tuned_device = -1;
+        if (tuned_device != c.device) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess) {
+                uint64_t keep = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+            cudaGetLastError();
+            tuned_device = c.device;
+        }
+    }
     return c;
 }
 

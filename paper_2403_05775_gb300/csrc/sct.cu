@@ -60,26 +60,41 @@ __device__ __forceinline__ int dev_class(int len) {
     return len <= 8 ? 0 : len <= 16 ? 1 : len <= 32 ? 2 : len <= 256 ? 3 : len <= 1024 ? 4 : -1;
 }
 
-struct CountOut {
-    int64_t *cntP;   // [NCLASS * n], class-major
-    int64_t *cntN;
-    unsigned long long *ck;  // [2] lo, hi
-    int *maxlen;
+// A work item is a node of the recursion: level 0 items are the roots; a
+// hold branch whose candidate set has at least SPLIT_MIN vertices (and whose
+// hold set can still grow) becomes an item of the next level instead of being
+// walked inline, so that dense regions are spread over many warps.
+// Record of a spawned item (uint32 words): root, |hold|, hold[0..k) (local
+// indices; the root is -1), candidate bitset [S], pivot bitset [S].
+constexpr int SPLIT_MIN = 16;
+enum { MODE_COUNT = 0, MODE_SPAWN = 1, MODE_EMIT = 2 };
+
+struct ItemsIn {
+    int64_t nitems;
+    const uint32_t *rec;     // nullptr: the items are the roots 0..n-1
+    int stride;              // words per record
 };
-struct EmitOut {
-    const int64_t *baseP;    // [NCLASS * n]
+struct PassOut {
+    int64_t *cntP;           // [NCLASS * nitems] class-major (COUNT)
+    int64_t *cntN;
+    int64_t *nspawn;         // [nitems] (COUNT)
+    unsigned long long *ck;  // [2] lo, hi (COUNT)
+    int *maxlen;             // (COUNT)
+    const int64_t *spawn_off;  // [nitems] (SPAWN)
+    uint32_t *spawn_rec;       // (SPAWN)
+    const int64_t *baseP;    // [NCLASS * nitems] output offsets (EMIT)
     const int64_t *baseN;
     int64_t *pair_off;
     int32_t *nodes;
     uint8_t *h;
 };
 
-template <bool EMIT>
+template <int MODE>
 __global__ void __launch_bounds__(SCT_THREADS)
 k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_adj,
       const int32_t *__restrict__ vert, int k, int dmax, int S,
       const uint64_t *__restrict__ binom, int bcols, uint32_t *gws, int use_shared,
-      unsigned long long *next_root, CountOut co, EmitOut eo, int *err) {
+      unsigned long long *next_item, ItemsIn items, PassOut po, int *err) {
     extern __shared__ uint32_t smem[];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -98,16 +113,19 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
     int32_t *fnp = fnh + F;
     int32_t *fph = fnp + F;
     int32_t *ids = fph + F;
+    const int64_t NI = items.nitems;
 
     while (true) {
         unsigned long long rr = 0;
-        if (lane == 0) rr = atomicAdd(next_root, 1ull);
+        if (lane == 0) rr = atomicAdd(next_item, 1ull);
         rr = __shfl_sync(FULL, rr, 0);
-        if (rr >= (unsigned long long)n) break;
-        const int64_t root = (int64_t)rr;
+        if (rr >= (unsigned long long)NI) break;
+        const int64_t item = (int64_t)rr;
+        const uint32_t *rec = items.rec ? items.rec + (size_t)item * items.stride : nullptr;
+        const int64_t root = rec ? (int64_t)rec[0] : item;
         const int64_t o0 = out_off[root];
         const int d = (int)(out_off[root + 1] - o0);
-        if (d + 1 < k) continue;
+        if (!rec && d + 1 < k) continue;
         const int W = (d + 31) >> 5;
 
         // local vertex list and its adjacency bitsets
@@ -130,21 +148,39 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 }
             }
         }
-        // per-root outputs (lane 0)
+        // per-item outputs (lane 0)
         int64_t cP[NCLASS], cN[NCLASS];
 #pragma unroll
         for (int c = 0; c < NCLASS; ++c) {
-            cP[c] = EMIT ? eo.baseP[(int64_t)c * n + root] : 0;
-            cN[c] = EMIT ? eo.baseN[(int64_t)c * n + root] : 0;
+            cP[c] = MODE == MODE_EMIT ? po.baseP[(int64_t)c * NI + item] : 0;
+            cN[c] = MODE == MODE_EMIT ? po.baseN[(int64_t)c * NI + item] : 0;
         }
+        int64_t nsp = MODE == MODE_SPAWN ? po.spawn_off[item] : 0;
         unsigned long long ck_lo = 0, ck_hi = 0;
         int mlen = 0;
 
-        if (lane < W) {
-            int rem = d - lane * 32;
-            cand[lane] = rem >= 32 ? FULL : ((1u << rem) - 1u);
+        // initial frame: the root, or the spawned recursion node
+        if (!rec) {
+            if (lane < W) {
+                int rem = d - lane * 32;
+                cand[lane] = rem >= 32 ? FULL : ((1u << rem) - 1u);
+            }
+            if (lane == 0) { fnh[0] = 1; fnp[0] = 0; fph[0] = 0; hold[0] = -1; }
+        } else {
+            const int nh0 = (int)rec[1];
+            const uint32_t *rc = rec + 2 + k;
+            const uint32_t *rp = rc + S;
+            if (lane < W) cand[lane] = rc[lane];
+            if (lane == 0) {
+                for (int t = 0; t < nh0; ++t) hold[t] = (int32_t)rec[2 + t];
+                int np0 = 0;
+                for (int w = 0; w < W; ++w) {
+                    uint32_t b = rp[w];
+                    while (b) { piv[np0++] = w * 32 + __ffs(b) - 1; b &= b - 1; }
+                }
+                fnh[0] = nh0; fnp[0] = np0; fph[0] = 0;
+            }
         }
-        if (lane == 0) { fnh[0] = 1; fnp[0] = 0; fph[0] = 0; hold[0] = -1; }
         __syncwarp();
         int depth = 0;
         while (depth >= 0) {
@@ -162,7 +198,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                         const uint64_t nC = binom[(size_t)p * bcols + (k - h)];
                         if (cls < 0 || nC == ~0ull) {
                             if (lane == 0) atomicOr(err, cls < 0 ? DERR_CAPACITY : DERR_OVERFLOW);
-                        } else if (!EMIT) {
+                        } else if (MODE == MODE_COUNT) {
                             if (lane == 0) {
                                 cP[cls] += 1;
                                 cN[cls] += len;
@@ -171,7 +207,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                                 ck_hi += ck_lo < o ? 1ull : 0ull;
                                 mlen = len > mlen ? len : mlen;
                             }
-                        } else {
+                        } else if (MODE == MODE_EMIT) {
                             int64_t pidx = 0, noff = 0;
                             if (lane == 0) {
                                 pidx = cP[cls]++;
@@ -199,11 +235,11 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                                 const int32_t my = raw & 0x7fffffff;
                                 int pos = 0;
                                 for (int u = 0; u < len; ++u) pos += ((ids[u] & 0x7fffffff) < my) ? 1 : 0;
-                                eo.nodes[noff + pos] = raw;
+                                po.nodes[noff + pos] = raw;
                             }
                             if (lane == 0) {
-                                eo.pair_off[pidx] = noff;
-                                eo.h[pidx] = (uint8_t)h;
+                                po.pair_off[pidx] = noff;
+                                po.h[pidx] = (uint8_t)h;
                             }
                             __syncwarp();
                         }
@@ -260,14 +296,42 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                     break;
                 }
                 const uint32_t *aw = A + (size_t)w * S;
+                uint32_t child = 0u;
                 if (lane < W) {
                     const uint32_t cw = cd[lane];
-                    cand[(size_t)(depth + 1) * S + lane] = cw & aw[lane];
+                    child = cw & aw[lane];
                     if (lane == src) {
                         td[lane] = tw & ~(1u << (w & 31));
                         cd[lane] = cw & ~(1u << (w & 31));
                     }
                 }
+                const int ncc = (int)__reduce_add_sync(FULL, (unsigned)__popc(child));
+                // big hold branch: becomes an item of the next level
+                if (h + 1 < k && ncc >= SPLIT_MIN && h + 1 + p + ncc >= k) {
+                    if (MODE == MODE_COUNT) {
+                        nsp += 1;
+                    } else if (MODE == MODE_SPAWN) {
+                        uint32_t *r2 = po.spawn_rec + (size_t)nsp * (2 + k + 2 * S);
+                        if (lane == 0) {
+                            r2[0] = (uint32_t)root;
+                            r2[1] = (uint32_t)(h + 1);
+                            for (int t = 0; t < h; ++t) r2[2 + t] = (uint32_t)hold[t];
+                            r2[2 + h] = (uint32_t)w;
+                            for (int t = h + 1; t < k; ++t) r2[2 + t] = 0u;
+                        }
+                        if (lane < S) {
+                            r2[2 + k + lane] = lane < W ? child : 0u;
+                            uint32_t pw = 0u;
+                            for (int t = 0; t < p; ++t)
+                                if ((piv[t] >> 5) == lane) pw |= 1u << (piv[t] & 31);
+                            r2[2 + k + S + lane] = pw;
+                        }
+                        nsp += 1;
+                    }
+                    __syncwarp();
+                    continue;  // stay at this depth: next hold branch
+                }
+                if (lane < W) cand[(size_t)(depth + 1) * S + lane] = child;
                 if (lane == 0) {
                     hold[h] = w;
                     fnh[depth + 1] = h + 1;
@@ -278,18 +342,19 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 ++depth;
             }
         }
-        if (!EMIT && lane == 0) {
+        if (MODE == MODE_COUNT && lane == 0) {
 #pragma unroll
             for (int c = 0; c < NCLASS; ++c) {
-                co.cntP[(int64_t)c * n + root] = cP[c];
-                co.cntN[(int64_t)c * n + root] = cN[c];
+                po.cntP[(int64_t)c * NI + item] = cP[c];
+                po.cntN[(int64_t)c * NI + item] = cN[c];
             }
+            po.nspawn[item] = nsp;
             if (ck_lo || ck_hi) {
-                unsigned long long old = atomicAdd(&co.ck[0], ck_lo);
+                unsigned long long old = atomicAdd(&po.ck[0], ck_lo);
                 unsigned long long carry = (old + ck_lo < old) ? 1ull : 0ull;
-                if (ck_hi + carry) atomicAdd(&co.ck[1], ck_hi + carry);
+                if (ck_hi + carry) atomicAdd(&po.ck[1], ck_hi + carry);
             }
-            atomicMax(co.maxlen, mlen);
+            atomicMax(po.maxlen, mlen);
         }
         __syncwarp();
     }
@@ -385,6 +450,7 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
     const int S = (dmax + 31) / 32;
     upload_binom(c, dmax + 2, k, out);
     const int bcols = k + 1;
+    const int stride = 2 + k + 2 * S;
 
     const size_t ww = ws_words(dmax, S);
     const size_t smem = ww * sizeof(uint32_t) * SCT_WARPS;
@@ -392,12 +458,12 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
     int grid;
     DBuf<uint32_t> gws;
     if (use_shared) {
-        KDSS_CUDA(cudaFuncSetAttribute(k_sct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        KDSS_CUDA(cudaFuncSetAttribute(k_sct<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_SPAWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sct<false>, SCT_THREADS, smem));
-        per_sm = std::max(1, per_sm);
-        grid = (int)std::min<int64_t>((int64_t)c.num_sms * per_sm, std::max<int64_t>(1, ceil_div(n, SCT_WARPS)));
+        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sct<MODE_COUNT>, SCT_THREADS, smem));
+        grid = c.num_sms * std::max(1, per_sm);
     } else {
         // global workspace: bound its size to about 1 GiB
         int64_t warps = std::max<int64_t>(SCT_WARPS, (int64_t)(1ull << 28) / (int64_t)ww);
@@ -407,24 +473,81 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
     }
     const size_t dyn = use_shared ? smem : 0;
 
-    DBuf<int64_t> cntP(c, (size_t)(NCLASS * n)), cntN(c, (size_t)(NCLASS * n));
-    zero(c, cntP.p, cntP.bytes());  // roots without pairs write nothing
-    zero(c, cntN.p, cntN.bytes());
-    DBuf<unsigned long long> ctr(c, 4);  // [0] next root, [1..2] c_k
+    DBuf<unsigned long long> ctr(c, 4);  // [0] next item, [1..2] c_k
     DBuf<int> ints(c, 2);                // [0] max len, [1] error
     zero(c, ctr.p, 4 * sizeof(unsigned long long));
     zero(c, ints.p, 2 * sizeof(int));
-    CountOut co{cntP.p, cntN.p, ctr.p + 1, ints.p};
-    EmitOut eo{nullptr, nullptr, nullptr, nullptr, nullptr};
-    if (n > 0) {
-        k_sct<false><<<grid, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k,
-                                                          dmax, S, out.binom.p, bcols, gws.p,
-                                                          use_shared, ctr.p, co, eo, ints.p + 1);
+
+    struct Level {
+        int64_t nitems = 0;
+        DBuf<uint32_t> rec;        // records (empty for the roots)
+        DBuf<int64_t> cntP, cntN;  // [NCLASS * nitems]
+    };
+    std::vector<Level> levels;
+    auto launch = [&](auto kern, const Level &L, const PassOut &po) {
+        zero(c, ctr.p, sizeof(unsigned long long));
+        int gsz = (int)std::min<int64_t>(grid, std::max<int64_t>(1, ceil_div(L.nitems, SCT_WARPS)));
+        ItemsIn in{L.nitems, L.rec.p, stride};
+        kern<<<gsz, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k, dmax,
+                                                 S, out.binom.p, bcols, gws.p, use_shared,
+                                                 ctr.p, in, po, ints.p + 1);
         KDSS_LAUNCH_CHECK();
+    };
+    // count and spawn, level by level; a spawned item has a larger hold set,
+    // so there are at most k levels
+    levels.reserve((size_t)k + 2);
+    levels.emplace_back();
+    levels[0].nitems = n;
+    for (size_t lv = 0; lv < levels.size(); ++lv) {
+        if (lv > (size_t)k) fail(KDSS_ERR_CUDA, "SCT build: more item levels than k");
+        Level &L = levels[lv];
+        if (L.nitems == 0) break;
+        L.cntP = DBuf<int64_t>(c, (size_t)(NCLASS * L.nitems));
+        L.cntN = DBuf<int64_t>(c, (size_t)(NCLASS * L.nitems));
+        zero(c, L.cntP.p, L.cntP.bytes());  // items without pairs write nothing
+        zero(c, L.cntN.p, L.cntN.bytes());
+        DBuf<int64_t> nspawn(c, (size_t)L.nitems), spoff(c, (size_t)L.nitems);
+        zero(c, nspawn.p, nspawn.bytes());
+        PassOut po{};
+        po.cntP = L.cntP.p; po.cntN = L.cntN.p; po.nspawn = nspawn.p;
+        po.ck = ctr.p + 1; po.maxlen = ints.p;
+        launch(k_sct<MODE_COUNT>, L, po);
+        const int64_t ns = exclusive_scan_i64(c, nspawn.p, spoff.p, L.nitems);
+        if (ns == 0) break;
+        DBuf<uint32_t> rec(c, (size_t)ns * stride);
+        PassOut ps{};
+        ps.spawn_off = spoff.p;
+        ps.spawn_rec = rec.p;
+        launch(k_sct<MODE_SPAWN>, L, ps);
+        levels.emplace_back();  // no reference into `levels` is used after this
+        levels.back().nitems = ns;
+        levels.back().rec = std::move(rec);
     }
-    DBuf<int64_t> baseP(c, (size_t)(NCLASS * n)), baseN(c, (size_t)(NCLASS * n));
-    int64_t npairs = exclusive_scan_i64(c, cntP.p, baseP.p, NCLASS * n);
-    int64_t nnodes = exclusive_scan_i64(c, cntN.p, baseN.p, NCLASS * n);
+    // output offsets: class-major over all items of all levels
+    int64_t total = 0;
+    for (auto &L : levels) {
+        if (L.nitems > 0 && !L.cntP.p) fail(KDSS_ERR_CUDA, "SCT build: a level was not counted");
+        total += L.nitems;
+    }
+    DBuf<int64_t> allP(c, (size_t)(NCLASS * std::max<int64_t>(total, 1)));
+    DBuf<int64_t> allN(c, (size_t)(NCLASS * std::max<int64_t>(total, 1)));
+    {
+        int64_t b = 0;
+        for (auto &L : levels) {
+            if (!L.cntP.p) continue;
+            for (int cl = 0; cl < NCLASS; ++cl) {
+                KDSS_CUDA(cudaMemcpyAsync(allP.p + cl * total + b, L.cntP.p + cl * L.nitems,
+                                          L.nitems * 8, cudaMemcpyDeviceToDevice, c.stream));
+                KDSS_CUDA(cudaMemcpyAsync(allN.p + cl * total + b, L.cntN.p + cl * L.nitems,
+                                          L.nitems * 8, cudaMemcpyDeviceToDevice, c.stream));
+            }
+            b += L.nitems;
+        }
+    }
+    DBuf<int64_t> baseP(c, (size_t)(NCLASS * std::max<int64_t>(total, 1)));
+    DBuf<int64_t> baseN(c, (size_t)(NCLASS * std::max<int64_t>(total, 1)));
+    const int64_t npairs = exclusive_scan_i64(c, allP.p, baseP.p, NCLASS * total);
+    const int64_t nnodes = exclusive_scan_i64(c, allN.p, baseN.p, NCLASS * total);
     unsigned long long hc[4];
     int hi[2];
     to_host(c, hc, ctr.p, 4);
@@ -439,22 +562,33 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
     out.nnodes = nnodes;
     for (int cl = 0; cl < NCLASS; ++cl) {
         int64_t v = 0;
-        if (n > 0) to_host(c, &v, baseP.p + (int64_t)cl * n, 1);
+        if (total > 0) to_host(c, &v, baseP.p + (int64_t)cl * total, 1);
         out.class_begin[cl] = v;
     }
     out.class_begin[NCLASS] = npairs;
-    cntP.reset();
-    cntN.reset();
+    allP.reset();
+    allN.reset();
     out.pair_off = DBuf<int64_t>(c, (size_t)(npairs + 1));
     out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1));
     out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(npairs, 1));
     if (npairs > 0) {
-        zero(c, ctr.p, sizeof(unsigned long long));
-        EmitOut eo2{baseP.p, baseN.p, out.pair_off.p, out.nodes.p, out.h.p};
-        k_sct<true><<<grid, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k,
-                                                         dmax, S, out.binom.p, bcols, gws.p,
-                                                         use_shared, ctr.p, co, eo2, ints.p + 1);
-        KDSS_LAUNCH_CHECK();
+        // per-level slices of the class-major offsets
+        int64_t b = 0;
+        for (auto &L : levels) {
+            if (!L.cntP.p) continue;
+            DBuf<int64_t> lp(c, (size_t)(NCLASS * L.nitems)), ln(c, (size_t)(NCLASS * L.nitems));
+            for (int cl = 0; cl < NCLASS; ++cl) {
+                KDSS_CUDA(cudaMemcpyAsync(lp.p + cl * L.nitems, baseP.p + cl * total + b,
+                                          L.nitems * 8, cudaMemcpyDeviceToDevice, c.stream));
+                KDSS_CUDA(cudaMemcpyAsync(ln.p + cl * L.nitems, baseN.p + cl * total + b,
+                                          L.nitems * 8, cudaMemcpyDeviceToDevice, c.stream));
+            }
+            PassOut pe{};
+            pe.baseP = lp.p; pe.baseN = ln.p;
+            pe.pair_off = out.pair_off.p; pe.nodes = out.nodes.p; pe.h = out.h.p;
+            launch(k_sct<MODE_EMIT>, L, pe);
+            b += L.nitems;
+        }
     }
     to_device(c, out.pair_off.p + npairs, &nnodes, 1);
     to_host(c, hi, ints.p, 2);

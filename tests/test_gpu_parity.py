@@ -158,6 +158,49 @@ def test_fw_every_length_class_is_bit_exact(maxlen):
     assert res["ids"].tolist() == want["ids"].tolist()
 
 
+def test_fw_large_counts_are_bit_exact():
+    """Pairs of 24-32 nodes sharing a hub with k = 14: per-pair counts up to
+    C(31, 13) ~ 2e8 push r beyond 2^32 within the run (64-bit arithmetic in
+    the fast first step and in the full walk)."""
+    rng = np.random.default_rng(21)
+    n, k, T = 400, 14, 20
+    po, nodes, hs = [0], [], []
+    for _ in range(2500):
+        ln = int(rng.integers(24, 33))
+        ids = [0] + rng.choice(np.arange(1, n), size=ln - 1, replace=False).tolist()
+        h = int(rng.integers(1, 4))
+        nodes.extend(ids)
+        hs.append(h)
+        po.append(len(nodes))
+    sc = dict(pair_off=np.array(po, np.int64), nodes=np.array(nodes, np.int32),
+              h=np.array(hs, np.int32))
+    sct = K.kdss_sct_from_pairs(n, k, sc["pair_off"], sc["nodes"], sc["h"])
+    want = O.fw_sync(n, sc, k, T)
+    assert int(want.max()) > (1 << 32)
+    for prec in (K.KDSS_INT64, K.KDSS_FP64):
+        st = K.kdss_fw_iterate(sct, None, T, K.make_opts(precision=prec))
+        r, _ = K.kdss_state_copy_r(st, n, prec)
+        assert np.array_equal(r.astype(np.uint64), want)
+
+
+def test_profiled_and_graph_runs_agree():
+    """The profiled path (separate graphs with events) and the plain path
+    (one graph per iteration) give the same r, for every precision."""
+    n, s, d = GRAPHS["rmat2k"]()
+    sct = K.kdss_build_sct(n, s, d, 4)
+    for prec in (K.KDSS_INT64, K.KDSS_FP64, K.KDSS_FP32K):
+        a = K.kdss_fw_iterate(sct, None, 30, K.make_opts(precision=prec, flags=K.KDSS_FLAG_PROFILE))
+        b = K.kdss_fw_iterate(sct, None, 30, K.make_opts(precision=prec))
+        ra, _ = K.kdss_state_copy_r(a, n, prec)
+        rb, _ = K.kdss_state_copy_r(b, n, prec)
+        if prec == K.KDSS_FP32K:
+            assert np.max(np.abs(ra - rb)) <= FP32_RTOL * np.max(np.abs(rb))
+        else:
+            assert np.array_equal(ra, rb)
+        tm = K.kdss_state_timing(a)
+        assert tm["fw_launches"] == 30 and tm["fw_kernel_ms"] > 0
+
+
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 @pytest.mark.parametrize("k", [3, 5])
 def test_whole_path_matches_oracle(name, k):
