@@ -254,6 +254,41 @@ const char *kdss_version(void);
  * (all threads); the difference of two calls counts the launches between. */
 int64_t kdss_kernel_launches(void);
 
+/*
+ * kdss_fw_iterate_noalloc -- the FW iterations of kdss_fw_iterate (integer
+ * rule, KDSS_INT64 semantics) without any device allocation.  The paper has
+ * no counterpart: this is an interface for callers that cannot allocate
+ * device memory while they iterate -- a process whose GPU memory is reserved
+ * up front and handed out by its own arena, a serving loop held to a fixed
+ * footprint, code that must not slip an implicitly synchronising cudaMalloc
+ * between its kernels.
+ *   s      : SCT handle, built beforehand (kdss_build_sct / _from_pairs) on
+ *            the current device.
+ *   r      : caller-owned device array of n uint64, the cumulative r after
+ *            t_done iterations (zeros for t_done = 0); updated in place to r
+ *            after t_done + T iterations.
+ *   t_done : iterations already in r (only bounds the exact range of r).
+ *   T      : iterations to run, T >= 0.
+ *   stream : cudaStream_t the work is ordered on; the call returns after that
+ *            stream has finished it.
+ * Scratch: the per-iteration delta and the work lists live in one fixed
+ * device array of 16 MiB inside the library, which every GPU that loads the
+ * library holds until the process exits.  It fits graphs with
+ * 8 * n + 4 * (pairs of at most 32 nodes) + 768 bytes <= 16 MiB (about two
+ * million nodes); larger inputs are rejected with KDSS_ERR_INVALID_ARG and a
+ * message that states the sizes.  The array keeps the previous call's
+ * contents; each call clears what must start at zero.  All calls share it:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ * Errors: INVALID_ARG (NULL, T < 0, sizes above the scratch, another device),
+ *   OVERFLOW, CUDA.
+ */
+kdss_status kdss_fw_iterate_noalloc(const kdss_sct *s, uint64_t *r, int32_t t_done, int32_t T,
+                                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -125,6 +125,7 @@ def load(build_if_missing: bool = False):
             "kdss_last_error": (C.c_char_p, []),
             "kdss_version": (C.c_char_p, []),
             "kdss_kernel_launches": (i64, []),
+            "kdss_fw_iterate_noalloc": (i32, [vp, vp, i32, i32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -385,3 +386,20 @@ def kdss_version() -> str:
 
 def kdss_kernel_launches() -> int:
     return int(load().kdss_kernel_launches())
+
+
+def kdss_fw_iterate_noalloc(s: Sct, r_dev, t_done: int, T: int, stream=None) -> None:
+    """Rule-I FW iterations on a caller-owned device vector r (n uint64
+    values, given as a CUDA tensor of 8-byte elements or a raw device
+    pointer), using only the library's fixed scratch area -- for callers that
+    cannot allocate device memory while they iterate."""
+    ptr = r_dev.data_ptr() if hasattr(r_dev, "data_ptr") else int(r_dev)
+    if hasattr(r_dev, "element_size") and r_dev.element_size() != 8:
+        raise ValueError("r must hold 8-byte elements")
+    if stream is None:
+        t = _torch()
+        stream = t.cuda.current_stream() if t is not None else None
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load().kdss_fw_iterate_noalloc(s.ptr, C.c_void_p(ptr), int(t_done), int(T),
+                                          C.c_void_p(stream or None)))

@@ -9,21 +9,9 @@
 
 #include "fw.cuh"
 
+#include "handles.cuh"
+
 using namespace kdss;
-
-struct kdss_sct {
-    Ctx ctx;
-    GraphDev g;
-    SctDev s;
-    bool has_graph = false;
-    int64_t m = 0;
-    int degeneracy = 0;
-    int max_out = 0;
-};
-
-struct kdss_state {
-    StateDev st;
-};
 
 namespace kdss {
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
@@ -37,6 +25,14 @@ kdss_status record(kdss_status code, const std::string &msg) {
     g_last_error = msg;
     return code;
 }
+
+}  // namespace
+
+namespace kdss {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace kdss
+
+namespace {
 
 #define API_BEGIN \
     try {         \

@@ -1080,4 +1080,24 @@ void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
     if (herr) fail(KDSS_ERR_CUDA, "FW iteration: water-filling invariant failed on the device");
 }
 
+// T rule-I iterations on caller-given device memory: r (uint64, cumulative)
+// and the scratch the iterations need -- the per-iteration delta `acc` (n
+// entries, zero on entry), the list of pairs left to the closed form `slow`
+// (one entry per pair of at most 32 nodes), its counter, the error word and
+// the running max of r.  Plain launches on c.stream: no allocation, no graph.
+void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, int32_t *slow,
+                     int *slow_count, int *err, unsigned long long *maxr, int T) {
+    const int64_t n = s.n;
+    const int B = 256;
+    const int sgrid = grid_for(c, n, B, 4);
+    for (int it = 0; it < T; ++it) {
+        launch_pbupdate_int<uint64_t>(c, s, r, acc, slow, slow_count, err);
+        if (n > 0) {
+            k_step_int<uint64_t><<<sgrid, B, 0, c.stream>>>(n, r, acc, maxr, slow_count);
+            KDSS_LAUNCH_CHECK();
+        }
+    }
+}
+
 }  // namespace kdss
+

@@ -36,5 +36,7 @@ struct StateDev {
 
 void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st);
 void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile);
+void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, int32_t *slow,
+                     int *slow_count, int *err, unsigned long long *maxr, int T);
 
 }  // namespace kdss
