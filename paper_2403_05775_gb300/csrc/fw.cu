@@ -608,61 +608,205 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
     }
 }
 
-// The same first step for the continuous rule on the normalised iterate:
-// the plateau A takes n_C/s each when that stays within its caps and below
-// m2; otherwise the pair goes to the full walk.
-__global__ void __launch_bounds__(FW_THREADS)
-k_pb_fast_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
-              const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
-              const float *__restrict__ r, float *acc, float *accc,
-              const uint64_t *__restrict__ binom, int bcols, int k, const int *t_done,
-              int32_t *slow, int *slow_count) {
+// Compensated form of warp_seg_add for FP32: the segmented scan carries a
+// TwoSum error term next to each partial sum, and the tail lane adds the sum
+// to g[id] with a compensated atomic and the error to gc[id].
+__device__ __forceinline__ void warp_seg_add_f32(int32_t id, float x, float *g, float *gc) {
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int32_t prev = __shfl_up_sync(FULL_, id, 1);
+    const bool head = lane == 0 || prev != id;
+    const unsigned heads = __ballot_sync(FULL_, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    float sm = x, cm = 0.f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ys = __shfl_up_sync(FULL_, sm, o);
+        const float yc = __shfl_up_sync(FULL_, cm, o);
+        if (lane - o >= start) {
+            const float t = sm + ys;
+            const float bp = t - sm;
+            const float e = (sm - (t - bp)) + (ys - bp);
+            sm = t;
+            cm = cm + yc + e;
+        }
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && id >= 0) {
+        if (sm != 0.f) gadd_f32(g, gc, id, sm);
+        if (cm != 0.f) atomicAdd(gc + id, cm);
+    }
+}
+
+// First step of the continuous rule for pairs of at most 32 nodes, staged like
+// k_pb_fast: the plateau A at the lowest level m1 takes n_C/s/|A| each when
+// that stays within its caps and below the next level m2 (no remainder in the
+// continuous rule); otherwise the pair goes to the closed form.  The sign bit
+// of a staged value marks V_h nodes (all r/t are >= 0).
+template <int DUMMY = 0>
+__global__ void __launch_bounds__(FA_WARPS * 32)
+k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+               const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
+               const float *__restrict__ r, float *acc, float *accc,
+               const uint64_t *__restrict__ binom, int bcols, int k, const int *t_done,
+               int32_t *slow, int *slow_count, int *err) {
+    __shared__ float sval[FA_WARPS][FA_CAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t np = p_end - p_begin;
+    const int64_t ntile = (np + 31) >> 5;
     const float INF = __int_as_float(0x7f800000);
     const float inv_sigma = inv_sigma_of(t_done);
-    __shared__ AggTable<float> tbl;
-    agg_init(tbl);
-    const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
-    const int64_t cb = blockIdx.x * chunk, ce = cb + chunk < np ? cb + chunk : np;
-    for (int64_t qi = cb + threadIdx.x; qi < ce; qi += blockDim.x) {
-        const int64_t q = p_begin + qi;
+    float *sv = sval[wib];
+    for (int64_t tile = blockIdx.x * (int64_t)FA_WARPS + wib; tile < ntile;
+         tile += (int64_t)gridDim.x * FA_WARPS) {
+        const int64_t qi = tile * 32 + lane;
+        const bool valid = qi < np;
+        const int64_t q = p_begin + (valid ? qi : np - 1);
+        const int64_t myb = pair_off[q], mye = pair_off[q + 1];
+        const int64_t B = __shfl_sync(0xffffffffu, myb, 0);
+        const int64_t lastq = p_begin + ((tile * 32 + 31 < np) ? tile * 32 + 31 : np - 1);
+        const int cnt = (int)(pair_off[lastq + 1] - B);
+        if (cnt > FA_CAP) {
+            if (lane == 0) atomicOr(err, DERR_CAPACITY);
+            continue;
+        }
+#pragma unroll 4
+        for (int i = lane; i < cnt; i += 32) {
+            const int32_t raw = __ldg(nodes + B + i);
+            const float v = __ldg(r + (raw & 0x7fffffff));
+            sv[i] = raw < 0 ? -v : v;  // -0.0 keeps the mark for v = 0
+        }
+        __syncwarp();
+        uint32_t rmask = 0;
+        float share = 0.f;
+        int o = 0;
+        if (valid) {
+            o = (int)(myb - B);
+            const int len = (int)(mye - myb);
+            const int h = hcnt[q];
+            const int p = len - h;
+            const float nC = (float)__ldg(binom + (size_t)p * bcols + (k - h)) * inv_sigma;
+            const float cap_p = (p >= 1 && k - h - 1 >= 0)
+                                    ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                                    : 0.f;
+            float m1 = INF, m2 = INF;
+            uint32_t mask1 = 0, holdm = 0;
+            for (int s2 = 0; s2 < len; ++s2) {
+                const float e = sv[o + s2];
+                const bool hold = signbit(e);
+                if (hold) holdm |= 1u << s2;
+                if (hold ? !(nC > 0.f) : !(cap_p > 0.f)) continue;
+                const float v = fabsf(e);
+                if (v < m1) { m2 = m1; m1 = v; mask1 = 1u << s2; }
+                else if (v == m1) mask1 |= 1u << s2;
+                else if (v < m2) m2 = v;
+            }
+            if (mask1) {
+                const float na = (float)__popc(mask1);
+                const float mu = (mask1 & ~holdm) ? cap_p : nC;
+                share = nC / na;
+                if (share <= mu && share <= m2 - m1) {
+                    rmask = mask1;
+                } else {
+                    const int slot = atomicAdd(slow_count, 1);
+                    if (slot < np) slow[slot] = (int32_t)qi;
+                }
+            }
+        }
+        while (__any_sync(0xffffffffu, rmask != 0)) {
+            int32_t rid = -1;
+            float amount = 0.f;
+            if (rmask) {
+                const int sl = __ffs(rmask) - 1;
+                rmask &= rmask - 1;
+                rid = __ldg(nodes + B + o + sl) & 0x7fffffff;
+                amount = share;
+            }
+            warp_seg_add_f32(rid, amount, acc, accc);
+        }
+        __syncwarp();
+    }
+}
+
+// Closed form of the continuous rule for the pairs the first step left, one
+// warp per pair of at most 32 nodes, in coordinates relative to the lowest
+// active level: L is the water level with g(L) = n_C/s, found from the
+// largest breakpoint b with g(b) <= n_C/s as b + (n_C/s - g(b)) / slope(b);
+// node j takes min(cap_j, max(0, L - x_j)).
+template <int DUMMY = 0>
+__global__ void __launch_bounds__(SB_WARPS * 32)
+k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+              const uint8_t *__restrict__ hcnt, int64_t p_begin, const float *__restrict__ r,
+              float *acc, float *accc, const uint64_t *__restrict__ binom, int bcols, int k,
+              const int *t_done, const int32_t *__restrict__ list, const int *list_count,
+              int64_t list_cap, int *err) {
+    __shared__ float2 sp[SB_WARPS][32];
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const float inv_sigma = inv_sigma_of(t_done);
+    const float INF = __int_as_float(0x7f800000);
+    int64_t np = *list_count;
+    np = np < list_cap ? np : list_cap;
+    for (int64_t li = blockIdx.x * (int64_t)SB_WARPS + wib; li < np;
+         li += (int64_t)gridDim.x * SB_WARPS) {
+        const int64_t q = p_begin + list[li];
         const int64_t off0 = pair_off[q];
         const int len = (int)(pair_off[q + 1] - off0);
+        if (len > 32) {
+            if (lane == 0) atomicOr(err, DERR_CAPACITY);
+            continue;
+        }
         const int h = hcnt[q];
         const int p = len - h;
         const float nC = (float)__ldg(binom + (size_t)p * bcols + (k - h)) * inv_sigma;
         const float cap_p = (p >= 1 && k - h - 1 >= 0)
                                 ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
                                 : 0.f;
-        float m1 = INF, m2 = INF;
-        uint32_t mask1 = 0, holdm = 0;
-        for (int s = 0; s < len; ++s) {
-            const int32_t raw = __ldg(nodes + off0 + s);
-            const bool hold = raw < 0;
-            if (hold) holdm |= 1u << s;
-            if (hold ? !(nC > 0.f) : !(cap_p > 0.f)) continue;
-            const float v = __ldg(r + (raw & 0x7fffffff));
-            if (v < m1) { m2 = m1; m1 = v; mask1 = 1u << s; }
-            else if (v == m1) mask1 |= 1u << s;
-            else if (v < m2) m2 = v;
+        int32_t id = -1;
+        float xj = 0.f, cj = 0.f;
+        if (lane < len) {
+            const int32_t raw = __ldg(nodes + off0 + lane);
+            id = raw & 0x7fffffff;
+            xj = __ldg(r + id);
+            cj = raw < 0 ? nC : cap_p;
         }
-        if (!mask1) continue;
-        const float na = (float)__popc(mask1);
-        const float mu = (mask1 & ~holdm) ? cap_p : nC;
-        const float share = nC / na;
-        if (!(share <= mu && share <= m2 - m1)) {
-            const int slot = atomicAdd(slow_count, 1);
-            if (slot < np) slow[slot] = (int32_t)qi;
+        float base = cj > 0.f ? xj : INF;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) base = fminf(base, __shfl_xor_sync(FULL_, base, o));
+        const float xl = cj > 0.f ? xj - base : 0.f;
+        sp[wib][lane] = make_float2(xl, cj);
+        __syncwarp();
+        const float b1 = xl, b2 = xl + cj;
+        float g1 = 0.f, g2 = 0.f;
+#pragma unroll 4
+        for (int i = 0; i < len; ++i) {
+            const float2 e = sp[wib][i];
+            g1 += fminf(e.y, fmaxf(0.f, b1 - e.x));
+            g2 += fminf(e.y, fmaxf(0.f, b2 - e.x));
+        }
+        float key = -1.f, bg = 0.f;
+        if (cj > 0.f) {
+            if (g1 <= nC) { key = b1; bg = g1; }
+            if (g2 <= nC) { key = b2; bg = g2; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ok = __shfl_xor_sync(FULL_, key, o);
+            const float og = __shfl_xor_sync(FULL_, bg, o);
+            if (ok > key) { key = ok; bg = og; }
+        }
+        if (key < 0.f) {
+            if (lane == 0) atomicOr(err, DERR_LOGIC);
             continue;
         }
-        uint32_t bits = mask1;
-        while (bits) {
-            const int sl = __ffs(bits) - 1;
-            bits &= bits - 1;
-            agg_add_f32(tbl, __ldg(nodes + off0 + sl) & 0x7fffffff, share, acc, accc);
-        }
+        // right slope at key: nodes with x_j <= key < x_j + c_j, the upper end
+        // rounded exactly as the breakpoint b2 was
+        const int sl = __popc(__ballot_sync(FULL_, cj > 0.f && key >= xl && key < b2));
+        const float L = sl > 0 ? key + (nC - bg) / (float)sl : key;
+        const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, L - xl)) : 0.f;
+        if (dj > 0.f) gadd_f32(acc, accc, id, dj);
+        __syncwarp();
     }
-    agg_flush_f32(tbl, acc, accc);
 }
 
 // Rule C (continuous) PBUpdate on the normalised iterate, FP32.
@@ -890,13 +1034,20 @@ void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
         KDSS_LAUNCH_CHECK();
     };
     if (e > b) {
-        int grid = (int)std::min<int64_t>(ceil_div(e - b, FW_THREADS), (int64_t)c.num_sms * 8);
-        k_pb_fast_f32<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
-                                                         st.r32.p, st.a32.p, st.a32c.p, s.binom.p,
-                                                         bc, s.k, st.dev_t.p, st.ovf_list.p,
-                                                         st.ovf_count.p);
+        const int64_t tiles = ceil_div(e - b, 32);
+        int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
+        k_pb_fast_f32s<<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
+                                                           st.r32.p, st.a32.p, st.a32c.p,
+                                                           s.binom.p, bc, s.k, st.dev_t.p,
+                                                           st.ovf_list.p, st.ovf_count.p, st.err.p);
         KDSS_LAUNCH_CHECK();
-        go(k_pbupdate_f32<8, 4>, 8, b, e, st.ovf_list.p, st.ovf_count.p);
+        int sgrid = (int)std::min<int64_t>(ceil_div(e - b, SB_WARPS), (int64_t)c.num_sms * 8);
+        k_pb_slow_f32<<<sgrid, SB_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b,
+                                                           st.r32.p, st.a32.p, st.a32c.p,
+                                                           s.binom.p, bc, s.k, st.dev_t.p,
+                                                           st.ovf_list.p, st.ovf_count.p, e - b,
+                                                           st.err.p);
+        KDSS_LAUNCH_CHECK();
     }
     if (s.class_begin[4] > s.class_begin[3])
         go(k_pbupdate_f32<32, 8>, 32, s.class_begin[3], s.class_begin[4], nullptr, nullptr);

@@ -74,9 +74,9 @@ struct PeelCtl {
     int degeneracy;
 };
 
-constexpr int PEEL_THREADS = 256;
+constexpr int PEEL_THREADS = 1024;
 
-__global__ void __launch_bounds__(PEEL_THREADS)
+__global__ void __launch_bounds__(PEEL_THREADS, 1)
 k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
        int32_t *deg, int32_t *rnd, int32_t *core, int32_t *fa, int32_t *fb, PeelCtl *ctl,
        uint64_t timeout_ns) {
@@ -138,15 +138,28 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
         for (int64_t i = warp; i < cnt; i += nwarps) {
             int32_t v = __ldcg(cur + i);
             int64_t e0 = off[v], e1 = off[v + 1];
-            for (int64_t e = e0 + lane; e < e1; e += 32) {
-                int32_t w = adj[e];
-                if (__ldcg(rnd + w) < 0) {
-                    int old = atomicSub(deg + w, 1);
-                    if (old == level + 1) {
-                        rnd[w] = round + 1;
-                        core[w] = level;
+            // four neighbours per lane at a time: their loads and atomics are
+            // independent and overlap (hubs have thousands of neighbours)
+            for (int64_t e = e0 + lane; e < e1; e += 128) {
+                int32_t w[4];
+                bool live[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t ee = e + 32 * u;
+                    w[u] = ee < e1 ? adj[ee] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) live[u] = w[u] >= 0 && __ldcg(rnd + w[u]) < 0;
+                int old[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) old[u] = live[u] ? atomicSub(deg + w[u], 1) : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (live[u] && old[u] == level + 1) {
+                        rnd[w[u]] = round + 1;
+                        core[w[u]] = level;
                         int idx = atomicAdd(&ctl->count[cn], 1);
-                        if (idx < n) nxt[idx] = w;
+                        if (idx < n) nxt[idx] = w[u];
                     }
                 }
             }
@@ -288,10 +301,12 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
         KDSS_CUDA(cudaMemcpyAsync(&ctl.p->minval, &ff, sizeof ff, cudaMemcpyHostToDevice, c.stream));
         k_degrees<<<grid_for(c, n, B), B, 0, c.stream>>>(out.off.p, n, deg.p, out.rnd.p);
         KDSS_LAUNCH_CHECK();
+        // One block per SM at most: every round ends in a grid barrier whose
+        // cost grows with the number of arriving blocks.
         int per_sm = 0;
         KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, PEEL_THREADS, 0));
-        per_sm = std::max(1, std::min(per_sm, 4));
-        int grid = (int)std::min<int64_t>((int64_t)c.num_sms * per_sm,
+        if (per_sm < 1) fail(KDSS_ERR_CUDA, "peeling kernel cannot be resident");
+        int grid = (int)std::min<int64_t>((int64_t)c.num_sms,
                                           std::max<int64_t>(1, ceil_div(n, PEEL_THREADS)));
         uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per barrier wait
         int64_t nn = n;

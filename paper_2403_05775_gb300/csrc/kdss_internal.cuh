@@ -167,10 +167,15 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned int nblo
             __threadfence();
             atomicAdd(&bar->gen, 1u);
         } else {
+            // poll without sleeping (the wait is usually a few microseconds);
+            // check the deadline only every 256 polls
             uint64_t t0 = globaltimer_ns();
-            while (*vgen == g) {
-                __nanosleep(64);
-                if (globaltimer_ns() - t0 > timeout_ns) {
+            unsigned int polls = 0;
+            while (true) {
+                unsigned int cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
+                if (cur != g) break;
+                if ((++polls & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
                     atomicOr(err, DERR_TIMEOUT);
                     ok = 0;
                     break;

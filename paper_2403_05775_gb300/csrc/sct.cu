@@ -132,19 +132,22 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
         for (int j = lane; j < d; j += 32) O[j] = out_adj[o0 + j];
         for (int q = lane; q < d * S; q += 32) A[q] = 0u;
         __syncwarp();
-        for (int j = 0; j < d; ++j) {
+        // one row per lane: the later neighbours of O[j] that are in O (both
+        // lists ascending, so a merge), each edge set in both rows
+        for (int j = lane; j < d; j += 32) {
             const int32_t u = O[j];
-            const int64_t e0 = out_off[u], e1 = out_off[u + 1];
-            for (int64_t e = e0 + lane; e < e1; e += 32) {
-                const int32_t w = out_adj[e];
-                int lo = j + 1, hi = d;  // w is later than u, so after j in O
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (O[mid] < w) lo = mid + 1; else hi = mid;
-                }
-                if (lo < d && O[lo] == w) {
-                    atomicOr(&A[(size_t)j * S + (lo >> 5)], 1u << (lo & 31));
-                    atomicOr(&A[(size_t)lo * S + (j >> 5)], 1u << (j & 31));
+            int64_t e = out_off[u];
+            const int64_t e1 = out_off[u + 1];
+            int x = j + 1;  // later than u, so after j in O
+            while (e < e1 && x < d) {
+                const int32_t w = out_adj[e], ox = O[x];
+                if (w < ox) ++e;
+                else if (ox < w) ++x;
+                else {
+                    atomicOr(&A[(size_t)j * S + (x >> 5)], 1u << (x & 31));
+                    atomicOr(&A[(size_t)x * S + (j >> 5)], 1u << (j & 31));
+                    ++e;
+                    ++x;
                 }
             }
         }
