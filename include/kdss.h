@@ -230,12 +230,28 @@ typedef struct kdss_query {
 } kdss_query;
 
 /*
- * kdss_solve_batch -- solve nq independent (graph, k, T) queries.  The SCTs
- * are built per query, then the FW iterations of all queries run together in
- * one launch per iteration over the concatenated pairs (queries that reached
- * their T are masked), and one segmented sort and scan extract every query.
- * out[i] receives query i's result and status.  Returns the first error, or
- * OK when every query succeeded.
+ * kdss_solve_batch -- solve nq independent (graph, k, T) queries (the
+ * paper solves one graph at a time; batching is this library's addition).
+ * Queries with equal (k, T) are joined into one disjoint-union graph (node
+ * ids shifted), which goes through one CSR build, one peeling and one SCT
+ * build: peeling acts on each connected component separately, so every
+ * query gets the order, the SCT and therefore the r it would get alone.
+ * All groups then iterate together (one CUDA graph per iteration; a group
+ * drops out after its T), and one segmented sort and scan per group extract
+ * every query's densest prefix.
+ *   q[i]   : the query (graph as in kdss_build_sct, k in [2, 64], T >= 0).
+ *   out[i] : caller-owned; receives query i's result and status (ids
+ *            allocated by the library, freed with kdss_result_free).
+ *   opts   : as for kdss_solve (one precision and order for all queries).
+ * Results equal kdss_solve's per query: bit for bit for KDSS_INT64 and
+ * KDSS_FP64; for KDSS_FP32K the same rule in the same precision (its atomic
+ * sums round in the order the hardware performs them, run to run, as in
+ * kdss_solve).
+ * A query that is invalid, has an edge endpoint outside [0, n) or leaves the
+ * exact range gets its own error status and a zeroed result; the others are
+ * solved.  Returns OK when every query succeeded, else the first failing
+ * query's status (its message in kdss_last_error); an error of the whole
+ * batch (device memory, CUDA) is every query's status.
  */
 kdss_status kdss_solve_batch(const kdss_query *q, int32_t nq, kdss_result *out,
                              const kdss_opts *opts);

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fw.cuh"
 
@@ -15,6 +16,8 @@ using namespace kdss;
 
 namespace kdss {
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
+void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts *opts,
+                 std::vector<kdss_status> &status, std::vector<std::string> &msgs);
 }
 
 namespace {
@@ -95,6 +98,16 @@ kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opt
         throw;
     }
     *out = h;
+    API_END
+}
+
+kdss_status batch_impl(const kdss_query *q, int32_t nq, kdss_result *out, const kdss_opts *opts,
+                       std::vector<kdss_status> &status, std::vector<std::string> &msgs) {
+    API_BEGIN
+    const int order = opts ? opts->order : KDSS_ORDER_PEEL;
+    if (order != KDSS_ORDER_PEEL && order != KDSS_ORDER_CORE)
+        fail(KDSS_ERR_INVALID_ARG, "unknown vertex order");
+    solve_batch(q, nq, out, opts, status, msgs);
     API_END
 }
 
@@ -283,15 +296,21 @@ kdss_status kdss_solve(const kdss_graph_desc *g, int32_t k, int32_t T, const kds
 kdss_status kdss_solve_batch(const kdss_query *q, int32_t nq, kdss_result *out,
                              const kdss_opts *opts) {
     if (nq < 0 || (nq > 0 && (!q || !out))) return record(KDSS_ERR_INVALID_ARG, "bad batch arguments");
-    kdss_status first = KDSS_OK;
-    std::string first_msg;
-    for (int32_t i = 0; i < nq; ++i) {
-        kdss_status rc = kdss_solve(&q[i].graph, q[i].k, q[i].T, opts, &out[i]);
-        out[i].status = rc;
-        if (rc != KDSS_OK && first == KDSS_OK) { first = rc; first_msg = g_last_error; }
+    for (int32_t i = 0; i < nq; ++i) memset(&out[i], 0, sizeof out[i]);
+    std::vector<kdss_status> status;
+    std::vector<std::string> msgs;
+    const kdss_status rc = batch_impl(q, nq, out, opts, status, msgs);
+    if (rc != KDSS_OK) {  // the whole batch failed: every query carries its status
+        for (int32_t i = 0; i < nq; ++i) {
+            free(out[i].ids);
+            memset(&out[i], 0, sizeof out[i]);
+            out[i].status = rc;
+        }
+        return rc;
     }
-    g_last_error = first_msg;
-    return first;
+    for (int32_t i = 0; i < nq; ++i)
+        if (status[i] != KDSS_OK) return record(status[i], msgs[i]);
+    return record(KDSS_OK, "");
 }
 
 void kdss_sct_free(kdss_sct *s) {

@@ -271,6 +271,17 @@ void launch_events(const Ctx &c, const SctDev &s, int cls, const int32_t *pos,
 
 }  // namespace
 
+// The increments of every class, positions taken from pos (used by the
+// segmented extraction of batches, whose positions index query segments).
+void launch_prefix_events_all(const Ctx &c, const SctDev &s, const int32_t *pos,
+                              unsigned long long *hist, unsigned long long *fhist) {
+    launch_events<8, 1>(c, s, 0, pos, hist, fhist);
+    launch_events<8, 2>(c, s, 1, pos, hist, fhist);
+    launch_events<8, 4>(c, s, 2, pos, hist, fhist);
+    launch_events<32, 8>(c, s, 3, pos, hist, fhist);
+    launch_events<32, 32>(c, s, 4, pos, hist, fhist);
+}
+
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out) {
     const int64_t n = s.n;
     memset(out, 0, sizeof *out);
@@ -317,11 +328,7 @@ void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_resu
     DBuf<unsigned long long> hist(c, (size_t)n + 2), fhist(c, (size_t)n + 2);
     zero(c, hist.p, (n + 2) * 8);
     zero(c, fhist.p, (n + 2) * 8);
-    launch_events<8, 1>(c, s, 0, pos.p, hist.p, fhist.p);
-    launch_events<8, 2>(c, s, 1, pos.p, hist.p, fhist.p);
-    launch_events<8, 4>(c, s, 2, pos.p, hist.p, fhist.p);
-    launch_events<32, 8>(c, s, 3, pos.p, hist.p, fhist.p);
-    launch_events<32, 32>(c, s, 4, pos.p, hist.p, fhist.p);
+    launch_prefix_events_all(c, s, pos.p, hist.p, fhist.p);
     inclusive_scan_u64_async(c, (const uint64_t *)hist.p, (uint64_t *)hist.p, n + 1);
     inclusive_scan_u64_async(c, (const uint64_t *)fhist.p, (uint64_t *)fhist.p, n + 1);
     unsigned long long best = 0, fbest = 0;

@@ -30,6 +30,7 @@
 // error-free (TwoSum) compensated atomics and folded into r/t by a Kahan
 // update in the step kernel.
 #include <algorithm>
+#include <functional>
 
 #include "fw.cuh"
 
@@ -957,7 +958,7 @@ __global__ void k_step_int(int64_t n, RT *r, RT *acc, unsigned long long *maxr, 
 // rhat_t = rhat_{t-1} + (s * a - rhat_{t-1}) / t with Kahan compensation,
 // t = *t_done + 1; the last block to finish advances *t_done.
 __global__ void k_step_f32(int64_t n, float *r, float *rc, float *a, float *ac, int *t_done,
-                           unsigned int *blocks_done, int *slow_count) {
+                           unsigned int *blocks_done, int *slow_count, int advance) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *slow_count = 0;  // next iteration's list
     const int t = *t_done + 1;
     const float sigma = (float)(t - 1 > 1 ? t - 1 : 1);
@@ -982,7 +983,7 @@ __global__ void k_step_f32(int64_t n, float *r, float *rc, float *a, float *ac, 
     __syncthreads();
     if (last && threadIdx.x == 0) {
         *blocks_done = 0u;
-        *t_done = t;
+        if (advance) *t_done = t;
         __threadfence();
     }
 }
@@ -1022,14 +1023,15 @@ void launch_pbupdate_int(const Ctx &c, const SctDev &s, RT *r, RT *acc, int32_t 
         go(k_pbupdate_int<32, 32, RT>, 32, s.class_begin[4], s.class_begin[5], nullptr, nullptr);
 }
 
-void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
+void launch_pbupdate_f32_on(const Ctx &c, const SctDev &s, StateDev &st, float *r32, float *a32,
+                            float *a32c) {
     const int bc = s.k + 1;
     const int64_t b = s.class_begin[0], e = s.class_begin[3];
     auto go = [&](auto kern, int G, int64_t pb, int64_t pe, const int32_t *list, const int *lc) {
         const int64_t groups_per_block = (FW_THREADS / 32) * (32 / G);
         int grid = (int)std::min<int64_t>(ceil_div(pe - pb, groups_per_block), (int64_t)c.num_sms * 4);
-        kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, pb, pe, st.r32.p,
-                                                st.a32.p, st.a32c.p, s.binom.p, bc, s.k,
+        kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, pb, pe, r32,
+                                                a32, a32c, s.binom.p, bc, s.k,
                                                 st.dev_t.p, list, lc, st.err.p);
         KDSS_LAUNCH_CHECK();
     };
@@ -1037,22 +1039,25 @@ void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
         const int64_t tiles = ceil_div(e - b, 32);
         int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
         k_pb_fast_f32s<<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
-                                                           st.r32.p, st.a32.p, st.a32c.p,
-                                                           s.binom.p, bc, s.k, st.dev_t.p,
-                                                           st.ovf_list.p, st.ovf_count.p, st.err.p);
+                                                           r32, a32, a32c, s.binom.p, bc, s.k,
+                                                           st.dev_t.p, st.ovf_list.p,
+                                                           st.ovf_count.p, st.err.p);
         KDSS_LAUNCH_CHECK();
         int sgrid = (int)std::min<int64_t>(ceil_div(e - b, SB_WARPS), (int64_t)c.num_sms * 8);
         k_pb_slow_f32<<<sgrid, SB_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b,
-                                                           st.r32.p, st.a32.p, st.a32c.p,
-                                                           s.binom.p, bc, s.k, st.dev_t.p,
-                                                           st.ovf_list.p, st.ovf_count.p, e - b,
-                                                           st.err.p);
+                                                           r32, a32, a32c, s.binom.p, bc, s.k,
+                                                           st.dev_t.p, st.ovf_list.p,
+                                                           st.ovf_count.p, e - b, st.err.p);
         KDSS_LAUNCH_CHECK();
     }
     if (s.class_begin[4] > s.class_begin[3])
         go(k_pbupdate_f32<32, 8>, 32, s.class_begin[3], s.class_begin[4], nullptr, nullptr);
     if (s.class_begin[5] > s.class_begin[4])
         go(k_pbupdate_f32<32, 32>, 32, s.class_begin[4], s.class_begin[5], nullptr, nullptr);
+}
+
+void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
+    launch_pbupdate_f32_on(c, s, st, st.r32.p, st.a32.p, st.a32c.p);
 }
 
 struct EventPair {
@@ -1116,7 +1121,7 @@ void enqueue_step(const Ctx &c, const SctDev &s, StateDev &st) {
     if (st.precision == KDSS_FP32K) {
         k_step_f32<<<sgrid, B, 0, c.stream>>>(n, st.r32.p, st.r32c.p, st.a32.p, st.a32c.p,
                                              st.dev_t.p, (unsigned int *)(st.dev_t.p + 1),
-                                             st.ovf_count.p);
+                                             st.ovf_count.p, 1);
     } else if (st.precision == KDSS_FP64) {
         k_step_int<double><<<sgrid, B, 0, c.stream>>>(n, (double *)st.r.p, (double *)st.acc.p,
                                                       st.maxr.p, st.ovf_count.p);
@@ -1250,5 +1255,55 @@ void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, 
     }
 }
 
+// ---- several SCTs over disjoint node ranges sharing one state (batches) ----
+
+void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, StateDev &st) {
+    SctDev shell;
+    shell.n = n;
+    shell.class_begin[0] = 0;
+    shell.class_begin[3] = short_capacity;
+    fw_init(c, shell, precision, st);
+}
+
+void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off) {
+    // the slow-pair list is shared by the groups of one iteration
+    KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), c.stream));
+    if (st.precision == KDSS_FP32K) {
+        launch_pbupdate_f32_on(c, s, st, st.r32.p + node_off, st.a32.p + node_off,
+                               st.a32c.p + node_off);
+    } else if (st.precision == KDSS_FP64) {
+        launch_pbupdate_int<double>(c, s, (double *)st.r.p + node_off, (double *)st.acc.p + node_off,
+                                    st.ovf_list.p, st.ovf_count.p, st.err.p);
+    } else {
+        launch_pbupdate_int<uint64_t>(c, s, st.r.p + node_off, st.acc.p + node_off, st.ovf_list.p,
+                                      st.ovf_count.p, st.err.p);
+    }
+}
+
+void fw_enqueue_step_range(const Ctx &c, StateDev &st, int64_t node_off, int64_t n, bool advance) {
+    if (n <= 0) return;
+    const int B = 256;
+    const int sgrid = grid_for(c, n, B, 4);
+    if (st.precision == KDSS_FP32K) {
+        k_step_f32<<<sgrid, B, 0, c.stream>>>(n, st.r32.p + node_off, st.r32c.p + node_off,
+                                             st.a32.p + node_off, st.a32c.p + node_off, st.dev_t.p,
+                                             (unsigned int *)(st.dev_t.p + 1), st.ovf_count.p,
+                                             advance ? 1 : 0);
+    } else if (st.precision == KDSS_FP64) {
+        k_step_int<double><<<sgrid, B, 0, c.stream>>>(n, (double *)st.r.p + node_off,
+                                                      (double *)st.acc.p + node_off, st.maxr.p,
+                                                      st.ovf_count.p);
+    } else {
+        k_step_int<uint64_t><<<sgrid, B, 0, c.stream>>>(n, st.r.p + node_off, st.acc.p + node_off,
+                                                        st.maxr.p, st.ovf_count.p);
+    }
+    KDSS_LAUNCH_CHECK();
+}
+
+long long fw_capture(const Ctx &c, cudaGraphExec_t *exec, const std::function<void(const Ctx &)> &fn) {
+    return capture(c, exec, fn);
+}
+
 }  // namespace kdss
+
 

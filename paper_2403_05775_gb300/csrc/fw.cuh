@@ -1,6 +1,8 @@
 // fw.cuh -- Frank-Wolfe state and iterations (steps A4-A5).
 #pragma once
 
+#include <functional>
+
 #include "sct.cuh"
 
 namespace kdss {
@@ -36,6 +38,11 @@ struct StateDev {
 
 void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st);
 void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile);
+// batches: several SCTs over disjoint node ranges of one state
+void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, StateDev &st);
+void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off);
+void fw_enqueue_step_range(const Ctx &c, StateDev &st, int64_t node_off, int64_t n, bool advance);
+long long fw_capture(const Ctx &c, cudaGraphExec_t *exec, const std::function<void(const Ctx &)> &fn);
 void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, int32_t *slow,
                      int *slow_count, int *err, unsigned long long *maxr, int T);
 

@@ -139,8 +139,72 @@ def chung_lu(n: int, mean_degree: float, beta: float, seed: int,
     return n, *_as_edges(src, dst), nodes.astype(np.int32)
 
 
+_clib = None
+
+
+def _rmat_lib():
+    """The C twin of ``_rmat_block_numpy`` (synth/_rmat.c, built with gcc on
+    first use into synth/_build); None when it cannot be built."""
+    global _clib
+    if _clib is None:
+        import ctypes as C
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        so = os.path.join(here, "_build", "librmat.so")
+        srcf = os.path.join(here, "_rmat.c")
+        try:
+            if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(srcf):
+                os.makedirs(os.path.dirname(so), exist_ok=True)
+                tmp = so + f".{os.getpid()}.tmp"
+                subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                                       srcf, "-o", tmp])
+                os.replace(tmp, so)
+            L = C.CDLL(so)
+            L.synth_rmat_block.restype = C.c_int64
+            L.synth_rmat_block.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_int, C.c_double,
+                                           C.c_double, C.c_double, C.c_int64, C.c_void_p,
+                                           C.c_void_p, C.c_int]
+            _clib = L
+        except (OSError, subprocess.CalledProcessError):
+            _clib = False
+    return _clib or None
+
+
+def _rmat_block_numpy(sseed_stream: tuple, base: int, cnt: int, scale: int, a, ab, abc, n):
+    """One block of R-MAT draws (the definition): draw j takes the uniforms
+    at positions base + j * scale + l, l < scale, of the stream; draws with an
+    endpoint >= n are dropped."""
+    seed, stream = sseed_stream
+    u = uniforms(seed, stream, base, cnt * scale).reshape(cnt, scale)
+    src = np.zeros(cnt, dtype=np.int64)
+    dst = np.zeros(cnt, dtype=np.int64)
+    for lvl in range(scale):
+        x = u[:, lvl]
+        bit = np.int64(1) << np.int64(scale - 1 - lvl)
+        right = ((x >= a) & (x < ab)) | (x >= abc)
+        down = x >= ab
+        src += np.where(down, bit, 0)
+        dst += np.where(right, bit, 0)
+    ok = (src < n) & (dst < n)
+    return src[ok], dst[ok]
+
+
+def _rmat_block(seed, stream, base, cnt, scale, a, ab, abc, n, use_c=True):
+    L = _rmat_lib() if use_c else None
+    if L is None:
+        return _rmat_block_numpy((seed, stream), base, cnt, scale, a, ab, abc, n)
+    import os
+    src = np.empty(cnt, np.int64)
+    dst = np.empty(cnt, np.int64)
+    kept = L.synth_rmat_block(stream_seed(seed, stream), base, cnt, scale, a, ab, abc, n,
+                              src.ctypes.data, dst.ctypes.data, min(os.cpu_count() or 1, 64))
+    return src[:kept], dst[:kept]
+
+
 def rmat(n: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19,
-         plant_size: int = 0, plant_prob: float = 1.0, stream_base: int = 0):
+         plant_size: int = 0, plant_prob: float = 1.0, stream_base: int = 0,
+         use_c: bool = True):
     """R-MAT graph on n nodes (scale = ceil(log2 n)) with ``edge_factor * n``
     edge draws.  Each draw descends ``scale`` levels choosing quadrant
     (a, b, c, d = 1-a-b-c) from one uniform per level; draws with an endpoint
@@ -155,19 +219,8 @@ def rmat(n: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19,
     ab, abc = a + b, a + b + c
     while have < want:
         cnt = int((want - have) * 1.1) + 16
-        base = attempt * (1 << 40)
-        u = uniforms(seed, stream_base + 0, base, cnt * scale).reshape(cnt, scale)
-        src = np.zeros(cnt, dtype=np.int64)
-        dst = np.zeros(cnt, dtype=np.int64)
-        for lvl in range(scale):
-            x = u[:, lvl]
-            bit = np.int64(1) << np.int64(scale - 1 - lvl)
-            right = ((x >= a) & (x < ab)) | (x >= abc)
-            down = x >= ab
-            src += np.where(down, bit, 0)
-            dst += np.where(right, bit, 0)
-        ok = (src < n) & (dst < n)
-        src, dst = src[ok], dst[ok]
+        src, dst = _rmat_block(seed, stream_base + 0, attempt * (1 << 40), cnt, scale, a, ab,
+                               abc, n, use_c)
         take = min(src.size, want - have)
         out_s.append(src[:take])
         out_d.append(dst[:take])

@@ -1,0 +1,32 @@
+"""The input generators: the C twin of the R-MAT draws equals the numpy
+definition draw for draw, and the generators are deterministic per seed."""
+import numpy as np
+
+import synth
+
+
+def test_rmat_c_twin_equals_the_numpy_definition():
+    assert synth._rmat_lib() is not None
+    for n, ef, sb in [(1, 4, 0), (2, 3, 4), (1000, 16, 100), (3001, 16, 104), (65536, 8, 7)]:
+        a = synth.rmat(n, ef, 3, plant_size=min(30, n), stream_base=sb)
+        b = synth.rmat(n, ef, 3, plant_size=min(30, n), stream_base=sb, use_c=False)
+        for x, y in zip(a[1:], b[1:]):
+            assert np.array_equal(x, y), (n, ef, sb)
+
+
+def test_rmat_shape():
+    n, s, d, planted = synth.rmat(5000, 16, 3, plant_size=30, plant_prob=1.0, stream_base=100)
+    assert s.dtype == np.int32 and s.size == d.size >= 16 * 5000
+    assert s.min() >= 0 and max(s.max(), d.max()) < n
+    assert planted.size == 30 and np.all(np.diff(planted) > 0)
+    # skew: the lowest ids carry most of the R-MAT mass (a = 0.57 quadrant)
+    deg = np.bincount(np.concatenate([s, d]), minlength=n)
+    assert deg[: n // 16].sum() > deg[-(n // 16):].sum() * 4
+
+
+def test_generators_are_deterministic():
+    a = synth.batch_rmat_graph(5, 1234)
+    b = synth.batch_rmat_graph(5, 1234)
+    assert all(np.array_equal(x, y) for x, y in zip(a[1:], b[1:]))
+    c = synth.batch_rmat_graph(6, 1234)
+    assert not np.array_equal(a[1], c[1])
