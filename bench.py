@@ -78,19 +78,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def code_digest(path):
+    """sha256 of a C/CUDA source with its comments and whitespace removed, so
+    that the digest changes with the code and not with its comments."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
+
+
 def ncu_traffic(kernel_src):
     """Per-launch DRAM bytes of the PBUpdate pass from the committed ncu
-    summary, or None when the kernel source changed since it was taken."""
+    summary, or None when the kernel code changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "fw_pbupdate_chunglu1e5.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_iteration:\s*([0-9.eE+]+)", text)
-    h = re.search(r"fw\.cu sha256:\s*([0-9a-f]{64})", text)
+    h = re.search(r"fw\.cu code digest:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m.group(1)) if cur == h.group(1) else None
+    return float(m.group(1)) if code_digest(kernel_src) == h.group(1) else None
 
 
 class ClockSampler:

@@ -4,8 +4,8 @@
  *
  * Pipeline (the paper's three steps, Fig. 1): build the SCT index of the
  * k-cliques (Sec. 2), run Frank-Wolfe iterations of PBUpdate over its pairs
- * (Alg. 2-3), sort the nodes by r and return the densest prefix (Alg. 2
- * lines 5-7).  Every step runs in CUDA kernels on one GPU; this header is the
+ * (Alg. 2-3), sort the nodes by r and return the densest prefix (the final
+ * step of Alg. 2).  Every step runs in CUDA kernels on one GPU; this header is the
  * only boundary.  No C++ or torch types cross it.
  *
  * Conventions
@@ -186,8 +186,9 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
 /*
  * kdss_fw_iterate -- step A4-A5: T Frank-Wolfe iterations of Alg. 2 with the
  * PBUpdate rule of Alg. 3 over every pair, all pairs of iteration t reading
- * r_{t-1} (synchronous form); the remainder units of Alg. 3 line 16 go to the
- * lowest node ids; r_0 = 0.  *state is created when NULL (precision from
+ * r_{t-1} (synchronous form); the remainder units of Alg. 3 (fewer than the
+ * plateau's size, placed at random in the paper) go to the lowest node ids;
+ * r_0 = 0.  *state is created when NULL (precision from
  * opts), otherwise continued from its iteration count t.
  *   s     : SCT handle.
  *   state : in/out FW state.
@@ -207,7 +208,7 @@ kdss_status kdss_state_copy_r(const kdss_state *st, void *r_host, int32_t *t_out
 kdss_status kdss_state_timing(const kdss_state *st, kdss_timing *out);
 
 /*
- * kdss_extract -- step A6 (Alg. 2 lines 5-7): sort the nodes by r
+ * kdss_extract -- step A6 (the final step of Alg. 2): sort the nodes by r
  * non-increasing (ties by ascending id), count the k-cliques of every prefix
  * V_i exactly from the pairs (Lemmas 2.5-2.6), and return the prefix of
  * largest rho_k(V_i) = |C_k(V_i)| / i (largest i on ties), with the bound

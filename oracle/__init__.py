@@ -287,7 +287,7 @@ def fw_cliques(n, cliques, k, T, r0=None):
 # --------------------------------------------------------------------------
 
 def sort_desc(r):
-    """Node order by (r desc, id asc) (Alg. 2 line 5)."""
+    """Node order by (r desc, id asc) (the final sort of Alg. 2, reading R4)."""
     n = len(r)
     out = np.zeros(n, np.int32)
     if np.asarray(r).dtype == np.float64:

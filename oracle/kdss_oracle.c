@@ -16,17 +16,21 @@
  *  R1  Pairs in one FW iteration read the ranking of the previous iteration
  *      (synchronous / Jacobi form of Alg. 2); the in-place sequential form of
  *      Alg. 2 is provided as well (orc_fw_seq).
- *  R2  Alg. 3 line 16 hands the remainder units to "random" nodes of the
- *      current plateau; here they go to the lowest original vertex ids
+ *  R2  Alg. 3 hands the units left after the last whole round (fewer than
+ *      the plateau's size) to randomly chosen nodes of the current plateau;
+ *      here they go to the lowest original vertex ids
  *      (this reproduces Example 3.1, where the single clique of
  *      ({u4},{u5,u6}) goes to u4).
- *  R3  r starts at zero (Alg. 2 line 1; Example 3.1 starts from zeros).
- *  R4  Alg. 2 line 5 sorts by non-increasing r, ties by ascending id.
+ *  R3  r starts at zero (Alg. 2 leaves the initial r open; Example 3.1
+ *      starts from zeros).
+ *  R4  The final sort of Alg. 2 is by non-increasing r, ties by ascending
+ *      id.
  *  R5  Ties in the final argmax take the largest prefix (maximality of the
  *      k-clique densest subgraph, Def. 2.1).
- *  R6  Alg. 3 removes capped nodes only after an allocation (line 18); nodes
- *      whose cap is zero from the start (every V_p node when |V_h| = k) are
- *      removed before the loop, otherwise line 16 could exceed the C4 cap.
+ *  R6  Alg. 3 removes a node whose cap is used up only after an allocation
+ *      round; nodes whose cap is zero from the start (every V_p node when
+ *      |V_h| = k) are removed before the first round, otherwise the
+ *      remainder units could go to them and exceed the C4 cap.
  *  R7  The SCT construction is only cited ([PIVOTER]).  It is restated from
  *      Lemmas 2.4-2.5: root v in the chosen vertex order with candidates
  *      N+(v); pivot = candidate with most neighbours among the candidates,
@@ -368,8 +372,9 @@ int64_t orc_sct(int64_t n, const int64_t *off, const int32_t *adj,
 /* PBUpdate (Alg. 3), integer form, reading R2 + R6.                         */
 /* Input: the len nodes of a pair (original ids), their rankings r, h =     */
 /* |V_h| (the first h nodes are V_h), k.  Output: delta[i] added to node i. */
-/* The steps follow Alg. 3: plateaus of equal r (line 1), n_C and the       */
-/* upper bounds of lines 2-5, then the plateau walk of lines 7-20.          */
+/* The steps follow Alg. 3: the count n_C and the per-node upper bounds    */
+/* (Lemma 2.6), plateaus of equal r in ascending order, then the walk that  */
+/* raises the lowest plateau round by round.                                */
 /* ------------------------------------------------------------------------ */
 static const uint64_t *g_sort_r; static const int32_t *g_sort_id;
 static int cmp_by_r_id(const void *a, const void *b) {
@@ -386,16 +391,16 @@ int orc_pbupdate_alg3(int len, const int32_t *ids, const uint64_t *r_in, int h, 
                       uint64_t *delta) {
     int p = len - h;
     int ovf = 0;
-    uint64_t nC = orc_binom(p, k - h, &ovf);                 /* line 2 */
-    uint64_t up_h = orc_binom(p, k - h, &ovf);               /* line 4 */
-    uint64_t up_p = orc_binom(p - 1, k - h - 1, &ovf);       /* line 5 */
+    uint64_t nC = orc_binom(p, k - h, &ovf);                 /* cliques of the pair */
+    uint64_t up_h = orc_binom(p, k - h, &ovf);               /* cap of a hold node */
+    uint64_t up_p = orc_binom(p - 1, k - h - 1, &ovf);       /* cap of a pivot node */
     if (ovf) return ORC_OVERFLOW;
     uint64_t *r = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)len);
     uint64_t *up = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)len);
     int *srt = (int *)malloc(sizeof(int) * (size_t)len);
     int *A = (int *)malloc(sizeof(int) * (size_t)len);
     for (int i = 0; i < len; ++i) { r[i] = r_in[i]; up[i] = i < h ? up_h : up_p; }
-    /* line 1: sort by r; R6: nodes without capacity take no part */
+    /* order by r; R6: nodes without capacity take no part */
     int ns = 0;
     for (int i = 0; i < len; ++i) if (up[i] > 0) srt[ns++] = i;
     g_sort_r = r_in; g_sort_id = ids;
@@ -408,33 +413,33 @@ int orc_pbupdate_alg3(int len, const int32_t *ids, const uint64_t *r_in, int h, 
     pstart[s] = ns;
     /* A holds V_i (the current plateau, with the merged lower plateaus) */
     int na = 0;
-    int i = 0;                                               /* line 6 (0-based) */
-    while (nC > 0 && i < s) {                                /* line 7 */
+    int i = 0;                                               /* lowest plateau */
+    while (nC > 0 && i < s) {                                /* units left to give */
         for (int j = pstart[i]; j < pstart[i + 1]; ++j) A[na++] = srt[j];
         uint64_t gap = (i + 1 >= s) ? UINT64_MAX
-                       : r_in[srt[pstart[i + 1]]] - r_in[srt[pstart[i]]];   /* line 8 */
-        while (nC > 0 && gap > 0 && na > 0) {                /* line 9 */
+                       : r_in[srt[pstart[i + 1]]] - r_in[srt[pstart[i]]];   /* distance to the next level */
+        while (nC > 0 && gap > 0 && na > 0) {                /* rounds on this plateau */
             uint64_t mu = UINT64_MAX;
             for (int j = 0; j < na; ++j) if (up[A[j]] < mu) mu = up[A[j]];
-            uint64_t w = mu;                                 /* line 10 */
+            uint64_t w = mu;                                 /* round size: min(cap, gap, n_C / |A|) */
             if (gap < w) w = gap;
             if (nC / (uint64_t)na < w) w = nC / (uint64_t)na;
-            if (w > 0) {                                     /* lines 11-14 */
+            if (w > 0) {                                     /* w units to every node of A */
                 for (int j = 0; j < na; ++j) { r[A[j]] += w; up[A[j]] -= w; }
                 nC -= w * (uint64_t)na;
                 if (gap != UINT64_MAX) gap -= w;
-            } else {                                         /* lines 15-17 (R2) */
+            } else {                                         /* fewer units than nodes (R2) */
                 g_sort_id = ids;
                 qsort(A, (size_t)na, sizeof(int), cmp_by_id);
                 for (uint64_t j = 0; j < nC; ++j) { r[A[j]] += 1; up[A[j]] -= 1; }
                 nC = 0;
             }
-            int q = 0;                                       /* line 18 */
+            int q = 0;                                       /* drop the capped nodes */
             for (int j = 0; j < na; ++j) if (up[A[j]] > 0) A[q++] = A[j];
             na = q;
         }
-        /* line 19: what is left of V_i joins V_{i+1} (kept in A) */
-        i++;                                                 /* line 20 */
+        /* what is left of the plateau joins the next one (kept in A) */
+        i++;
     }
     int rc = nC == 0 ? ORC_OK : ORC_OVERFLOW;
     for (int j = 0; j < len; ++j) delta[j] = r[j] - r_in[j];
@@ -612,8 +617,8 @@ int orc_fw_sync(int64_t n, int64_t npairs, const int64_t *pair_off, const int32_
     return rc;
 }
 
-/* Sequential iterations: Alg. 2 line 4 updates r in place, pair by pair in */
-/* array order.                                                             */
+/* Sequential iterations: Alg. 2 as printed updates r in place, pair by    */
+/* pair, here in array order.                                               */
 int orc_fw_seq(int64_t n, int64_t npairs, const int64_t *pair_off, const int32_t *nodes,
                const int32_t *hcnt, int k, int T, uint64_t *r) {
     (void)n;
@@ -675,7 +680,7 @@ void orc_fw_cliques(int64_t c, const int32_t *cl, int k, int T, uint64_t *r) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* O5: extraction (Alg. 2 lines 5-7, R4, R5).                               */
+/* O5: extraction (the final sort and prefix step of Alg. 2, R4, R5).      */
 /* ------------------------------------------------------------------------ */
 static const double *g_key_d;
 static int cmp_desc_d(const void *a, const void *b) {

@@ -1,5 +1,5 @@
-// extract.cu -- step A6: the densest prefix of the nodes sorted by r
-// (Alg. 2 lines 5-7).
+// extract.cu -- step A6: the densest prefix of the nodes sorted by r (the
+// final sort and prefix step of Alg. 2).
 //
 // 1. Sort V by r non-increasing, ties by ascending id: a stable LSD radix sort
 //    of key = max(r) - r over ids 0..n-1 (key bits of the float / double

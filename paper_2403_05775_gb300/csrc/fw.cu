@@ -10,11 +10,11 @@
 // PBUpdate of one pair (Alg. 3): n_C = C(p, k-h) units; V_h nodes may take up
 // to C(p, k-h), V_p nodes up to C(p-1, k-h-1) (C3-C4 of SCT-CP, Lemma 2.6).
 // Starting from the lowest plateau of r, the current plateau is raised by
-// w = min(smallest remaining cap, gap to the next plateau, floor(n_C/|V_i|))
-// (line 10); capped nodes leave (line 18); a plateau that reaches the next
-// one merges with it (line 19); when floor(n_C/|V_i|) = 0 the remaining
-// units go one each to the lowest-id nodes of the plateau (lines 15-17, with
-// "random" read as "lowest id").  Nodes with zero cap never take part.
+// w = min(smallest remaining cap, gap to the next plateau, floor(n_C/|V_i|));
+// capped nodes leave; a plateau that reaches the next one merges with it;
+// when floor(n_C/|V_i|) = 0 the remaining units go one each to the lowest-id
+// nodes of the plateau (the paper picks them at random; the lowest ids make
+// the result deterministic).  Nodes with zero cap never take part.
 //
 // GPU mapping: a pair is handled by a group of G lanes (G = 8 or 32 by length
 // class), each lane holding NPL node slots in registers; node j of the pair
@@ -346,7 +346,8 @@ __device__ __forceinline__ void warp_seg_add(int32_t id, V x, V *gacc) {
 // the next level m2.  With w = floor(n_C/|A|) and R = n_C - w|A|, the walk of
 // Alg. 3 ends on this plateau exactly when no node of A reaches its cap and
 // the plateau does not reach m2: w < min(cap, m2 - m1) (w <= when R = 0).
-// Then every node of A takes w and the R lowest ids one more (lines 10-17).
+// Then every node of A takes w and the R lowest ids one more (one round of
+// Alg. 3 plus its remainder step).
 // The other pairs (several plateaus or a cap inside the fill) are appended
 // to `slow`.
 constexpr int FA_WARPS = 4;

@@ -20,13 +20,11 @@ import test_oracle_pins as P
 
 MUTANTS = {
     "pivot_cap_drops_the_minus_one": (
-        "uint64_t up_p = orc_binom(p - 1, k - h - 1, &ovf);       /* line 5 */",
-        "uint64_t up_p = orc_binom(p, k - h - 1, &ovf);       /* line 5 */"),
+        "uint64_t up_p = orc_binom(p - 1, k - h - 1, &ovf);",
+        "uint64_t up_p = orc_binom(p, k - h - 1, &ovf);"),
     "zero_cap_nodes_kept_in_plateaus": (
-        "/* line 1: sort by r; R6: nodes without capacity take no part */\n"
-        "    int ns = 0;\n    for (int i = 0; i < len; ++i) if (up[i] > 0) srt[ns++] = i;",
-        "/* line 1: sort by r; R6: nodes without capacity take no part */\n"
-        "    int ns = 0;\n    for (int i = 0; i < len; ++i) srt[ns++] = i;"),
+        "if (up[i] > 0) srt[ns++] = i;\n    g_sort_r = r_in;",
+        "srt[ns++] = i;\n    g_sort_r = r_in;"),
     "remainder_to_highest_id": (
         "for (uint64_t j = 0; j < nC; ++j) { r[A[j]] += 1; up[A[j]] -= 1; }",
         "for (uint64_t j = 0; j < nC; ++j) { r[A[na - 1 - j]] += 1; up[A[na - 1 - j]] -= 1; }"),

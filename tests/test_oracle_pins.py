@@ -71,7 +71,8 @@ def test_g1_sct_matches_example_2_2():
 
 
 def test_g1_example_3_1_pbupdate_steps():
-    """Example 3.1: P4 then P3 from r = 0 (lines 16 and 13 of Alg. 3)."""
+    """Example 3.1: P4 then P3 from r = 0 (the remainder step, then a whole
+    round of Alg. 3)."""
     r = np.zeros(7, np.uint64)
     for step in ("ex31_step1", "ex31_step2"):
         (hold, piv), = _pairs_from_golden(G[step + "_pair"])
