@@ -206,6 +206,24 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def slowest_rank_ms(dist, local_ms, device):
+    """Max over ranks of the timed region: the whole job ends with its
+    slowest replica.  One rank (or no process group) returns local_ms."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() \
+            or dist.get_world_size() == 1:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, max_ms):
+    """Replicas run the same workload: the job processes world * units in
+    the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def batched_rmat(K, torch, dev, stream, flush, allocator, count=256, T=300, nmax=1e4):
     """The batched workload: 256 R-MAT graphs (a, b, c, d = 0.57, 0.19, 0.19,
     0.05; edge factor 16; planted 30-node clique; k uniform in {3..8}; seed
@@ -339,17 +357,13 @@ def main():
         torch.cuda.synchronize()
     launches = K.kdss_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = slowest_rank_ms(dist if world > 1 else None, sum(step_ms), dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
 
     ck = info["c_k"]
-    units = T * ck * args.steps * world
-    value = units / (total_ms / 1e3)
+    value = whole_job_value(T * ck * args.steps, world, total_ms)
 
     # end to end through the public API with host buffers
     e2e_ms = []
