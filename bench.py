@@ -224,6 +224,59 @@ def whole_job_value(units_per_rank, world, max_ms):
     return units_per_rank * world / (max_ms / 1e3)
 
 
+def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01, every=5):
+    """The serving workload: a Poisson stream (rate 200/s, seed 5) of k-DSS
+    queries on a pool of Chung-Lu graphs (the n = 1e5 workload's generator
+    with n log-uniform in [1e3, 1e6]) with k uniform in {3..10}, through the
+    continuous-batching server: a query stops once its certificate gap is
+    <= 1% (checked every 5 iterations) or at T = 300.  Latency is submit to
+    result; throughput is queries over first submit to last result."""
+    import threading
+    pool = synth.serving_pool(pool_size)
+    arr, gi, ks = synth.serving_stream(count, rate, pool_size)
+    dpool = [(n, torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for n, s, d in pool]
+    torch.cuda.synchronize()
+    tickets = [None] * count
+    with K.Server(precision=PRECISIONS["fp64"], check_every=every, eps_stop=eps) as srv:
+        t0 = time.perf_counter()
+
+        def feed():
+            for i in range(count):
+                dt = arr[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                n, s, d = dpool[gi[i]]
+                tickets[i] = srv.submit(n, s, d, int(ks[i]), T)
+
+        th = threading.Thread(target=feed)
+        th.start()
+        res = []
+        for i in range(count):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            res.append(srv.wait(tickets[i]))
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.array([r["timing"]["latency_ms"] for r in res])
+    ok = [r for r in res if r["status"] == 0]
+    return {
+        "workload": f"{count} queries, Poisson {rate:g}/s, pool of {pool_size} Chung-Lu graphs "
+                    f"(mean degree 20, exponent 2.5, planted 60-node near-clique p=0.9, n "
+                    f"log-uniform in [1e3, 1e6], sum {sum(p[0] for p in pool)}), k in {{3..10}}, "
+                    f"seed 5; stop at gap <= {eps:g} (every {every}) or T = {T}; FP64",
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "throughput_qps": len(res) / wall,
+        "offered_qps": rate, "completed": len(ok), "failed": len(res) - len(ok),
+        "mean_iterations": float(np.mean([r["t_used"] for r in ok])) if ok else 0.0,
+        "stopped_by_gap": sum(1 for r in ok if r["gap"] <= eps),
+        "mean_build_ms": float(np.mean([r["timing"]["build_ms"] for r in res])),
+        "mean_queue_ms": float(np.mean([r["timing"]["queue_ms"] for r in res])),
+        "peak_active": st["peak_active"], "captures": st["captures"], "replays": st["replays"],
+        "peak_resident_bytes": st["peak_resident_bytes"], "hbm_budget": st["hbm_budget"],
+    }
+
+
 def batched_rmat(K, torch, dev, stream, flush, allocator, count=256, T=300, nmax=1e4):
     """The batched workload: 256 R-MAT graphs (a, b, c, d = 0.57, 0.19, 0.19,
     0.05; edge factor 16; planted 30-node clique; k uniform in {3..8}; seed
@@ -458,6 +511,10 @@ def main():
             extras["batched"] = batched_rmat(K, torch, dev, stream, flush, args.allocator)
         except K.KdssError as e:
             extras["batched"] = {"error": str(e)}
+        try:
+            extras["serving"] = serving(K, torch, dev)
+        except K.KdssError as e:
+            extras["serving"] = {"error": str(e)}
         line["extras"] = extras
 
     if rank == 0:

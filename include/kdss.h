@@ -219,7 +219,11 @@ kdss_status kdss_state_timing(const kdss_state *st, kdss_timing *out);
 kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opts *opts,
                          kdss_result *out);
 
-/* kdss_solve -- build, T iterations and extraction in one call. */
+/* kdss_solve -- build, iterations and extraction in one call.  Runs T
+ * iterations; with opts->check_every = j > 0 and opts->eps_stop = eps > 0 it
+ * extracts after every j iterations and stops early once the certificate gap
+ * 1 - rho'_max / max r-hat (Thms 3.5-3.6) is <= eps (out->t_used holds the
+ * iterations run). */
 kdss_status kdss_solve(const kdss_graph_desc *g, int32_t k, int32_t T, const kdss_opts *opts,
                        kdss_result *out);
 
@@ -243,7 +247,8 @@ typedef struct kdss_query {
  *   q[i]   : the query (graph as in kdss_build_sct, k in [2, 64], T >= 0).
  *   out[i] : caller-owned; receives query i's result and status (ids
  *            allocated by the library, freed with kdss_result_free).
- *   opts   : as for kdss_solve (one precision and order for all queries).
+ *   opts   : as for kdss_solve (one precision and order for all queries);
+ *            every query runs its T iterations (no early stop).
  * Results equal kdss_solve's per query: bit for bit for KDSS_INT64 and
  * KDSS_FP64; for KDSS_FP32K the same rule in the same precision (its atomic
  * sums round in the order the hardware performs them, run to run, as in

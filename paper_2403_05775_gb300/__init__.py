@@ -68,6 +68,24 @@ class kdss_result(C.Structure):
                 ("t_used", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
+class kdss_server_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("order", C.c_int32), ("check_every", C.c_int32),
+                ("max_active", C.c_int32), ("eps_stop", C.c_double), ("hbm_budget", C.c_int64)]
+
+
+class kdss_query_timing(C.Structure):
+    _fields_ = [("queue_ms", C.c_double), ("build_ms", C.c_double), ("wait_ms", C.c_double),
+                ("iterate_ms", C.c_double), ("latency_ms", C.c_double), ("iterations", C.c_int32),
+                ("peak_batch", C.c_int32), ("resident_bytes", C.c_int64)]
+
+
+class kdss_server_stats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("submitted", "completed", "failed", "pending", "active",
+                                        "resident_bytes", "peak_resident_bytes", "hbm_budget",
+                                        "replays", "captures")] + \
+               [("peak_active", C.c_int32), ("reserved", C.c_int32)]
+
+
 class kdss_timing(C.Structure):
     _fields_ = [("fw_kernel_ms", C.c_double), ("step_kernel_ms", C.c_double),
                 ("fw_launches", C.c_int64), ("step_launches", C.c_int64)]
@@ -126,6 +144,11 @@ def load(build_if_missing: bool = False):
             "kdss_version": (C.c_char_p, []),
             "kdss_kernel_launches": (i64, []),
             "kdss_fw_iterate_noalloc": (i32, [vp, vp, i32, i32, vp]),
+            "kdss_server_create": (i32, [P(kdss_server_opts), P(vp)]),
+            "kdss_server_submit": (i32, [vp, P(kdss_query), P(i64)]),
+            "kdss_server_wait": (i32, [vp, i64, i32, P(kdss_result), P(kdss_query_timing)]),
+            "kdss_server_get_stats": (i32, [vp, P(kdss_server_stats)]),
+            "kdss_server_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -403,3 +426,68 @@ def kdss_fw_iterate_noalloc(s: Sct, r_dev, t_done: int, T: int, stream=None) -> 
         stream = stream.cuda_stream
     _check(load().kdss_fw_iterate_noalloc(s.ptr, C.c_void_p(ptr), int(t_done), int(T),
                                           C.c_void_p(stream or None)))
+
+
+# ---------------------------------------------------------------------------
+# query server (include/kdss_server.h)
+# ---------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server: submit() queues a query and returns its
+    ticket, wait() returns the result dict with a ``timing`` entry."""
+
+    def __init__(self, precision=KDSS_INT64, order=KDSS_ORDER_PEEL, check_every=5,
+                 eps_stop=0.0, max_active=0, hbm_budget=0):
+        L = load()
+        o = kdss_server_opts(precision=precision, order=order, check_every=check_every,
+                             max_active=max_active, eps_stop=eps_stop, hbm_budget=int(hbm_budget))
+        p = C.c_void_p()
+        _check(L.kdss_server_create(C.byref(o), C.byref(p)))
+        self.ptr = p
+
+    def submit(self, n, src, dst, k, T) -> int:
+        g, keep = _graph_desc(n, src, dst)
+        q = kdss_query()
+        q.graph, q.k, q.T = g, int(k), int(T)
+        t = C.c_int64()
+        _check(load().kdss_server_submit(self.ptr, C.byref(q), C.byref(t)))
+        del keep          # the server copied the edge list
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        L = load()
+        r = kdss_result()
+        tm = kdss_query_timing()
+        rc = L.kdss_server_wait(self.ptr, int(ticket), int(timeout_ms), C.byref(r), C.byref(tm))
+        if rc == KDSS_ERR_TIMEOUT or rc == KDSS_ERR_INVALID_ARG:
+            _check(rc)
+        try:
+            out = _result_dict(r)
+        finally:
+            L.kdss_result_free(C.byref(r))
+        out["status"] = int(rc)
+        out["message"] = (L.kdss_last_error() or b"").decode()
+        out["timing"] = {f: getattr(tm, f) for f, _ in kdss_query_timing._fields_}
+        return out
+
+    def stats(self) -> dict:
+        st = kdss_server_stats()
+        _check(load().kdss_server_get_stats(self.ptr, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in kdss_server_stats._fields_ if f != "reserved"}
+
+    def close(self):
+        if self.ptr:
+            load().kdss_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

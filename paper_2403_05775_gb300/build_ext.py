@@ -38,7 +38,7 @@ def sources():
 
 def _deps():
     return (sources() + glob.glob(os.path.join(CSRC, "*.cuh"))
-            + [os.path.join(INCLUDE, "kdss.h"), os.path.abspath(__file__)])
+            + sorted(glob.glob(os.path.join(INCLUDE, "*.h"))) + [os.path.abspath(__file__)])
 
 
 def _stale(target, deps):

@@ -2,6 +2,7 @@
 //
 // Every entry point converts internal exceptions into a kdss_status and a
 // thread-local message; nothing throws across the boundary.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -282,7 +283,26 @@ kdss_status kdss_solve(const kdss_graph_desc *g, int32_t k, int32_t T, const kds
     kdss_sct *s = nullptr;
     kdss_state *st = nullptr;
     kdss_status rc = kdss_build_sct(g, k, opts, &s);
-    if (rc == KDSS_OK) rc = kdss_fw_iterate(s, &st, T, opts);
+    const int32_t every = opts ? opts->check_every : 0;
+    const double eps = opts ? opts->eps_stop : 0.0;
+    if (rc == KDSS_OK && every > 0 && eps > 0.0 && T > 0) {
+        // stop rule: the certificate gap after every `every` iterations
+        int32_t t = 0;
+        while (rc == KDSS_OK && t < T) {
+            const int32_t j = std::min(every, T - t);
+            rc = kdss_fw_iterate(s, &st, j, opts);
+            t += j;
+            if (rc != KDSS_OK || t >= T) break;
+            kdss_result chk;
+            memset(&chk, 0, sizeof chk);
+            rc = kdss_extract(s, st, opts, &chk);
+            const bool stop = rc == KDSS_OK && chk.gap <= eps;
+            kdss_result_free(&chk);
+            if (stop) break;
+        }
+    } else if (rc == KDSS_OK) {
+        rc = kdss_fw_iterate(s, &st, T, opts);
+    }
     if (rc == KDSS_OK) rc = kdss_extract(s, st, opts, out);
     if (rc == KDSS_OK) out->T = T;
     out->status = rc;

@@ -1141,7 +1141,7 @@ long long capture(const Ctx &c, cudaGraphExec_t *exec, F fn) {
     KDSS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     Ctx cc = c;
     cc.stream = cap;
-    const long long before = launches();
+    const long long before = thread_launches();
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -1155,7 +1155,7 @@ long long capture(const Ctx &c, cudaGraphExec_t *exec, F fn) {
         }
         e = cudaStreamEndCapture(cap, &g);
     }
-    const long long nk = launches() - before;
+    const long long nk = thread_launches() - before;
     add_launches(-nk);  // captured, not run
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);

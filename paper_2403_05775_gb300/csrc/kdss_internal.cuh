@@ -29,6 +29,7 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 // Every kernel launch is followed by KDSS_LAUNCH_CHECK(), which also counts it.
 void count_launch();
 long long launches();               // kernels launched so far (process-wide)
+long long thread_launches();        // kernels launched so far by the calling thread
 void add_launches(long long d);     // graph replays add the kernels they run
 #define KDSS_LAUNCH_CHECK() \
     (::kdss::count_launch(), ::kdss::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))

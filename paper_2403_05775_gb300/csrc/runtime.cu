@@ -8,8 +8,13 @@
 namespace kdss {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // this thread's launches (graph capture counts)
+void count_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
+long long thread_launches() { return t_launches; }
 void add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 
 void fail(kdss_status code, const std::string &msg) { throw Error{code, msg}; }

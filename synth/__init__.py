@@ -112,7 +112,7 @@ def _plant(n: int, size: int, prob: float, seed: int, stream_pick: int,
 
 
 def chung_lu(n: int, mean_degree: float, beta: float, seed: int,
-             plant_size: int = 0, plant_prob: float = 1.0):
+             plant_size: int = 0, plant_prob: float = 1.0, use_c: bool = True):
     """Chung-Lu power-law graph.
 
     Weights w_i = (i+1)^(-1/(beta-1)), scaled to mean ``mean_degree`` and
@@ -129,10 +129,19 @@ def chung_lu(n: int, mean_degree: float, beta: float, seed: int,
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
     m = int(round(n * mean_degree / 2.0))
-    ua = uniforms(seed, 0, 0, m)
-    ub = uniforms(seed, 1, 0, m)
-    a = np.minimum(np.searchsorted(cdf, ua, side="right"), n - 1)
-    b = np.minimum(np.searchsorted(cdf, ub, side="right"), n - 1)
+    L = _rmat_lib() if use_c else None
+    if L is None:
+        ua = uniforms(seed, 0, 0, m)
+        ub = uniforms(seed, 1, 0, m)
+        a = np.minimum(np.searchsorted(cdf, ua, side="right"), n - 1)
+        b = np.minimum(np.searchsorted(cdf, ub, side="right"), n - 1)
+    else:   # the C twin of the three lines above
+        import os
+        cdf = np.ascontiguousarray(cdf, np.float64)
+        a = np.empty(m, np.int64)
+        b = np.empty(m, np.int64)
+        L.synth_chunglu_draws(stream_seed(seed, 0), stream_seed(seed, 1), m, cdf.ctypes.data, n,
+                              a.ctypes.data, b.ctypes.data, min(os.cpu_count() or 1, 64))
     nodes, pa, pb = _plant(n, plant_size, plant_prob, seed, 2, 3)
     src = np.concatenate([a, pa])
     dst = np.concatenate([b, pb])
@@ -165,6 +174,9 @@ def _rmat_lib():
             L.synth_rmat_block.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_int, C.c_double,
                                            C.c_double, C.c_double, C.c_int64, C.c_void_p,
                                            C.c_void_p, C.c_int]
+            L.synth_chunglu_draws.restype = None
+            L.synth_chunglu_draws.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_void_p,
+                                              C.c_int64, C.c_void_p, C.c_void_p, C.c_int]
             _clib = L
         except (OSError, subprocess.CalledProcessError):
             _clib = False
@@ -270,3 +282,27 @@ def batch_rmat_graph(i: int, n: int, seed: int = 3):
     n, s, d, _ = rmat(int(n), 16, seed, plant_size=30, plant_prob=1.0,
                       stream_base=100 + 4 * i)
     return n, s, d
+
+
+def serving_pool(count: int = 32, seed: int = 5, nmin=1e3, nmax=1e6):
+    """Graphs of the serving workload: the Chung-Lu generator of the n = 1e5
+    workload (mean degree 20, exponent 2.5, planted 60-node near-clique at
+    p = 0.9) with n log-uniform in [nmin, nmax] (stream 20 of ``seed``);
+    graph i draws from seed * 1000 + i."""
+    un = uniforms(seed, 20, 0, count)
+    ns = np.rint(np.exp(np.log(nmin) + un * (np.log(nmax) - np.log(nmin)))).astype(np.int64)
+    out = []
+    for i, n in enumerate(ns):
+        n, s, d, _ = chung_lu(int(n), 20.0, 2.5, seed * 1000 + i, plant_size=60, plant_prob=0.9)
+        out.append((n, s, d))
+    return out
+
+
+def serving_stream(count: int, rate: float, pool_size: int, seed: int = 5):
+    """Arrival times (s) of a Poisson stream of ``rate`` queries/s
+    (exponential gaps, stream 21), the pool graph of each query (stream 22)
+    and its k, uniform in {3..10} (stream 23)."""
+    gaps = -np.log1p(-uniforms(seed, 21, 0, count)) / rate
+    g = np.minimum((uniforms(seed, 22, 0, count) * pool_size).astype(np.int64), pool_size - 1)
+    k = 3 + np.minimum((uniforms(seed, 23, 0, count) * 8).astype(np.int64), 7)
+    return np.cumsum(gaps), g, k

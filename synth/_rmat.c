@@ -82,3 +82,56 @@ int64_t synth_rmat_block(uint64_t sseed, uint64_t base, int64_t cnt, int scale, 
     }
     return w;
 }
+
+/* Chung-Lu endpoint draws, identical to synth.chung_lu's numpy path: draw j
+ * takes the uniforms number j of the two streams (seeds sa, sb) and maps each
+ * by inverse CDF: the count of cdf entries <= u (numpy searchsorted, side
+ * 'right'), clipped to n - 1. */
+typedef struct {
+    uint64_t sa, sb;
+    int64_t lo, hi, n;
+    const double *cdf;
+    int64_t *a, *b;
+} CLJob;
+
+static inline int64_t upper(const double *cdf, int64_t n, double u) {
+    int64_t lo = 0, hi = n;  /* first index with cdf > u */
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (cdf[mid] <= u) lo = mid + 1; else hi = mid;
+    }
+    return lo < n - 1 ? lo : n - 1;
+}
+
+static void *run_cl(void *p) {
+    CLJob *J = (CLJob *)p;
+    for (int64_t j = J->lo; j < J->hi; ++j) {
+        const uint64_t xa = mix64(J->sa + ((uint64_t)j + 1ull) * GAMMA);
+        const uint64_t xb = mix64(J->sb + ((uint64_t)j + 1ull) * GAMMA);
+        J->a[j] = upper(J->cdf, J->n, (double)(xa >> 11) * 0x1p-53);
+        J->b[j] = upper(J->cdf, J->n, (double)(xb >> 11) * 0x1p-53);
+    }
+    return NULL;
+}
+
+void synth_chunglu_draws(uint64_t sa, uint64_t sb, int64_t m, const double *cdf, int64_t n,
+                         int64_t *a, int64_t *b, int nthreads) {
+    enum { MAXT = 128 };
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > MAXT) nthreads = MAXT;
+    if (m < 4096) nthreads = 1;
+    CLJob jobs[MAXT];
+    pthread_t th[MAXT];
+    int started[MAXT];
+    for (int t = 0; t < nthreads; ++t) {
+        CLJob *J = &jobs[t];
+        J->sa = sa; J->sb = sb; J->n = n; J->cdf = cdf; J->a = a; J->b = b;
+        J->lo = m * t / nthreads; J->hi = m * (t + 1) / nthreads;
+        started[t] = t > 0 && pthread_create(&th[t], NULL, run_cl, J) == 0;
+    }
+    run_cl(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) {
+        if (started[t]) pthread_join(th[t], NULL);
+        else run_cl(&jobs[t]);
+    }
+}

@@ -11,11 +11,12 @@ import pytest
 import paper_2403_05775_gb300 as K
 from paper_2403_05775_gb300 import build_ext
 
-HEADER = os.path.join(build_ext.INCLUDE, "kdss.h")
+HEADERS = sorted(os.path.join(build_ext.INCLUDE, f) for f in os.listdir(build_ext.INCLUDE)
+                 if f.endswith(".h"))
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(kdss_[a-z_0-9]+)\s*\(", text)) - {"kdss_alloc_fn", "kdss_free_fn"})
 
@@ -30,7 +31,7 @@ def test_library_exports_every_declared_entry_point(lib):
     names = declared_functions()
     assert len(names) >= 16
     for name in names:
-        assert hasattr(lib, name), f"{name} declared in kdss.h but not exported"
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
     out = subprocess.run(["nm", "-D", "--defined-only", build_ext.LIB], capture_output=True,
                          text=True).stdout
     exported = set(re.findall(r" T (kdss_\w+)", out))
@@ -43,18 +44,22 @@ def test_binding_loads_and_reports_version():
 
 def test_struct_layouts_match_the_header(tmp_path):
     src = tmp_path / "sizes.c"
-    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kdss.h"\n'
-                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kdss_server.h"\n'
+                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
                    "sizeof(kdss_opts), sizeof(kdss_graph_desc), sizeof(kdss_sct_stats),"
                    "sizeof(kdss_result), sizeof(kdss_timing), sizeof(kdss_query),"
-                   "offsetof(kdss_result, status), offsetof(kdss_opts, stream));return 0;}\n")
+                   "offsetof(kdss_result, status), offsetof(kdss_opts, stream),"
+                   "sizeof(kdss_server_opts), sizeof(kdss_query_timing),"
+                   "sizeof(kdss_server_stats));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", build_ext.INCLUDE, "-o", str(exe), str(src)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(K.kdss_opts), ctypes.sizeof(K.kdss_graph_desc),
             ctypes.sizeof(K.kdss_sct_stats), ctypes.sizeof(K.kdss_result),
             ctypes.sizeof(K.kdss_timing), ctypes.sizeof(K.kdss_query),
-            K.kdss_result.status.offset, K.kdss_opts.stream.offset]
+            K.kdss_result.status.offset, K.kdss_opts.stream.offset,
+            ctypes.sizeof(K.kdss_server_opts), ctypes.sizeof(K.kdss_query_timing),
+            ctypes.sizeof(K.kdss_server_stats)]
     assert got == want
 
 

@@ -14,6 +14,14 @@ def test_rmat_c_twin_equals_the_numpy_definition():
             assert np.array_equal(x, y), (n, ef, sb)
 
 
+def test_chung_lu_c_twin_equals_the_numpy_definition():
+    for n, md, seed in [(50, 4.0, 1), (3000, 12.0, 9), (100000, 20.0, 2)]:
+        a = synth.chung_lu(n, md, 2.5, seed, plant_size=20, plant_prob=0.9)
+        b = synth.chung_lu(n, md, 2.5, seed, plant_size=20, plant_prob=0.9, use_c=False)
+        for x, y in zip(a[1:], b[1:]):
+            assert np.array_equal(x, y), (n, md, seed)
+
+
 def test_rmat_shape():
     n, s, d, planted = synth.rmat(5000, 16, 3, plant_size=30, plant_prob=1.0, stream_base=100)
     assert s.dtype == np.int32 and s.size == d.size >= 16 * 5000
