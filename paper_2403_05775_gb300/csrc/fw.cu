@@ -80,6 +80,38 @@ template <>
 __device__ __forceinline__ uint64_t load_r<double>(const double *r, int32_t id) {
     return (uint64_t)__ldg(r + id);
 }
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes): the data
+// does not pass through registers, so a lane can have every copy of a tile in
+// flight at once.  Completion is awaited per thread; a __syncwarp() then
+// publishes the warp's copies to all its lanes.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Integer value of a double that holds an integer in [0, 2^53), from its bit
+// pattern with integer operations only.  Non-negative doubles order like
+// their bit patterns, so comparisons may use the raw word; only levels that
+// enter arithmetic are converted.
+template <class RT>
+__device__ __forceinline__ uint64_t level_of(uint64_t w);
+template <>
+__device__ __forceinline__ uint64_t level_of<uint64_t>(uint64_t w) { return w; }
+template <>
+__device__ __forceinline__ uint64_t level_of<double>(uint64_t w) {
+    const int e = (int)(w >> 52) - 1023;  // 0.0 gives e < 0
+    if (e < 0) return 0ull;
+    const uint64_t m = (w & ((1ull << 52) - 1)) | (1ull << 52);
+    return e >= 52 ? (m << (e - 52)) : (m >> (52 - e));
+}
+
 // ---------------------------------------------------------------------------
 // Block-local aggregation of the scatter-adds.  Most pairs hand their units
 // to a few low-r nodes (on a power-law graph with a planted dense region,
@@ -339,8 +371,10 @@ __device__ __forceinline__ void warp_seg_add(int32_t id, V x, V *gacc) {
 }
 
 // First step of Alg. 3 for pairs of at most 32 nodes.  A warp takes 32
-// consecutive pairs: their node ids are read with coalesced loads and their
-// r values gathered in parallel into shared memory (bit 63 marks V_h nodes);
+// consecutive pairs: their node ids are copied to shared memory (coalesced)
+// and then the r words they address (gathers), both as asynchronous copies so
+// that all loads of the tile are in flight at once (the FP32 twin gathers
+// through registers, its 4-byte words with the V_h mark in the sign bit);
 // then lane i streams pair i from shared memory, finding the lowest level m1
 // among the nodes that can receive, the set A of nodes at m1 (slot mask) and
 // the next level m2.  With w = floor(n_C/|A|) and R = n_C - w|A|, the walk of
@@ -352,7 +386,6 @@ __device__ __forceinline__ void warp_seg_add(int32_t id, V x, V *gacc) {
 // to `slow`.
 constexpr int FA_WARPS = 4;
 constexpr int FA_CAP = 32 * 32;
-constexpr uint64_t VHOLD = 1ull << 63;
 
 template <class RT>
 __global__ void __launch_bounds__(FA_WARPS * 32)
@@ -360,12 +393,14 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
           const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
           const RT *__restrict__ r, RT *acc, const uint64_t *__restrict__ binom, int bcols,
           int k, int32_t *slow, int *slow_count, int *err) {
+    __shared__ int32_t sidv[FA_WARPS][FA_CAP];
     __shared__ uint64_t sval[FA_WARPS][FA_CAP];
     using AV = typename AccV<RT>::T;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t np = p_end - p_begin;
     const int64_t ntile = (np + 31) >> 5;
     uint64_t *sv = sval[wib];
+    int32_t *sid = sidv[wib];
     for (int64_t tile = blockIdx.x * (int64_t)FA_WARPS + wib; tile < ntile;
          tile += (int64_t)gridDim.x * FA_WARPS) {
         const int64_t qi = tile * 32 + lane;
@@ -380,13 +415,13 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
             if (lane == 0) atomicOr(err, DERR_CAPACITY);
             continue;
         }
-        // stage: coalesced ids, parallel gathers
-#pragma unroll 4
-        for (int i = lane; i < cnt; i += 32) {
-            const int32_t raw = __ldg(nodes + B + i);
-            const uint64_t v = load_r<RT>(r, raw & 0x7fffffff);
-            sv[i] = raw < 0 ? (v | VHOLD) : v;
-        }
+        // stage: the tile's ids (coalesced), then the r words they address,
+        // both as asynchronous copies
+        for (int i = lane; i < cnt; i += 32) cp_async4(sid + i, nodes + B + i);
+        cp_async_wait_all();
+        __syncwarp();
+        for (int i = lane; i < cnt; i += 32) cp_async8(sv + i, r + (sid[i] & 0x7fffffff));
+        cp_async_wait_all();
         __syncwarp();
         uint32_t rmask = 0;     // receivers (slot bits)
         uint64_t w = 0, R = 0;
@@ -399,22 +434,32 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
             const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
             const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
                                        ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+            // one branch-free pass over the raw r words (ordered like the
+            // levels): lowest level m1 among the nodes that can receive, its
+            // node set (mask1, whether it holds a pivot node) and the next
+            // level m2.  A pivot node of zero cap (|V_h| = k) reads as ~0 and
+            // never receives; hold nodes always can (n_C >= 1).
+            const uint64_t pm = cap_p > 0 ? 0ull : ~0ull;
             uint64_t m1 = ~0ull, m2 = ~0ull;
-            uint32_t mask1 = 0, holdm = 0;
+            uint32_t mask1 = 0;
+            bool piv1 = false;
             for (int s = 0; s < len; ++s) {
                 const uint64_t e = sv[o + s];
-                const bool hold = (e & VHOLD) != 0;
-                if (hold) holdm |= 1u << s;
-                if (hold ? nC == 0 : cap_p == 0) continue;  // zero cap: never receives
-                const uint64_t v = e & ~VHOLD;
-                if (v < m1) { m2 = m1; m1 = v; mask1 = 1u << s; }
-                else if (v == m1) mask1 |= 1u << s;
-                else if (v < m2) m2 = v;
+                const bool hold = sid[o + s] < 0;
+                const uint64_t v = e | (hold ? 0ull : pm);
+                const bool lt = v < m1;
+                const bool eq = v == m1 && v != ~0ull;
+                const uint64_t mn = v < m2 ? v : m2;
+                m2 = lt ? m1 : (eq ? m2 : mn);
+                m1 = lt ? v : m1;
+                const uint32_t bit = 1u << s;
+                mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                piv1 = lt ? !hold : (piv1 || (eq && !hold));
             }
             if (mask1) {
                 const uint64_t na = (uint64_t)__popc(mask1);
-                const uint64_t mu = (mask1 & ~holdm) ? cap_p : nC;
-                const uint64_t gap = m2 == ~0ull ? ~0ull : m2 - m1;
+                const uint64_t mu = piv1 ? cap_p : nC;
+                const uint64_t gap = m2 == ~0ull ? ~0ull : level_of<RT>(m2) - level_of<RT>(m1);
                 w = nC / na;
                 R = nC - w * na;
                 const uint64_t lim = mu < gap ? mu : gap;
@@ -437,13 +482,13 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
                 const uint64_t dl = w + (rank < R ? 1ull : 0ull);
                 ++rank;
                 if (dl) {
-                    rid = __ldg(nodes + B + o + sl) & 0x7fffffff;
+                    rid = sid[o + sl] & 0x7fffffff;
                     amount = (AV)dl;
                 }
             }
             warp_seg_add<AV>(rid, amount, (AV *)acc);
         }
-        __syncwarp();  // sv is rewritten by the next tile
+        __syncwarp();  // sv and sid are rewritten by the next tile
     }
 }
 
@@ -691,21 +736,27 @@ k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
             const float cap_p = (p >= 1 && k - h - 1 >= 0)
                                     ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
                                     : 0.f;
+            // branch-free pass as in k_pb_fast; zero-cap pivot nodes read as +inf
+            const bool prx = cap_p > 0.f;
             float m1 = INF, m2 = INF;
-            uint32_t mask1 = 0, holdm = 0;
+            uint32_t mask1 = 0;
+            bool piv1 = false;
             for (int s2 = 0; s2 < len; ++s2) {
                 const float e = sv[o + s2];
                 const bool hold = signbit(e);
-                if (hold) holdm |= 1u << s2;
-                if (hold ? !(nC > 0.f) : !(cap_p > 0.f)) continue;
-                const float v = fabsf(e);
-                if (v < m1) { m2 = m1; m1 = v; mask1 = 1u << s2; }
-                else if (v == m1) mask1 |= 1u << s2;
-                else if (v < m2) m2 = v;
+                const float v = (hold || prx) ? fabsf(e) : INF;
+                const bool lt = v < m1;
+                const bool eq = v == m1 && v < INF;
+                const float mn = fminf(m2, v);
+                m2 = lt ? m1 : (eq ? m2 : mn);
+                m1 = lt ? v : m1;
+                const uint32_t bit = 1u << s2;
+                mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                piv1 = lt ? !hold : (piv1 || (eq && !hold));
             }
             if (mask1) {
                 const float na = (float)__popc(mask1);
-                const float mu = (mask1 & ~holdm) ? cap_p : nC;
+                const float mu = piv1 ? cap_p : nC;
                 share = nC / na;
                 if (share <= mu && share <= m2 - m1) {
                     rmask = mask1;
