@@ -78,7 +78,11 @@ __device__ __forceinline__ uint64_t load_r<uint64_t>(const uint64_t *r, int32_t 
 }
 template <>
 __device__ __forceinline__ uint64_t load_r<double>(const double *r, int32_t id) {
-    return (uint64_t)__ldg(r + id);
+    const uint64_t w = __ldg(reinterpret_cast<const unsigned long long *>(r) + id);
+    const int e = (int)(w >> 52) - 1023;  // integer value of the double, integer ops only
+    if (e < 0) return 0ull;
+    const uint64_t m = (w & ((1ull << 52) - 1)) | (1ull << 52);
+    return e >= 52 ? (m << (e - 52)) : (m >> (52 - e));
 }
 // Asynchronous global -> shared copies (cp.async, 4 or 8 bytes): the data
 // does not pass through registers, so a lane can have every copy of a tile in
@@ -504,6 +508,7 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
 // a warp reduction, and L* = b + floor((n_C - g(b)) / s(b)) lies before the
 // next breakpoint.  Remainder ranks come from a ballot (lanes are in id order).
 constexpr int SB_WARPS = 8;
+constexpr int SB_ROUNDS = 24;
 
 template <class RT>
 __global__ void __launch_bounds__(SB_WARPS * 32)
@@ -541,19 +546,66 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
             cj = raw < 0 ? nC : cap_p;
         }
         // levels relative to the lowest node that can receive: 32-bit when
-        // the spread and n_C fit in 31 bits (the usual case)
-        uint64_t base = cj > 0 ? rj : ~0ull, top = cj > 0 ? rj : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t ob = __shfl_xor_sync(FULL_, base, o), ot = __shfl_xor_sync(FULL_, top, o);
-            base = ob < base ? ob : base;
-            top = ot > top ? ot : top;
-        }
+        // the spread and n_C fit in 31 bits (the usual case).  64-bit min and
+        // max as two 32-bit warp reductions (high word, then low word).
+        const uint64_t vb = cj > 0 ? rj : ~0ull, vt = cj > 0 ? rj : 0ull;
+        const uint32_t bh = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32));
+        const uint32_t bl = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32) == bh ? (uint32_t)vb : 0xffffffffu);
+        const uint32_t th = __reduce_max_sync(FULL_, (uint32_t)(vt >> 32));
+        const uint32_t tl = __reduce_max_sync(FULL_, (uint32_t)(vt >> 32) == th ? (uint32_t)vt : 0u);
+        const uint64_t base = ((uint64_t)bh << 32) | bl, top = ((uint64_t)th << 32) | tl;
         if (top - base < (1ull << 31) && nC < (1ull << 31)) {
+            const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
+            // The walk of Alg. 3 with warp-uniform state: at water level L the
+            // receiving nodes are those with rl <= L < rl + cl; the level rises
+            // to the next event (a node's level, or a receiving node's level
+            // plus cap) while the units last, and stops at
+            // L* = L + floor(rem / na) with R = rem mod na units left for the
+            // lowest ids receiving at L*.  A level where every node is capped
+            // jumps to the next node.  Pairs that cross more than SB_ROUNDS
+            // events take the closed form below.
+            {
+                const uint32_t nC32 = (uint32_t)nC, INF32 = 0xffffffffu;
+                uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
+                bool done = false;
+                for (int round = 0; round < SB_ROUNDS; ++round) {
+                    const bool act = cl > 0 && rl <= L && L - rl < cl;
+                    const uint32_t na = (uint32_t)__popc(__ballot_sync(FULL_, act));
+                    const uint32_t e1 = (cl > 0 && rl > L) ? rl : INF32;
+                    const uint32_t e2 = act ? rl + cl : INF32;
+                    const uint32_t ev = __reduce_min_sync(FULL_, e1 < e2 ? e1 : e2);
+                    if (na == 0) {
+                        if (ev == INF32) break;
+                        L = ev;
+                        continue;
+                    }
+                    const uint32_t qd = rem / na;
+                    if (ev == INF32 || qd < ev - L) {
+                        Ls = L + qd;
+                        R = rem - qd * na;
+                        done = true;
+                        break;
+                    }
+                    rem -= (ev - L) * na;
+                    L = ev;
+                }
+                if (done) {
+                    uint32_t dj = 0;
+                    bool elig = false;
+                    if (cl > 0) {
+                        if (Ls > rl) dj = min(Ls - rl, cl);
+                        elig = rl <= Ls && Ls - rl < cl;
+                    }
+                    const unsigned eb = __ballot_sync(FULL_, elig);
+                    if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+                    if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+                    __syncwarp();
+                    continue;
+                }
+            }
             // (level, cap) of every node as one 64-bit word; a zero cap adds
             // nothing below (min(d, 0) = 0), so no special case
             uint2 *sp = (uint2 *)sr[wib];
-            const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
             sp[lane] = make_uint2(rl, cl);
             __syncwarp();
             const uint32_t b1 = rl, b2 = rl + cl, lim = (uint32_t)nC + 1u, nC32 = (uint32_t)nC;
@@ -823,10 +875,51 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
             xj = __ldg(r + id);
             cj = raw < 0 ? nC : cap_p;
         }
-        float base = cj > 0.f ? xj : INF;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) base = fminf(base, __shfl_xor_sync(FULL_, base, o));
+        // lowest level among the nodes that can receive (non-negative floats
+        // order like their bit patterns: one 32-bit warp reduction)
+        const float base = __uint_as_float(
+            __reduce_min_sync(FULL_, __float_as_uint(cj > 0.f ? xj : INF)));
         const float xl = cj > 0.f ? xj - base : 0.f;
+        // the walk of Alg. 3 in real arithmetic, as in k_pb_slow: the level
+        // rises from event to event while the units last and stops at
+        // L* = L + rem / na; pairs that cross more than SB_ROUNDS events take
+        // the closed form below
+        {
+            const float top = xl + cj;
+            float L = 0.f, rem = nC, Ls = 0.f;
+            bool done = false;
+            for (int round = 0; round < SB_ROUNDS; ++round) {
+                const bool act = cj > 0.f && xl <= L && L < top;
+                const int na = __popc(__ballot_sync(FULL_, act));
+                const float e1 = (cj > 0.f && xl > L) ? xl : INF;
+                const float e2 = act ? top : INF;
+                const float ev = __uint_as_float(__reduce_min_sync(FULL_, __float_as_uint(fminf(e1, e2))));
+                if (na == 0) {
+                    if (ev == INF) break;
+                    L = ev;
+                    continue;
+                }
+                const float qd = rem / (float)na;
+                if (ev == INF || L + qd < ev) {
+                    Ls = L + qd;
+                    done = true;
+                    break;
+                }
+                rem -= (ev - L) * (float)na;
+                L = ev;
+                if (!(rem > 0.f)) {
+                    Ls = L;
+                    done = true;
+                    break;
+                }
+            }
+            if (done) {
+                const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, Ls - xl)) : 0.f;
+                if (dj > 0.f) gadd_f32(acc, accc, id, dj);
+                __syncwarp();
+                continue;
+            }
+        }
         sp[wib][lane] = make_float2(xl, cj);
         __syncwarp();
         const float b1 = xl, b2 = xl + cj;
