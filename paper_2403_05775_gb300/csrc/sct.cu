@@ -79,6 +79,9 @@ struct PassOut {
     int64_t *cntN;
     int64_t *nspawn;         // [nitems] (COUNT)
     unsigned long long *ck;  // [2] lo, hi (COUNT)
+    unsigned long long *nodes_seen;  // node entries counted so far, all levels (COUNT)
+    unsigned long long node_budget;  // more than this: stop counting (COUNT)
+    int *stop;                       // set once the budget is exceeded (COUNT)
     int *maxlen;             // (COUNT)
     const int64_t *spawn_off;  // [nitems] (SPAWN)
     uint32_t *spawn_rec;       // (SPAWN)
@@ -117,7 +120,11 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
 
     while (true) {
         unsigned long long rr = 0;
-        if (lane == 0) rr = atomicAdd(next_item, 1ull);
+        if (lane == 0) {
+            // a count pass over budget stops handing out items
+            if (MODE == MODE_COUNT && *(volatile int *)po.stop) rr = ~0ull;
+            else rr = atomicAdd(next_item, 1ull);
+        }
         rr = __shfl_sync(FULL, rr, 0);
         if (rr >= (unsigned long long)NI) break;
         const int64_t item = (int64_t)rr;
@@ -160,6 +167,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
         }
         int64_t nsp = MODE == MODE_SPAWN ? po.spawn_off[item] : 0;
         unsigned long long ck_lo = 0, ck_hi = 0;
+        unsigned long long pend = 0;  // node entries not yet added to nodes_seen
         int mlen = 0;
 
         // initial frame: the root, or the spawned recursion node
@@ -202,6 +210,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                         if (cls < 0 || nC == ~0ull) {
                             if (lane == 0) atomicOr(err, cls < 0 ? DERR_CAPACITY : DERR_OVERFLOW);
                         } else if (MODE == MODE_COUNT) {
+                            int over = 0;
                             if (lane == 0) {
                                 cP[cls] += 1;
                                 cN[cls] += len;
@@ -209,7 +218,17 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                                 ck_lo += nC;
                                 ck_hi += ck_lo < o ? 1ull : 0ull;
                                 mlen = len > mlen ? len : mlen;
+                                // report progress against the memory budget
+                                // every 2^16 node entries, and stop once over
+                                pend += (unsigned long long)len;
+                                if (pend >= (1ull << 16)) {
+                                    const unsigned long long t = atomicAdd(po.nodes_seen, pend) + pend;
+                                    pend = 0;
+                                    if (t > po.node_budget) atomicExch(po.stop, 1);
+                                    over = *(volatile int *)po.stop;
+                                }
                             }
+                            if (__shfl_sync(FULL, over, 0)) break;
                         } else if (MODE == MODE_EMIT) {
                             int64_t pidx = 0, noff = 0;
                             if (lane == 0) {
@@ -346,6 +365,11 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
             }
         }
         if (MODE == MODE_COUNT && lane == 0) {
+            if (pend) {
+                const unsigned long long t = atomicAdd(po.nodes_seen, pend) + pend;
+                if (t > po.node_budget) atomicExch(po.stop, 1);
+                pend = 0;
+            }
 #pragma unroll
             for (int c = 0; c < NCLASS; ++c) {
                 po.cntP[(int64_t)c * NI + item] = cP[c];
@@ -448,8 +472,13 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
     out.k = k;
     out.n = n;
     const int dmax = std::max(1, g.max_out);
-    if (dmax + 1 > MAX_PAIR_LEN)
-        fail(KDSS_ERR_UNSUPPORTED, "out-degree above 1023: pairs could exceed 1024 nodes");
+    if (dmax + 1 > MAX_PAIR_LEN) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "out-degree %d above 1023 (degeneracy %d): pairs could exceed 1024 nodes",
+                 g.max_out, g.degeneracy);
+        fail(KDSS_ERR_UNSUPPORTED, buf);
+    }
     const int S = (dmax + 31) / 32;
     upload_binom(c, dmax + 2, k, out);
     const int bcols = k + 1;
@@ -476,10 +505,17 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
     }
     const size_t dyn = use_shared ? smem : 0;
 
-    DBuf<unsigned long long> ctr(c, 4);  // [0] next item, [1..2] c_k
-    DBuf<int> ints(c, 2);                // [0] max len, [1] error
+    DBuf<unsigned long long> ctr(c, 4);  // [0] next item, [1..2] c_k, [3] node entries seen
+    DBuf<int> ints(c, 3);                // [0] max len, [1] error, [2] over budget
     zero(c, ctr.p, 4 * sizeof(unsigned long long));
-    zero(c, ints.p, 2 * sizeof(int));
+    zero(c, ints.p, 3 * sizeof(int));
+    // The SCT must fit the device: about 4.5 bytes per node entry (4 for the
+    // id, the offset and h of pairs of ~20 nodes), within 85% of the free
+    // memory at the start of the build.  The count pass stops once it has
+    // seen more node entries than that.
+    size_t free_b = 0, total_b = 0;
+    KDSS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const unsigned long long node_budget = (unsigned long long)(0.85 * (double)free_b / 4.5);
 
     struct Level {
         int64_t nitems = 0;
@@ -514,7 +550,24 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
         PassOut po{};
         po.cntP = L.cntP.p; po.cntN = L.cntN.p; po.nspawn = nspawn.p;
         po.ck = ctr.p + 1; po.maxlen = ints.p;
+        po.nodes_seen = ctr.p + 3; po.node_budget = node_budget; po.stop = ints.p + 2;
         launch(k_sct<MODE_COUNT>, L, po);
+        {
+            int over = 0;
+            to_host(c, &over, ints.p + 2, 1);
+            if (over) {
+                unsigned long long seen = 0;
+                to_host(c, &seen, ctr.p + 3, 1);
+                char buf[320];
+                snprintf(buf, sizeof buf,
+                         "the SCT does not fit the device: the count pass stopped after %llu node "
+                         "entries (about %.1f GB) with %.1f GB free; the SCT has more (k = %d, "
+                         "degeneracy %d, out-degree %d)",
+                         seen, 4.5e-9 * (double)seen, 1e-9 * (double)free_b, k, g.degeneracy,
+                         g.max_out);
+                fail(KDSS_ERR_OOM, buf);
+            }
+        }
         const int64_t ns = exclusive_scan_i64(c, nspawn.p, spoff.p, L.nitems);
         if (ns == 0) break;
         DBuf<uint32_t> rec(c, (size_t)ns * stride);

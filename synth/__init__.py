@@ -266,6 +266,13 @@ def workload_chunglu_1e5():
     return n, s, d
 
 
+def workload_rmat24():
+    """The large single graph: R-MAT scale 24 (16,777,216 nodes), edge factor
+    32 (536,870,912 draws), planted 200-node near-clique at p = 0.95, seed 4."""
+    n, s, d, _ = rmat(1 << 24, 32, 4, plant_size=200, plant_prob=0.95)
+    return n, s, d
+
+
 def batch_rmat_specs(count: int = 256, seed: int = 3, nmin=1e3, nmax=1e5):
     """Per-instance (n, k) of the batched workload: n log-uniform in
     [nmin, nmax], k uniform in {3..8}; stream 10 and 11 of ``seed``."""
