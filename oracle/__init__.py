@@ -41,8 +41,11 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB_PATH) >= os.path.getmtime(SRC)):
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                           "-o", tmp, SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, SRC, "-lm"]
+    try:   # host threads for orc_fw_sync_par; without OpenMP it runs serially
+        subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -81,6 +84,9 @@ def lib():
                 f = getattr(L, nm)
                 f.restype = C.c_int
                 f.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i32p, C.c_int, C.c_int, u64p]
+            L.orc_fw_sync_par.restype = C.c_int
+            L.orc_fw_sync_par.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i32p, C.c_int,
+                                          C.c_int, u64p, C.c_int]
             L.orc_fw_cont.restype = C.c_int
             L.orc_fw_cont.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i32p, C.c_int,
                                       C.c_int, f64p]
@@ -256,6 +262,18 @@ def fw_sync(n, s, k, T, r0=None):
     return r
 
 
+def fw_sync_par(n, s, k, T, threads=None, r0=None):
+    """fw_sync with the pairs of each iteration split over host threads
+    (same r_T; a timing baseline)."""
+    threads = threads or os.cpu_count() or 1
+    r = np.zeros(n, np.uint64) if r0 is None else np.array(r0, np.uint64)
+    rc = lib().orc_fw_sync_par(n, len(s["h"]), s["pair_off"], s["nodes"], s["h"], k, T, r,
+                               int(threads))
+    if rc != 0:
+        raise OverflowError(f"fw_sync_par failed ({rc})")
+    return r
+
+
 def fw_seq(n, s, k, T, r0=None):
     """Alg. 2 as printed: pairs update r in place, in array order."""
     r = np.zeros(n, np.uint64) if r0 is None else np.array(r0, np.uint64)
@@ -343,18 +361,20 @@ def brute_best(n, masks, weights):
 # The whole path (A1-A6) in one call
 # --------------------------------------------------------------------------
 
-def solve(n, src, dst, k, T, order_kind=ORDER_PEEL, mode="sync", with_cliques=False):
+def solve(n, src, dst, k, T, order_kind=ORDER_PEEL, mode="sync", with_cliques=False,
+          threads=1):
     """Run the oracle's path: graph, order, SCT, T iterations, extraction.
 
     mode: 'sync' (rule I, synchronous), 'seq' (rule I, in place), 'cont'
-    (continuous rule, FP64).  Returns a dict with the SCT, r_T, the order, the
-    extracted prefix (i*, ids, exact count) and the bounds."""
+    (continuous rule, FP64).  threads > 1 runs the synchronous iterations on
+    that many host threads (same result).  Returns a dict with the SCT, r_T,
+    the order, the extracted prefix (i*, ids, exact count) and the bounds."""
     off, adj = csr(n, src, dst)
     core, rnd, degen = peel(n, off, adj)
     rank, vert = order(n, core, rnd, order_kind)
     s = sct(n, off, adj, rank, vert, k)
     if mode == "sync":
-        r = fw_sync(n, s, k, T)
+        r = fw_sync(n, s, k, T) if threads <= 1 else fw_sync_par(n, s, k, T, threads)
     elif mode == "seq":
         r = fw_seq(n, s, k, T)
     elif mode == "cont":

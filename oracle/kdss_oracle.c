@@ -376,7 +376,8 @@ int64_t orc_sct(int64_t n, const int64_t *off, const int32_t *adj,
 /* (Lemma 2.6), plateaus of equal r in ascending order, then the walk that  */
 /* raises the lowest plateau round by round.                                */
 /* ------------------------------------------------------------------------ */
-static const uint64_t *g_sort_r; static const int32_t *g_sort_id;
+/* comparator inputs, one set per host thread (orc_fw_sync_par runs PBUpdate on several) */
+static _Thread_local const uint64_t *g_sort_r; static _Thread_local const int32_t *g_sort_id;
 static int cmp_by_r_id(const void *a, const void *b) {
     int x = *(const int *)a, y = *(const int *)b;
     if (g_sort_r[x] != g_sort_r[y]) return g_sort_r[x] < g_sort_r[y] ? -1 : 1;
@@ -528,7 +529,7 @@ int orc_pbupdate_level(int len, const int32_t *ids, const uint64_t *r, int h, in
 
 /* Continuous analogue of Alg. 3 (no floor: w = min(up, gap, n_C/|V_i|) as a */
 /* real number), FP64.  The allocation is the exact water level of the pair. */
-static const double *g_sort_rd;
+static _Thread_local const double *g_sort_rd;
 static int cmp_by_rd_id(const void *a, const void *b) {
     int x = *(const int *)a, y = *(const int *)b;
     if (g_sort_rd[x] != g_sort_rd[y]) return g_sort_rd[x] < g_sort_rd[y] ? -1 : 1;
@@ -614,6 +615,51 @@ int orc_fw_sync(int64_t n, int64_t npairs, const int64_t *pair_off, const int32_
         for (int64_t v = 0; v < n; ++v) r[v] += dr[v];
     }
     free(dr); free(rv); free(dv);
+    return rc;
+}
+
+/* The synchronous iterations of orc_fw_sync with the pairs of an iteration
+ * split into `threads` contiguous chunks run by host threads (OpenMP when the
+ * oracle is built with it, one after the other otherwise).  Each chunk sums its
+ * pairs' allocations into its own delta vector and the vectors are added after
+ * the iteration: integer sums, so r_T equals orc_fw_sync's exactly.  Timing
+ * baseline only; the pins test it against orc_fw_sync. */
+int orc_fw_sync_par(int64_t n, int64_t npairs, const int64_t *pair_off, const int32_t *nodes,
+                    const int32_t *hcnt, int k, int T, uint64_t *r, int threads) {
+    if (threads < 1) threads = 1;
+    const int mx = max_pair_len(npairs, pair_off);
+    const size_t stride = (size_t)n + 1;
+    uint64_t *dr = (uint64_t *)malloc(sizeof(uint64_t) * stride * (size_t)threads);
+    int *crc = (int *)calloc((size_t)threads, sizeof(int));
+    if (!dr || !crc) { free(dr); free(crc); return ORC_OVERFLOW; }
+    int rc = ORC_OK;
+    for (int t = 1; t <= T && rc == ORC_OK; ++t) {
+        memset(dr, 0, sizeof(uint64_t) * stride * (size_t)threads);
+#pragma omp parallel for num_threads(threads) schedule(static, 1)
+        for (int c = 0; c < threads; ++c) {
+            uint64_t *d = dr + (size_t)c * stride;
+            uint64_t *rv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(mx + 1));
+            uint64_t *dv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(mx + 1));
+            const int64_t q0 = npairs * c / threads, q1 = npairs * (c + 1) / threads;
+            for (int64_t q = q0; q < q1 && crc[c] == ORC_OK; ++q) {
+                const int len = (int)(pair_off[q + 1] - pair_off[q]);
+                const int32_t *ids = nodes + pair_off[q];
+                for (int i = 0; i < len; ++i) rv[i] = r[ids[i]];
+                crc[c] = orc_pbupdate_alg3(len, ids, rv, hcnt[q], k, dv);
+                if (crc[c] == ORC_OK)
+                    for (int i = 0; i < len; ++i) d[ids[i]] += dv[i];
+            }
+            free(rv); free(dv);
+        }
+        for (int c = 0; c < threads; ++c) if (crc[c]) rc = crc[c];
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int64_t v = 0; v < n; ++v) {
+            uint64_t x = 0;
+            for (int c = 0; c < threads; ++c) x += dr[(size_t)c * stride + (size_t)v];
+            r[v] += x;
+        }
+    }
+    free(dr); free(crc);
     return rc;
 }
 

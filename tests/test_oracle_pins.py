@@ -365,3 +365,18 @@ def test_sequential_and_synchronous_reach_the_same_density():
     a = O.solve(n, s, d, 3, 50, mode="seq")
     b = O.solve(n, s, d, 3, 50, mode="sync")
     assert a["istar"] == b["istar"] == 6 and a["count"] == b["count"] == 8
+
+
+def test_threaded_synchronous_iterations_equal_the_serial_ones():
+    """The host-threaded form of the synchronous iterations (the timed CPU
+    baseline on all cores) sums the same integer allocations: r_T is equal."""
+    for n, s, d, k, T in [(*synth.g1(), 3, 30),
+                          (*synth.erdos_renyi(400, 0.04, 11), 3, 25),
+                          (*synth.chung_lu(3000, 10.0, 2.4, 12, plant_size=20, plant_prob=0.9)[:3], 4, 20)]:
+        off, adj = O.csr(n, s, d)
+        core, rnd, _ = O.peel(n, off, adj)
+        rank, vert = O.order(n, core, rnd)
+        sc = O.sct(n, off, adj, rank, vert, k)
+        want = O.fw_sync(n, sc, k, T)
+        for th in (1, 3, 8):
+            assert np.array_equal(O.fw_sync_par(n, sc, k, T, th), want)
