@@ -227,6 +227,39 @@ def whole_job_value(units_per_rank, world, max_ms):
     return units_per_rank * world / (max_ms / 1e3)
 
 
+def async_vs_sync(K, torch, dev, n, src, dst, k, T):
+    """The in-place (asynchronous) iterations against the synchronous ones on
+    the benchmark graph: the certificate gap 1 - rho'/max r-hat after 5, 20,
+    50, 100 and T iterations, the first multiple of 5 with gap <= 2%, and the
+    per-iteration time of each (CUDA events around T iterations)."""
+    out = {}
+    sct = K.kdss_build_sct(n, src, dst, k)
+    for mode, fl in (("sync", 0), ("async", K.KDSS_FLAG_ASYNC)):
+        o = K.make_opts(precision=PRECISIONS["fp64"], flags=fl)
+        st, t, gaps, first = None, 0, {}, None
+        while t < T:
+            st = K.kdss_fw_iterate(sct, st, 5, o)
+            t += 5
+            g = K.kdss_extract(sct, st)["gap"]
+            if t in (5, 20, 50, 100, T):
+                gaps[t] = g
+            if first is None and g <= 0.02:
+                first = t
+        st.free()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize()
+        a.record(stream)
+        st = K.kdss_fw_iterate(sct, None, T, o)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st.free()
+        out[mode] = {"gap_at": gaps, "first_t_gap_le_2pct": first,
+                     "ms_per_iteration": a.elapsed_time(b) / T}
+    sct.free()
+    return out
+
+
 def large_rmat_report(K, torch, dev):
     """The large single graph (R-MAT scale 24, edge factor 32, planted
     200-node near-clique, k = 6, seed 4, T = 100): the edge list goes to the
@@ -559,6 +592,7 @@ def main():
             "target_source": "oracle density after T iterations" if rho_oracle else "own T"}
         st.free()
         sct.free()
+        extras["async_vs_sync"] = async_vs_sync(K, torch, dev, n, src, dst, k, T)
         try:
             extras["batched"] = batched_rmat(K, torch, dev, stream, flush, args.allocator)
         except K.KdssError as e:

@@ -65,6 +65,7 @@ typedef int32_t kdss_status;
 /* flags */
 #define KDSS_FLAG_PROFILE 1u        /* time every FW kernel with CUDA events */
 #define KDSS_FLAG_KEEP_GRAPH 2u     /* keep the CSR, cores and order in the SCT handle */
+#define KDSS_FLAG_ASYNC 4u          /* kdss_fw_iterate: pairs update r in place (see there) */
 
 typedef void *(*kdss_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*kdss_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
@@ -193,7 +194,15 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
  *   s     : SCT handle.
  *   state : in/out FW state.
  *   T     : iterations to run, T >= 0.
- * Errors: INVALID_ARG, OVERFLOW (r would leave the exact range), OOM, CUDA.
+ * With KDSS_FLAG_ASYNC (integer rule, KDSS_INT64 / KDSS_FP64 only) the pairs
+ * add their allocations straight into r while others read it, the way Alg. 2
+ * as printed updates r in place pair after pair: a pair reads r as it stands
+ * when it loads it (updates made earlier in the same iteration may or may
+ * not be visible), so the result depends on the schedule and is not
+ * reproducible; each pair still hands out exactly its n_C units within its
+ * caps, so sum_u r_t(u) = t c_k and r_t / t stays feasible.
+ * Errors: INVALID_ARG, OVERFLOW (r would leave the exact range), OOM,
+ *   UNSUPPORTED (KDSS_FLAG_ASYNC with KDSS_FP32K), CUDA.
  */
 kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts);
 

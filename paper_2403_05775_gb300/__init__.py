@@ -37,6 +37,7 @@ KDSS_ORDER_PEEL = 0
 KDSS_ORDER_CORE = 1
 KDSS_FLAG_PROFILE = 1
 KDSS_FLAG_KEEP_GRAPH = 2
+KDSS_FLAG_ASYNC = 4
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

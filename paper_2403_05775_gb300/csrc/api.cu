@@ -238,7 +238,10 @@ kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kd
     }
     if ((*state)->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
     try {
-        fw_run(c, s->s, (*state)->st, T, opts && (opts->flags & KDSS_FLAG_PROFILE));
+        if (opts && (opts->flags & KDSS_FLAG_ASYNC))
+            fw_run_async(c, s->s, (*state)->st, T);
+        else
+            fw_run(c, s->s, (*state)->st, T, opts && (opts->flags & KDSS_FLAG_PROFILE));
         sync(c);
     } catch (...) {
         if (created) { delete *state; *state = nullptr; }

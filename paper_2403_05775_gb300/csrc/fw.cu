@@ -1400,6 +1400,44 @@ void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, 
     }
 }
 
+// ---- in-place iterations (KDSS_FLAG_ASYNC) ----
+//
+// The PBUpdate launches of one iteration with the delta vector replaced by r
+// itself: every pair's allocation lands in r at once and pairs that read r
+// later see it (Alg. 2's in-place update, in the order the GPU happens to
+// run the pairs).  Iterations are replayed from one CUDA graph holding the
+// slow-list reset and the PBUpdate launches; the running max of r for the
+// bound is taken once at the end (r only grows), by the step kernel over a
+// zero delta.
+void fw_run_async(const Ctx &c, const SctDev &s, StateDev &st, int T) {
+    if (T <= 0) return;
+    if (st.precision == KDSS_FP32K)
+        fail(KDSS_ERR_UNSUPPORTED, "in-place iterations exist for the integer rule only");
+    const long double lim = st.precision == KDSS_INT64 ? 9.2e18L : 9.007199254740992e15L;
+    const long double ck = (long double)s.ck_lo + (long double)s.ck_hi * 18446744073709551616.0L;
+    if ((long double)(st.t + T) * ck >= lim)
+        fail(KDSS_ERR_OVERFLOW, "T * c_k leaves the exact range of r");
+    cudaGraphExec_t exec = nullptr;
+    const long long nk = capture(c, &exec, [&](const Ctx &cc) {
+        KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), cc.stream));
+        if (st.precision == KDSS_FP64)
+            launch_pbupdate_int<double>(cc, s, (double *)st.r.p, (double *)st.r.p, st.ovf_list.p,
+                                        st.ovf_count.p, st.err.p);
+        else
+            launch_pbupdate_int<uint64_t>(cc, s, st.r.p, st.r.p, st.ovf_list.p, st.ovf_count.p,
+                                          st.err.p);
+    });
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < T && e == cudaSuccess; ++it) {
+        e = cudaGraphLaunch(exec, c.stream);
+        add_launches(nk);
+    }
+    cudaGraphExecDestroy(exec);
+    check_cuda(e, "in-place FW graph launch", __FILE__, __LINE__);
+    enqueue_step(c, s, st);  // delta is zero: only the max of r
+    st.t += T;
+}
+
 // ---- several SCTs over disjoint node ranges sharing one state (batches) ----
 
 void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, StateDev &st) {
