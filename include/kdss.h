@@ -63,7 +63,7 @@ typedef int32_t kdss_status;
 #define KDSS_ORDER_CORE 1
 
 /* flags */
-#define KDSS_FLAG_PROFILE 1u        /* time every FW kernel with CUDA events */
+#define KDSS_FLAG_PROFILE 1u        /* time the FW kernels of every 8th iteration with CUDA events */
 #define KDSS_FLAG_KEEP_GRAPH 2u     /* keep the CSR, cores and order in the SCT handle */
 #define KDSS_FLAG_ASYNC 4u          /* kdss_fw_iterate: pairs update r in place (see there) */
 
@@ -129,9 +129,9 @@ typedef struct kdss_result {
 } kdss_result;
 
 typedef struct kdss_timing {
-    double fw_kernel_ms;    /* summed event time of the PBUpdate kernels */
-    double step_kernel_ms;  /* summed event time of the step kernels */
-    int64_t fw_launches;    /* PBUpdate kernel launches timed */
+    double fw_kernel_ms;    /* summed event time of the timed PBUpdate passes */
+    double step_kernel_ms;  /* summed event time of the timed step kernels */
+    int64_t fw_launches;    /* PBUpdate passes timed (every 8th iteration) */
     int64_t step_launches;
 } kdss_timing;
 

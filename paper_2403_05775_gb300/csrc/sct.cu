@@ -79,6 +79,9 @@ struct PassOut {
     int64_t *cntN;
     int64_t *nspawn;         // [nitems] (COUNT)
     unsigned long long *ck;  // [2] lo, hi (COUNT)
+    uint32_t *direct_rec;            // spawn records written by the count pass (COUNT)
+    unsigned long long *direct_cursor;
+    long long direct_cap;
     unsigned long long *nodes_seen;  // node entries counted so far, all levels (COUNT)
     unsigned long long node_budget;  // more than this: stop counting (COUNT)
     int *stop;                       // set once the budget is exceeded (COUNT)
@@ -330,10 +333,21 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 const int ncc = (int)__reduce_add_sync(FULL, (unsigned)__popc(child));
                 // big hold branch: becomes an item of the next level
                 if (h + 1 < k && ncc >= SPLIT_MIN && h + 1 + p + ncc >= k) {
+                    // the count pass also writes the record, at a slot taken
+                    // from a cursor, while the slots last; if they run out,
+                    // a spawn pass writes every record in item order
+                    uint32_t *r2 = nullptr;
                     if (MODE == MODE_COUNT) {
+                        long long slot = 0;
+                        if (lane == 0) slot = (long long)atomicAdd(po.direct_cursor, 1ull);
+                        slot = __shfl_sync(FULL, slot, 0);
+                        if (slot < po.direct_cap) r2 = po.direct_rec + (size_t)slot * (2 + k + 2 * S);
                         nsp += 1;
                     } else if (MODE == MODE_SPAWN) {
-                        uint32_t *r2 = po.spawn_rec + (size_t)nsp * (2 + k + 2 * S);
+                        r2 = po.spawn_rec + (size_t)nsp * (2 + k + 2 * S);
+                        nsp += 1;
+                    }
+                    if (r2) {
                         if (lane == 0) {
                             r2[0] = (uint32_t)root;
                             r2[1] = (uint32_t)(h + 1);
@@ -348,7 +362,6 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                                 if ((piv[t] >> 5) == lane) pw |= 1u << (piv[t] & 31);
                             r2[2 + k + S + lane] = pw;
                         }
-                        nsp += 1;
                     }
                     __syncwarp();
                     continue;  // stay at this depth: next hold branch
@@ -547,10 +560,18 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
         zero(c, L.cntN.p, L.cntN.bytes());
         DBuf<int64_t> nspawn(c, (size_t)L.nitems), spoff(c, (size_t)L.nitems);
         zero(c, nspawn.p, nspawn.bytes());
+        // the count pass writes the next level's records into `direct` while
+        // it has room (2 per item, at least 16384, at most 256 MB)
+        const int64_t dcap = std::min<int64_t>(std::max<int64_t>(2 * L.nitems, 16384),
+                                               (int64_t)(256ll << 20) / (4ll * stride));
+        DBuf<uint32_t> direct(c, (size_t)dcap * stride);
+        DBuf<unsigned long long> dcur(c, 1);
+        zero(c, dcur.p, sizeof(unsigned long long));
         PassOut po{};
         po.cntP = L.cntP.p; po.cntN = L.cntN.p; po.nspawn = nspawn.p;
         po.ck = ctr.p + 1; po.maxlen = ints.p;
         po.nodes_seen = ctr.p + 3; po.node_budget = node_budget; po.stop = ints.p + 2;
+        po.direct_rec = direct.p; po.direct_cursor = dcur.p; po.direct_cap = dcap;
         launch(k_sct<MODE_COUNT>, L, po);
         {
             int over = 0;
@@ -570,11 +591,17 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
         }
         const int64_t ns = exclusive_scan_i64(c, nspawn.p, spoff.p, L.nitems);
         if (ns == 0) break;
-        DBuf<uint32_t> rec(c, (size_t)ns * stride);
-        PassOut ps{};
-        ps.spawn_off = spoff.p;
-        ps.spawn_rec = rec.p;
-        launch(k_sct<MODE_SPAWN>, L, ps);
+        DBuf<uint32_t> rec;
+        if (ns <= dcap) {
+            rec = std::move(direct);  // every record is there (in arrival order)
+        } else {
+            direct.reset();
+            rec = DBuf<uint32_t>(c, (size_t)ns * stride);
+            PassOut ps{};
+            ps.spawn_off = spoff.p;
+            ps.spawn_rec = rec.p;
+            launch(k_sct<MODE_SPAWN>, L, ps);
+        }
         levels.emplace_back();  // no reference into `levels` is used after this
         levels.back().nitems = ns;
         levels.back().rec = std::move(rec);

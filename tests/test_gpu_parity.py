@@ -184,8 +184,9 @@ def test_fw_large_counts_are_bit_exact():
 
 
 def test_profiled_and_graph_runs_agree():
-    """The profiled path (separate graphs with events) and the plain path
-    (one graph per iteration) give the same r, for every precision."""
+    """The profiled path (every 8th iteration as separate graphs between
+    events, the others fused) and the plain path (one graph per iteration)
+    give the same r, for every precision."""
     n, s, d = GRAPHS["rmat2k"]()
     sct = K.kdss_build_sct(n, s, d, 4)
     for prec in (K.KDSS_INT64, K.KDSS_FP64, K.KDSS_FP32K):
@@ -198,7 +199,7 @@ def test_profiled_and_graph_runs_agree():
         else:
             assert np.array_equal(ra, rb)
         tm = K.kdss_state_timing(a)
-        assert tm["fw_launches"] == 30 and tm["fw_kernel_ms"] > 0
+        assert tm["fw_launches"] == 4 and tm["fw_kernel_ms"] > 0   # iterations 0, 8, 16, 24
 
 
 @pytest.mark.parametrize("name", sorted(GRAPHS))
