@@ -91,6 +91,8 @@ def lib():
             L.orc_fw_cont.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i32p, C.c_int,
                                       C.c_int, f64p]
             L.orc_fw_cliques.argtypes = [C.c_int64, i32p, C.c_int, C.c_int, u64p]
+            L.orc_fw_cliques_sync.restype = None
+            L.orc_fw_cliques_sync.argtypes = [C.c_int64, C.c_int64, i32p, C.c_int, C.c_int, u64p]
             L.orc_sort_desc_u64.argtypes = [C.c_int64, u64p, i32p]
             L.orc_sort_desc_f64.argtypes = [C.c_int64, f64p, i32p]
             L.orc_prefix_counts_cliques.argtypes = [C.c_int64, i32p, C.c_int64, i32p,
@@ -297,6 +299,15 @@ def fw_cliques(n, cliques, k, T, r0=None):
     cl = np.ascontiguousarray(cliques, np.int32).reshape(-1)
     r = np.zeros(n, np.uint64) if r0 is None else np.array(r0, np.uint64)
     lib().orc_fw_cliques(cl.size // k if k else 0, cl, k, T, r)
+    return r
+
+
+def fw_cliques_sync(n, cliques, k, T, r0=None):
+    """Alg. 1 over the explicit list, synchronous reading (every clique of an
+    iteration reads r_{t-1}; units summed after the iteration)."""
+    cl = np.ascontiguousarray(cliques, np.int32).reshape(-1)
+    r = np.zeros(n, np.uint64) if r0 is None else np.array(r0, np.uint64)
+    lib().orc_fw_cliques_sync(n, cl.size // k if k else 0, cl, k, T, r)
     return r
 
 

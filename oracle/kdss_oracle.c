@@ -725,6 +725,26 @@ void orc_fw_cliques(int64_t c, const int32_t *cl, int k, int T, uint64_t *r) {
         }
 }
 
+/* Alg. 1 over the explicit list in the synchronous reading R1: every clique
+ * of iteration t looks at r_{t-1} and hands its unit to its member of least
+ * (r, id); the units are summed into r_t after the iteration. */
+void orc_fw_cliques_sync(int64_t n, int64_t c, const int32_t *cl, int k, int T, uint64_t *r) {
+    uint64_t *d = (uint64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(uint64_t));
+    for (int t = 1; t <= T; ++t) {
+        for (int64_t q = 0; q < c; ++q) {
+            const int32_t *C = cl + q * k;
+            int32_t best = C[0];
+            for (int j = 1; j < k; ++j) {
+                const int32_t u = C[j];
+                if (r[u] < r[best] || (r[u] == r[best] && u < best)) best = u;
+            }
+            d[best]++;
+        }
+        for (int64_t v = 0; v < n; ++v) { r[v] += d[v]; d[v] = 0; }
+    }
+    free(d);
+}
+
 /* ------------------------------------------------------------------------ */
 /* O5: extraction (the final sort and prefix step of Alg. 2, R4, R5).      */
 /* ------------------------------------------------------------------------ */

@@ -33,6 +33,9 @@ MUTANTS = {
         "for (int j = 0; j < ncur; ++j) cur[q++] = cur[j];"),
     "prefix_event_one_position_early": (
         "acc[mh + 1] += prev;", "acc[mh] += prev;"),
+    "alg1_sync_ties_to_highest_id": (
+        "if (r[u] < r[best] || (r[u] == r[best] && u < best)) best = u;",
+        "if (r[u] < r[best] || (r[u] == r[best] && u > best)) best = u;"),
     "argmax_ties_to_smallest_prefix": (
         "if (frac_cmp(a, (uint64_t)i, b, (uint64_t)best) >= 0) best = i;",
         "if (frac_cmp(a, (uint64_t)i, b, (uint64_t)best) > 0) best = i;"),
@@ -59,6 +62,7 @@ PINS = [
     P.test_prefix_counts_from_pairs_equal_explicit_list,
     P.test_argmax_takes_the_largest_prefix_on_ties,
     lambda: P.test_brute_force_small_graphs(3),
+    P.test_alg1_synchronous_over_explicit_cliques,
 ]
 
 

@@ -380,3 +380,38 @@ def test_threaded_synchronous_iterations_equal_the_serial_ones():
         want = O.fw_sync(n, sc, k, T)
         for th in (1, 3, 8):
             assert np.array_equal(O.fw_sync_par(n, sc, k, T, th), want)
+
+
+def test_alg1_synchronous_over_explicit_cliques():
+    """Alg. 1 over the explicit clique list, synchronous reading: the first
+    iteration from r = 0 gives every clique's unit to its lowest id (closed
+    form); sum r_t = t c exactly; on vertex-disjoint cliques it equals the
+    sequential form (no clique sees another's update); r_T / T is feasible
+    for CP(G), so max r_T / T >= rho_k(V*) (brute force), and the prefix
+    extracted from it reaches V* on small graphs (Lemma 2.3)."""
+    n, s, d = synth.g1()
+    off, adj = O.csr(n, s, d)
+    cl = O.list_cliques(n, off, adj, 3)
+    r1 = O.fw_cliques_sync(n, cl, 3, 1)
+    assert r1.tolist() == np.bincount(cl.min(axis=1), minlength=n).tolist()
+    rT = O.fw_cliques_sync(n, cl, 3, 57)
+    assert int(rT.sum()) == 57 * len(cl)
+    # disjoint triangles: synchronous == sequential
+    tri = np.array([[3 * i, 3 * i + 1, 3 * i + 2] for i in range(5)], np.int32)
+    assert np.array_equal(O.fw_cliques_sync(15, tri, 3, 20), O.fw_cliques(15, tri, 3, 20))
+    for seed in range(4):
+        n, s, d = _planted(12 + seed % 3, 0.25, 6, 500 + seed)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        for k in (2, 3):
+            cl = O.list_cliques(n, off, adj, k)
+            if len(cl) == 0:
+                continue
+            masks = [sum(1 << int(v) for v in c) for c in cl]
+            bm, num, den, union = O.brute_best(n, masks, [1] * len(masks))
+            T = 3000
+            r = O.fw_cliques_sync(n, cl, k, T)
+            assert Fraction(int(r.max()), T) >= Fraction(num, den)
+            o2 = O.sort_desc(r)
+            lo2, hi2 = O.prefix_counts_cliques(n, o2, cl, k)
+            i2 = O.argmax_density(lo2, hi2)
+            assert Fraction(int(lo2[i2]), i2) == Fraction(num, den)
