@@ -260,6 +260,34 @@ def async_vs_sync(K, torch, dev, n, src, dst, k, T):
     return out
 
 
+def alg1_vs_sct(K, torch, dev, n, src, dst, k, T):
+    """Alg. 1 over the explicit k-clique list (expanded from the SCT on the
+    device) against the SCT iterations on the benchmark graph: clique-updates/s
+    of each (T iterations timed with CUDA events), the memory of the list and
+    of the SCT, and the bound max r / t each reaches after T iterations."""
+    stream = torch.cuda.current_stream(dev)
+    sct = K.kdss_build_sct(n, src, dst, k)
+    info = K.kdss_sct_info(sct)
+    ck = info["c_k"]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K.kdss_fw_cliques(sct, None, 1).free()          # expands the list (kept in the handle)
+    out = {"c_k": ck, "list_bytes": 4 * k * ck, "sct_bytes": 4 * info["L_k"] + 9 * info["eta_k"]}
+    for name, fn in (("alg1_explicit", lambda: K.kdss_fw_cliques(sct, None, T)),
+                     ("sct", lambda: K.kdss_fw_iterate(sct, None, T))):
+        torch.cuda.synchronize()
+        a.record(stream)
+        st = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res = K.kdss_extract(sct, st)
+        out[name] = {"value": T * ck / (ms / 1e3), "unit": UNIT, "ms": ms,
+                     "density": res["density"], "upper_bound": res["upper_bound"]}
+        st.free()
+    sct.free()
+    return out
+
+
 def large_rmat_report(K, torch, dev):
     """The large single graph (R-MAT scale 24, edge factor 32, planted
     200-node near-clique, k = 6, seed 4, T = 100): the edge list goes to the
@@ -593,6 +621,10 @@ def main():
         st.free()
         sct.free()
         extras["async_vs_sync"] = async_vs_sync(K, torch, dev, n, src, dst, k, T)
+        try:
+            extras["alg1_vs_sct"] = alg1_vs_sct(K, torch, dev, n, src, dst, k, T)
+        except K.KdssError as e:
+            extras["alg1_vs_sct"] = {"error": str(e)}
         try:
             extras["batched"] = batched_rmat(K, torch, dev, stream, flush, args.allocator)
         except K.KdssError as e:

@@ -207,6 +207,31 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
 kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts);
 
 /*
+ * kdss_fw_cliques -- T iterations of Alg. 1 (the Frank-Wolfe step over the
+ * explicit k-clique list): every k-clique gives its unit to its member of
+ * least (r, id), all cliques of iteration t reading r_{t-1} (synchronous
+ * form, as kdss_fw_iterate).  The list is the expansion of the SCT (each pair
+ * (V_h, V_p) holds V_h + S for the (k - |V_h|)-subsets S of V_p, Lemmas
+ * 2.4-2.5), built on the device on first use and kept in the handle.  The
+ * state is an ordinary KDSS_INT64 state, so kdss_extract applies; r_t / t is
+ * feasible for CP(G) and max r / t bounds rho_k(V*) from above (Lemma 2.3).
+ *   s, state, T : as for kdss_fw_iterate (opts->precision must be KDSS_INT64).
+ * Errors: INVALID_ARG, UNSUPPORTED (precision), OOM (the list would take
+ *   more than half of the free device memory; the message gives its size),
+ *   OVERFLOW, CUDA.
+ */
+kdss_status kdss_fw_cliques(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts);
+
+/*
+ * kdss_sct_copy_cliques -- the explicit k-clique list of kdss_fw_cliques
+ * (expanded on first use): min(capacity, c_k) rows of k node ids are copied
+ * to the host buffer `cliques`; *count receives c_k.  Rows come grouped by
+ * pair, hold ids first.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacity, int64_t *count);
+
+/*
  * kdss_state_copy_r -- copy r to a host buffer of n entries: uint64 for
  * KDSS_INT64 (cumulative r_t), double for KDSS_FP64 (cumulative r_t), float
  * for KDSS_FP32K (normalised r_t / t).  *t_out receives t (may be NULL).

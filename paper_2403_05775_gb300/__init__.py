@@ -145,6 +145,8 @@ def load(build_if_missing: bool = False):
             "kdss_version": (C.c_char_p, []),
             "kdss_kernel_launches": (i64, []),
             "kdss_fw_iterate_noalloc": (i32, [vp, vp, i32, i32, vp]),
+            "kdss_fw_cliques": (i32, [vp, P(vp), i32, P(kdss_opts)]),
+            "kdss_sct_copy_cliques": (i32, [vp, vp, i64, P(i64)]),
             "kdss_server_create": (i32, [P(kdss_server_opts), P(vp)]),
             "kdss_server_submit": (i32, [vp, P(kdss_query), P(i64)]),
             "kdss_server_wait": (i32, [vp, i64, i32, P(kdss_result), P(kdss_query_timing)]),
@@ -340,6 +342,28 @@ def kdss_fw_iterate(s: Sct, state: State | None, T: int, opts: kdss_opts | None 
     if state is None:
         return State(p.value)
     return state
+
+
+def kdss_fw_cliques(s: Sct, state: State | None, T: int, opts: kdss_opts | None = None) -> State:
+    """Alg. 1 over the explicit k-clique list (expanded from the SCT)."""
+    L = load()
+    p = C.c_void_p(state.ptr.value if state is not None else None)
+    _check(L.kdss_fw_cliques(s.ptr, C.byref(p), int(T), C.byref(opts or make_opts())))
+    if state is None:
+        return State(p.value)
+    return state
+
+
+def kdss_sct_copy_cliques(s: Sct) -> np.ndarray:
+    """The explicit k-clique list as a (c_k, k) int32 array."""
+    L = load()
+    cnt = C.c_int64()
+    _check(L.kdss_sct_copy_cliques(s.ptr, None, 0, C.byref(cnt)))
+    k = kdss_sct_info(s)["k"]
+    out = np.zeros((cnt.value, k), np.int32)
+    if cnt.value:
+        _check(L.kdss_sct_copy_cliques(s.ptr, out.ctypes.data, cnt.value, C.byref(cnt)))
+    return out
 
 
 def kdss_state_copy_r(st: State, n: int, precision: int):

@@ -250,6 +250,49 @@ kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kd
     API_END
 }
 
+kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacity,
+                                  int64_t *count) {
+    API_BEGIN
+    if (!s || !count) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (capacity < 0 || (capacity > 0 && !cliques)) fail(KDSS_ERR_INVALID_ARG, "bad output buffer");
+    if (s->nclq < 0) expand_cliques(s->ctx, s->s, s->cliques, s->nclq);
+    *count = s->nclq;
+    const int64_t rows = std::min<int64_t>(capacity, s->nclq);
+    if (rows > 0) to_host(s->ctx, cliques, s->cliques.p, (size_t)(rows * s->s.k));
+    API_END
+}
+
+kdss_status kdss_fw_cliques(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
+    API_BEGIN
+    if (!s || !state) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
+    Ctx c = make_ctx(opts);
+    if (s->nclq < 0) expand_cliques(s->ctx, s->s, s->cliques, s->nclq);
+    bool created = false;
+    if (!*state) {
+        const int prec = opts ? opts->precision : KDSS_INT64;
+        if (prec != KDSS_INT64) fail(KDSS_ERR_UNSUPPORTED, "Alg. 1 iterations keep r in KDSS_INT64");
+        kdss_state *st = new kdss_state();
+        try {
+            fw_init(c, s->s, prec, st->st);
+        } catch (...) {
+            delete st;
+            throw;
+        }
+        *state = st;
+        created = true;
+    }
+    if ((*state)->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
+    try {
+        fw_cliques_run(c, s->cliques.p, s->nclq, s->s.k, (*state)->st, T);
+        sync(c);
+    } catch (...) {
+        if (created) { delete *state; *state = nullptr; }
+        throw;
+    }
+    API_END
+}
+
 kdss_status kdss_state_copy_r(const kdss_state *st, void *r_host, int32_t *t_out) {
     API_BEGIN
     if (!st) fail(KDSS_ERR_INVALID_ARG, "NULL state");

@@ -11,7 +11,14 @@ struct kdss_sct {
     int64_t m = 0;
     int degeneracy = 0;
     int max_out = 0;
+    kdss::DBuf<int32_t> cliques;  // explicit k-clique list (expanded on first use)
+    int64_t nclq = -1;            // its length, -1 before expansion
 };
+
+namespace kdss {
+void expand_cliques(const Ctx &c, const SctDev &s, DBuf<int32_t> &out, int64_t &count);
+void fw_cliques_run(const Ctx &c, const int32_t *cl, int64_t count, int k, StateDev &st, int T);
+}  // namespace kdss
 
 struct kdss_state {
     kdss::StateDev st;
