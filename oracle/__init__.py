@@ -93,6 +93,14 @@ def lib():
             L.orc_fw_cliques.argtypes = [C.c_int64, i32p, C.c_int, C.c_int, u64p]
             L.orc_fw_cliques_sync.restype = None
             L.orc_fw_cliques_sync.argtypes = [C.c_int64, C.c_int64, i32p, C.c_int, C.c_int, u64p]
+            u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+            L.orc_color_greedy.restype = C.c_int
+            L.orc_color_greedy.argtypes = [C.c_int64, i64p, i32p, i32p, i32p]
+            L.orc_ccpath_dp.restype = C.c_int
+            L.orc_ccpath_dp.argtypes = [C.c_int64, i64p, i32p, i32p, C.c_int, u64p]
+            L.orc_ccpath_sample.restype = C.c_int
+            L.orc_ccpath_sample.argtypes = [C.c_int64, i64p, i32p, i32p, C.c_int, u64p, C.c_int64,
+                                            C.c_uint64, i32p, u8p, C.POINTER(C.c_uint64)]
             L.orc_sort_desc_u64.argtypes = [C.c_int64, u64p, i32p]
             L.orc_sort_desc_f64.argtypes = [C.c_int64, f64p, i32p]
             L.orc_prefix_counts_cliques.argtypes = [C.c_int64, i32p, C.c_int64, i32p,
@@ -408,3 +416,57 @@ def solve(n, src, dst, k, T, order_kind=ORDER_PEEL, mode="sync", with_cliques=Fa
     if with_cliques:
         out["cliques"] = list_cliques(n, off, adj, k)
     return out
+
+
+# --------------------------------------------------------------------------
+# CPSample (Sec. 5, Alg. 4); readings S1-S4 in kdss_oracle.c
+# --------------------------------------------------------------------------
+
+def color_greedy(n, off, adj, rank):
+    """S1: greedy colouring by decreasing rank; returns (colour, #colours)."""
+    color = np.zeros(max(n, 1), np.int32)
+    nc = lib().orc_color_greedy(n, off, adj, np.ascontiguousarray(rank, np.int32), color)
+    return color[:n], int(nc)
+
+
+def ccpath_dp(n, off, adj, color, k):
+    """S2: dp[v, i-1] = increasing-colour paths of i vertices from v."""
+    dp = np.zeros(max(n, 1) * k, np.uint64)
+    if lib().orc_ccpath_dp(n, off, adj, np.ascontiguousarray(color, np.int32), k, dp) != 0:
+        raise OverflowError("more than 2^64 color paths")
+    return dp[:n * k].reshape(n, k)
+
+
+def ccpath_sample(n, off, adj, color, k, dp, t, seed):
+    """S3: t uniform k-color paths; returns (paths (t, k), is_clique, #paths)."""
+    paths = np.zeros(max(t, 1) * k, np.int32)
+    flags = np.zeros(max(t, 1), np.uint8)
+    tot = C.c_uint64(0)
+    rc = lib().orc_ccpath_sample(n, off, adj, np.ascontiguousarray(color, np.int32), k,
+                                 np.ascontiguousarray(dp, np.uint64).reshape(-1), int(t),
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, paths, flags, C.byref(tot))
+    if rc != 0:
+        raise OverflowError("more than 2^64 color paths")
+    return paths[:t * k].reshape(t, k), flags[:t].astype(bool), int(tot.value)
+
+
+def cpsample(n, src, dst, k, t, T, seed, order_kind=ORDER_PEEL):
+    """Alg. 4: t sampled k-color paths, the set of cliques among them (S4),
+    T synchronous iterations of Alg. 1 over that set (reading R1), and the
+    prefix of largest |C_k(V_i) & sample| / i (ties to the larger i)."""
+    off, adj = csr(n, src, dst)
+    core, rnd, _ = peel(n, off, adj)
+    rank, _ = order(n, core, rnd, order_kind)
+    color, ncol = color_greedy(n, off, adj, rank)
+    dp = ccpath_dp(n, off, adj, color, k)
+    paths, flags, total = ccpath_sample(n, off, adj, color, k, dp, t, seed)
+    cl = np.sort(paths[flags], axis=1)
+    cl = np.unique(cl, axis=0) if len(cl) else cl.reshape(0, k)
+    r = fw_cliques_sync(n, cl, k, T)
+    ordr = sort_desc(r)
+    lo, hi = prefix_counts_cliques(n, ordr, cl, k)
+    i = argmax_density(lo, hi) if n > 0 else 0
+    return dict(color=color, ncolors=ncol, paths_total=total, samples_clique=int(flags.sum()),
+                cliques=cl, r=r, istar=i, ids=np.sort(ordr[:i]), count=int(lo[i]) if n else 0,
+                density=(int(lo[i]) / i) if i else 0.0,
+                upper_bound=float(r.max()) / T if n and T else 0.0)

@@ -746,6 +746,117 @@ void orc_fw_cliques_sync(int64_t n, int64_t c, const int32_t *cl, int k, int T, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* CPSample (Sec. 5, Alg. 4): greedy colouring, k-color paths, sampling.    */
+/* Readings:                                                                */
+/*  S1  The colouring is the linear-time greedy one, vertices taken by      */
+/*      decreasing rank of the vertex order (the densest core first), each  */
+/*      given the smallest colour no coloured neighbour has.                */
+/*  S2  A k-color path is a path v_1 .. v_k with strictly increasing colours */
+/*      (a clique's members, sorted by colour, form exactly one such path,  */
+/*      so uniform paths give uniform cliques).                              */
+/*  S3  A sample is one uniformly drawn path: index R in [0, #paths), from  */
+/*      one SplitMix64 word x as R = floor((x >> 11) * #paths / 2^53), then */
+/*      the path of rank R in the order (start vertex id, then each next    */
+/*      vertex in adjacency order) -- samples are drawn with replacement.    */
+/*  S4  The sampled set of k-cliques is a set: repeated cliques count once. */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_rank_desc(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return g_key1[x] > g_key1[y] ? -1 : g_key1[x] < g_key1[y];
+}
+
+/* S1: colour[v] for every vertex; returns the number of colours. */
+int orc_color_greedy(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *rank,
+                     int32_t *color) {
+    int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    unsigned char *used = (unsigned char *)calloc((size_t)n + 2, 1);
+    for (int64_t v = 0; v < n; ++v) { ord[v] = (int32_t)v; color[v] = -1; }
+    g_key1 = rank;
+    qsort(ord, (size_t)n, sizeof(int32_t), cmp_rank_desc);
+    int ncol = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t v = ord[i];
+        for (int64_t e = off[v]; e < off[v + 1]; ++e)
+            if (color[adj[e]] >= 0) used[color[adj[e]]] = 1;
+        int c = 0;
+        while (used[c]) ++c;
+        color[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+        for (int64_t e = off[v]; e < off[v + 1]; ++e)
+            if (color[adj[e]] >= 0) used[color[adj[e]]] = 0;
+    }
+    free(ord); free(used);
+    return ncol;
+}
+
+/* S2: dp[v * k + (i - 1)] = number of increasing-colour paths of i vertices
+ * starting at v (i = 1..k).  Returns ORC_OVERFLOW when a count needs more
+ * than 64 bits. */
+int orc_ccpath_dp(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *color, int k,
+                  uint64_t *dp) {
+    for (int64_t v = 0; v < n; ++v) dp[v * k] = 1;
+    for (int i = 2; i <= k; ++i)
+        for (int64_t v = 0; v < n; ++v) {
+            unsigned __int128 sum = 0;
+            for (int64_t e = off[v]; e < off[v + 1]; ++e)
+                if (color[adj[e]] > color[v]) sum += dp[(int64_t)adj[e] * k + (i - 2)];
+            if (sum >> 64) return ORC_OVERFLOW;
+            dp[v * k + (i - 1)] = (uint64_t)sum;
+        }
+    return ORC_OK;
+}
+
+static uint64_t orc_splitmix64(uint64_t seed, uint64_t index) {
+    uint64_t z = seed + (index + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* S3: t samples; sample j draws word j of the SplitMix64 generator seeded
+ * with `seed`.  paths[j * k ..] receives the path's vertices, clique[j] = 1
+ * when they are pairwise adjacent.  *total receives the number of paths. */
+int orc_ccpath_sample(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *color,
+                      int k, const uint64_t *dp, int64_t t, uint64_t seed, int32_t *paths,
+                      uint8_t *clique, uint64_t *total) {
+    unsigned __int128 tot = 0;
+    for (int64_t v = 0; v < n; ++v) tot += dp[v * k + (k - 1)];
+    if (tot >> 64) return ORC_OVERFLOW;
+    *total = (uint64_t)tot;
+    for (int64_t j = 0; j < t; ++j) {
+        int32_t *P = paths + j * k;
+        clique[j] = 0;
+        if (tot == 0) { for (int i = 0; i < k; ++i) P[i] = -1; continue; }
+        const uint64_t x = orc_splitmix64(seed, (uint64_t)j);
+        uint64_t R = (uint64_t)(((unsigned __int128)(x >> 11) * tot) >> 53);
+        int64_t v = 0;
+        while (R >= dp[v * k + (k - 1)]) { R -= dp[v * k + (k - 1)]; ++v; }
+        P[0] = (int32_t)v;
+        for (int i = k - 1; i >= 1; --i) {         /* i vertices still to choose */
+            for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+                const int32_t w = adj[e];
+                if (color[w] <= color[v]) continue;
+                const uint64_t c = dp[(int64_t)w * k + (i - 1)];
+                if (R < c) { v = w; break; }
+                R -= c;
+            }
+            P[k - i] = (int32_t)v;
+        }
+        int ok = 1;
+        for (int a = 0; a < k && ok; ++a)
+            for (int b = a + 2; b < k && ok; ++b) {   /* consecutive ones are adjacent */
+                int found = 0;
+                for (int64_t e = off[P[a]]; e < off[P[a] + 1]; ++e)
+                    if (adj[e] == P[b]) { found = 1; break; }
+                ok = found;
+            }
+        clique[j] = (uint8_t)ok;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* O5: extraction (the final sort and prefix step of Alg. 2, R4, R5).      */
 /* ------------------------------------------------------------------------ */
 static const double *g_key_d;
