@@ -288,6 +288,29 @@ def alg1_vs_sct(K, torch, dev, n, src, dst, k, T):
     return out
 
 
+def cpsample_run(K, torch, dev, n, src, dst, k, t=1 << 26, T=30, seed=5):
+    """CPSample (Alg. 4) on the benchmark graph: t sampled k-color paths,
+    Alg. 1 over the sampled cliques, sampled-density prefix; samples/s over
+    the whole call (colouring, path counts, sampling, set, iterations,
+    extraction), and how the returned set compares with the SCT solver's."""
+    o = K.make_opts(precision=PRECISIONS["int64"])
+    K.kdss_cpsample(n, src, dst, k, 1 << 16, T, seed, o)   # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    a.record(stream)
+    res = K.kdss_cpsample(n, src, dst, k, t, T, seed, o)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ref = K.kdss_solve(n, src, dst, k, 200)
+    inter = len(set(res["ids"].tolist()) & set(ref["ids"].tolist()))
+    return {"t": t, "T": T, "ms": ms, "samples_per_s": t / (ms / 1e3), **res["stats"],
+            "istar": res["istar"], "sampled_count": res["count"],
+            "overlap_with_sct_result": inter / max(len(ref["ids"]), 1),
+            "sct_result_istar": ref["istar"]}
+
+
 def large_rmat_report(K, torch, dev):
     """The large single graph (R-MAT scale 24, edge factor 32, planted
     200-node near-clique, k = 6, seed 4, T = 100): the edge list goes to the
@@ -621,6 +644,10 @@ def main():
         st.free()
         sct.free()
         extras["async_vs_sync"] = async_vs_sync(K, torch, dev, n, src, dst, k, T)
+        try:
+            extras["cpsample"] = cpsample_run(K, torch, dev, n, src, dst, k)
+        except K.KdssError as e:
+            extras["cpsample"] = {"error": str(e)}
         try:
             extras["alg1_vs_sct"] = alg1_vs_sct(K, torch, dev, n, src, dst, k, T)
         except K.KdssError as e:

@@ -231,6 +231,41 @@ kdss_status kdss_fw_cliques(kdss_sct *s, kdss_state **state, int32_t T, const kd
  */
 kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacity, int64_t *count);
 
+/* Counters of a kdss_cpsample run. */
+typedef struct kdss_cpsample_stats {
+    uint64_t paths_total;     /* k-color paths (strictly increasing colours) */
+    int64_t samples;          /* paths drawn (t) */
+    int64_t samples_clique;   /* drawn paths that are k-cliques */
+    int64_t cliques;          /* distinct k-cliques among them (the sample set) */
+    int32_t colors;           /* colours of the greedy colouring */
+    int32_t reserved;
+} kdss_cpsample_stats;
+
+/*
+ * kdss_cpsample -- CPSample (Sec. 5, Alg. 4): t uniform k-color paths (the
+ * CCPATH sampler: a greedy colouring, then paths whose colours increase; a
+ * clique's members sorted by colour form exactly one such path, so uniform
+ * paths give uniform cliques), the set of k-cliques among them, T iterations
+ * of Alg. 1 over that set (synchronous form), and the prefix of the nodes
+ * sorted by r with the largest |C_k(V_i) & set| / i.  No SCT is built.
+ * Readings: the colouring is greedy by decreasing rank of the build order
+ * (opts->order), each vertex taking the smallest colour its coloured
+ * neighbours lack; sample j takes word j of SplitMix64 seeded with `seed`,
+ * x, and the path of rank floor((x >> 11) * #paths / 2^53) in the order
+ * (start id, then adjacency order); repeated cliques count once.
+ *   g     : input graph, as for kdss_build_sct.
+ *   k     : 2..16.   t : samples, 0..2^31.   T : Alg. 1 iterations >= 0.
+ *   out   : istar, ids (library-owned, kdss_result_free), count_lo =
+ *           |C_k(V_i*) & set|, density = count_lo / istar (the sampled
+ *           density), upper_bound = max r / T.
+ *   stats : may be NULL.
+ * Errors: INVALID_ARG, BAD_GRAPH, OVERFLOW (path counts beyond 63 bits),
+ *   UNSUPPORTED (a vertex with more than 4095 higher-ranked neighbours), OOM,
+ *   CUDA.
+ */
+kdss_status kdss_cpsample(const kdss_graph_desc *g, int32_t k, int64_t t, int32_t T, uint64_t seed,
+                          const kdss_opts *opts, kdss_result *out, kdss_cpsample_stats *stats);
+
 /*
  * kdss_state_copy_r -- copy r to a host buffer of n entries: uint64 for
  * KDSS_INT64 (cumulative r_t), double for KDSS_FP64 (cumulative r_t), float

@@ -87,6 +87,11 @@ class kdss_server_stats(C.Structure):
                [("peak_active", C.c_int32), ("reserved", C.c_int32)]
 
 
+class kdss_cpsample_stats(C.Structure):
+    _fields_ = [("paths_total", C.c_uint64), ("samples", C.c_int64), ("samples_clique", C.c_int64),
+                ("cliques", C.c_int64), ("colors", C.c_int32), ("reserved", C.c_int32)]
+
+
 class kdss_timing(C.Structure):
     _fields_ = [("fw_kernel_ms", C.c_double), ("step_kernel_ms", C.c_double),
                 ("fw_launches", C.c_int64), ("step_launches", C.c_int64)]
@@ -146,6 +151,8 @@ def load(build_if_missing: bool = False):
             "kdss_kernel_launches": (i64, []),
             "kdss_fw_iterate_noalloc": (i32, [vp, vp, i32, i32, vp]),
             "kdss_fw_cliques": (i32, [vp, P(vp), i32, P(kdss_opts)]),
+            "kdss_cpsample": (i32, [P(kdss_graph_desc), i32, i64, i32, C.c_uint64, P(kdss_opts),
+                                    P(kdss_result), P(kdss_cpsample_stats)]),
             "kdss_sct_copy_cliques": (i32, [vp, vp, i64, P(i64)]),
             "kdss_server_create": (i32, [P(kdss_server_opts), P(vp)]),
             "kdss_server_submit": (i32, [vp, P(kdss_query), P(i64)]),
@@ -352,6 +359,25 @@ def kdss_fw_cliques(s: Sct, state: State | None, T: int, opts: kdss_opts | None 
     if state is None:
         return State(p.value)
     return state
+
+
+def kdss_cpsample(n, src, dst, k, t, T, seed, opts: kdss_opts | None = None) -> dict:
+    """CPSample (Alg. 4): sampled k-color paths, Alg. 1 over the sampled
+    cliques, sampled-density prefix.  Returns the result dict with 'stats'."""
+    L = load()
+    g, keep = _graph_desc(n, src, dst)
+    r = kdss_result()
+    st = kdss_cpsample_stats()
+    rc = L.kdss_cpsample(C.byref(g), int(k), int(t), int(T), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                         C.byref(opts or make_opts()), C.byref(r), C.byref(st))
+    try:
+        _check(rc)
+        out = _result_dict(r)
+        out["stats"] = {f: getattr(st, f) for f, _ in kdss_cpsample_stats._fields_ if f != "reserved"}
+        return out
+    finally:
+        L.kdss_result_free(C.byref(r))
+        del keep
 
 
 def kdss_sct_copy_cliques(s: Sct) -> np.ndarray:

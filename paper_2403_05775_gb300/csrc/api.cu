@@ -19,6 +19,8 @@ namespace kdss {
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
 void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts *opts,
                  std::vector<kdss_status> &status, std::vector<std::string> &msgs);
+void cpsample_run(const Ctx &c, const kdss_graph_desc &g, int k, int64_t t, int T, uint64_t seed,
+                  int order, kdss_result *out, kdss_cpsample_stats *stats);
 }
 
 namespace {
@@ -288,6 +290,26 @@ kdss_status kdss_fw_cliques(kdss_sct *s, kdss_state **state, int32_t T, const kd
         sync(c);
     } catch (...) {
         if (created) { delete *state; *state = nullptr; }
+        throw;
+    }
+    API_END
+}
+
+kdss_status kdss_cpsample(const kdss_graph_desc *g, int32_t k, int64_t t, int32_t T, uint64_t seed,
+                          const kdss_opts *opts, kdss_result *out, kdss_cpsample_stats *stats) {
+    API_BEGIN
+    if (!out) fail(KDSS_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof *out);
+    check_graph(g);
+    const int order = opts ? opts->order : KDSS_ORDER_PEEL;
+    if (order != KDSS_ORDER_PEEL && order != KDSS_ORDER_CORE)
+        fail(KDSS_ERR_INVALID_ARG, "unknown vertex order");
+    Ctx c = make_ctx(opts);
+    try {
+        cpsample_run(c, *g, k, t, T, seed, order, out, stats);
+    } catch (...) {
+        free(out->ids);
+        memset(out, 0, sizeof *out);
         throw;
     }
     API_END

@@ -282,6 +282,64 @@ void launch_prefix_events_all(const Ctx &c, const SctDev &s, const int32_t *pos,
     launch_events<32, 32>(c, s, 4, pos, hist, fhist);
 }
 
+namespace {
+// each clique of an explicit set adds 1 at prefix length (last position of
+// its members) + 1
+__global__ void k_clique_events(int64_t c, const int32_t *__restrict__ cl, int k,
+                                const int32_t *__restrict__ pos, unsigned long long *hist) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < c;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int mx = -1;
+        for (int j = 0; j < k; ++j) mx = max(mx, pos[cl[(size_t)q * k + j]]);
+        atomicAdd(hist + (mx + 1), 1ull);
+    }
+}
+}  // namespace
+
+// The final step of Alg. 4: nodes sorted by r (non-increasing, ties by id),
+// |C_k(V_i) & set| for every prefix from an explicit clique set, and the
+// prefix of largest count / i (largest i on ties).  INT64 state.
+void extract_from_cliques(const Ctx &c, const StateDev &st, const int32_t *cl, int64_t count,
+                          int k, kdss_result *out) {
+    const int64_t n = st.n;
+    memset(out, 0, sizeof *out);
+    out->t_used = st.t;
+    out->T = st.t;
+    if (n == 0) return;
+    const int B = 256;
+    DBuf<uint64_t> keys(c, (size_t)n);
+    DBuf<int32_t> order(c, (size_t)n);
+    unsigned long long mb = 0;
+    to_host(c, &mb, st.maxr.p, 1);
+    k_keys_u64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mb, keys.p, order.p);
+    KDSS_LAUNCH_CHECK();
+    radix_sort_u64(c, keys.p, order.p, n, {{0, bit_length(mb)}});
+    keys.reset();
+    DBuf<int32_t> pos(c, (size_t)n);
+    k_positions<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, order.p, pos.p);
+    KDSS_LAUNCH_CHECK();
+    DBuf<unsigned long long> hist(c, (size_t)n + 2);
+    zero(c, hist.p, (n + 2) * 8);
+    if (count > 0) {
+        k_clique_events<<<grid_for(c, count, B, 4), B, 0, c.stream>>>(count, cl, k, pos.p, hist.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    inclusive_scan_u64_async(c, (const uint64_t *)hist.p, (uint64_t *)hist.p, n + 1);
+    unsigned long long best = 0;
+    long long istar = 0;
+    best_prefix(c, n, hist.p, &best, &istar);
+    out->istar = istar;
+    out->count_lo = best;
+    out->density = istar > 0 ? (double)best / (double)istar : 0.0;
+    out->upper_bound = st.t > 0 ? (double)mb / st.t : 0.0;
+    if (istar > 0) {
+        out->ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)istar);
+        if (!out->ids) fail(KDSS_ERR_OOM, "host allocation of the result ids");
+        to_host(c, out->ids, order.p, (size_t)istar);
+        std::sort(out->ids, out->ids + istar);
+    }
+}
+
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out) {
     const int64_t n = s.n;
     memset(out, 0, sizeof *out);
