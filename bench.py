@@ -311,6 +311,36 @@ def cpsample_run(K, torch, dev, n, src, dst, k, t=1 << 26, T=30, seed=5):
             "sct_result_istar": ref["istar"]}
 
 
+def k_agnostic(K, torch, dev, n, src, dst, kmax=8):
+    """One k-agnostic SCT of the benchmark graph restricted to k = 3..kmax,
+    against one k-pruned build per k: wall time of each (device work
+    synchronised) and the sizes."""
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, 1e3 * (time.perf_counter() - t0)
+
+    K.kdss_build_sct(n, src, dst, 3).free()                 # warm-up
+    multi, ms_multi = wall(lambda: K.kdss_build_sct_multi(n, src, dst, kmax))
+    info = K.kdss_sct_info(multi)
+    per_k = {}
+    for k in range(3, kmax + 1):
+        a, ms_r = wall(lambda: K.kdss_sct_restrict(multi, k))
+        b, ms_b = wall(lambda: K.kdss_build_sct(n, src, dst, k))
+        ia = K.kdss_sct_info(a)
+        per_k[k] = {"restrict_ms": ms_r, "build_ms": ms_b, "eta_k": ia["eta_k"],
+                    "same_size": ia["eta_k"] == K.kdss_sct_info(b)["eta_k"]}
+        a.free()
+        b.free()
+    multi.free()
+    return {"k_max": kmax, "multi_build_ms": ms_multi, "multi_pairs": info["eta_k"],
+            "multi_nodes": info["L_k"], "per_k": per_k,
+            "all_k_restrict_ms": ms_multi + sum(v["restrict_ms"] for v in per_k.values()),
+            "all_k_build_ms": sum(v["build_ms"] for v in per_k.values())}
+
+
 def large_rmat_report(K, torch, dev):
     """The large single graph (R-MAT scale 24, edge factor 32, planted
     200-node near-clique, k = 6, seed 4, T = 100): the edge list goes to the
@@ -591,7 +621,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_pbupdate_int (one FW iteration, all length classes)",
+                     "kernel": "PBUpdate pass of one FW iteration (k_pb_fast + k_pb_slow + length-class group kernels)",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu,
@@ -644,6 +674,10 @@ def main():
         st.free()
         sct.free()
         extras["async_vs_sync"] = async_vs_sync(K, torch, dev, n, src, dst, k, T)
+        try:
+            extras["k_agnostic"] = k_agnostic(K, torch, dev, n, src, dst)
+        except K.KdssError as e:
+            extras["k_agnostic"] = {"error": str(e)}
         try:
             extras["cpsample"] = cpsample_run(K, torch, dev, n, src, dst, k)
         except K.KdssError as e:

@@ -185,6 +185,29 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
                                 int32_t *round_, int32_t *rank);
 
 /*
+ * kdss_build_sct_multi -- a k-agnostic SCT: steps A1-A3 with the pruning of
+ * Lemma 2.5 relaxed to |V_h| <= k_max and |V(P)| >= 2, so that the handle
+ * holds P_k for every k in [2, k_max] at once (P_k = the pairs with
+ * |V_h| <= k <= |V(P)|, Sec. 2).  It is built once per graph and cut to one
+ * k by kdss_sct_restrict; the iteration and extraction calls refuse it
+ * (INVALID_ARG).  kdss_sct_info reports every kept pair (eta, L), k = k_max
+ * and c_k = c_{k_max}.
+ * Errors: as kdss_build_sct.
+ */
+kdss_status kdss_build_sct_multi(const kdss_graph_desc *g, int32_t k_max, const kdss_opts *opts,
+                                 kdss_sct **out);
+
+/*
+ * kdss_sct_restrict -- P_k of a k-agnostic SCT (2 <= k <= its k_max): the
+ * pairs with |V_h| <= k <= |V(P)|, in the stored order, with the binomial
+ * table and c_k of k -- the same pairs kdss_build_sct(g, k) emits.
+ * *out is a new, ordinary SCT handle (free it with kdss_sct_free).
+ * Errors: INVALID_ARG (not k-agnostic, k out of range), OVERFLOW, OOM, CUDA.
+ */
+kdss_status kdss_sct_restrict(const kdss_sct *multi, int32_t k, const kdss_opts *opts,
+                              kdss_sct **out);
+
+/*
  * kdss_fw_iterate -- step A4-A5: T Frank-Wolfe iterations of Alg. 2 with the
  * PBUpdate rule of Alg. 3 over every pair, all pairs of iteration t reading
  * r_{t-1} (synchronous form); the remainder units of Alg. 3 (fewer than the

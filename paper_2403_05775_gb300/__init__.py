@@ -151,6 +151,8 @@ def load(build_if_missing: bool = False):
             "kdss_kernel_launches": (i64, []),
             "kdss_fw_iterate_noalloc": (i32, [vp, vp, i32, i32, vp]),
             "kdss_fw_cliques": (i32, [vp, P(vp), i32, P(kdss_opts)]),
+            "kdss_build_sct_multi": (i32, [P(kdss_graph_desc), i32, P(kdss_opts), P(vp)]),
+            "kdss_sct_restrict": (i32, [vp, i32, P(kdss_opts), P(vp)]),
             "kdss_cpsample": (i32, [P(kdss_graph_desc), i32, i64, i32, C.c_uint64, P(kdss_opts),
                                     P(kdss_result), P(kdss_cpsample_stats)]),
             "kdss_sct_copy_cliques": (i32, [vp, vp, i64, P(i64)]),
@@ -298,6 +300,23 @@ def kdss_build_sct(n, src, dst, k, opts: kdss_opts | None = None) -> Sct:
     out = C.c_void_p()
     _check(L.kdss_build_sct(C.byref(g), int(k), C.byref(opts or make_opts()), C.byref(out)))
     del keep
+    return Sct(out.value)
+
+
+def kdss_build_sct_multi(n, src, dst, k_max, opts: kdss_opts | None = None) -> Sct:
+    """A k-agnostic SCT (every pair with |V_h| <= k_max), to be restricted."""
+    L = load()
+    g, keep = _graph_desc(n, src, dst)
+    out = C.c_void_p()
+    _check(L.kdss_build_sct_multi(C.byref(g), int(k_max), C.byref(opts or make_opts()), C.byref(out)))
+    del keep
+    return Sct(out.value)
+
+
+def kdss_sct_restrict(multi: Sct, k, opts: kdss_opts | None = None) -> Sct:
+    """P_k of a k-agnostic SCT as an ordinary SCT handle."""
+    out = C.c_void_p()
+    _check(load().kdss_sct_restrict(multi.ptr, int(k), C.byref(opts or make_opts()), C.byref(out)))
     return Sct(out.value)
 
 

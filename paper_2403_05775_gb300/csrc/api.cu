@@ -71,7 +71,8 @@ int64_t sct_bytes(const kdss_sct *h) {
                      s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + s.binom.bytes());
 }
 
-kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts, kdss_sct **out) {
+kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts, kdss_sct **out,
+                       int klo = -1) {
     API_BEGIN
     if (!out) fail(KDSS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -85,7 +86,8 @@ kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opt
     try {
         h->ctx = c;
         build_graph(c, *g, order, h->g);
-        build_sct(c, h->g, k, h->s);
+        build_sct(c, h->g, k, h->s, klo);
+        if (klo >= 0 && klo < k) h->kmax_multi = k;
         h->m = h->g.nadj / 2;
         h->degeneracy = h->g.degeneracy;
         h->max_out = h->g.max_out;
@@ -121,6 +123,35 @@ extern "C" {
 kdss_status kdss_build_sct(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts,
                            kdss_sct **out) {
     return build_impl(g, k, opts, out);
+}
+
+kdss_status kdss_build_sct_multi(const kdss_graph_desc *g, int32_t k_max, const kdss_opts *opts,
+                                 kdss_sct **out) {
+    return build_impl(g, k_max, opts, out, 2);
+}
+
+kdss_status kdss_sct_restrict(const kdss_sct *multi, int32_t k, const kdss_opts *opts,
+                              kdss_sct **out) {
+    API_BEGIN
+    if (!multi || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (multi->kmax_multi <= 0) fail(KDSS_ERR_INVALID_ARG, "not a k-agnostic SCT (kdss_build_sct_multi)");
+    if (k < 2 || k > multi->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, k_max of the SCT]");
+    Ctx c = make_ctx(opts);
+    kdss_sct *h = new kdss_sct();
+    try {
+        h->ctx = c;
+        sct_restrict(c, multi->s, k, h->s);
+        h->m = multi->m;
+        h->degeneracy = multi->degeneracy;
+        h->max_out = multi->max_out;
+        sync(c);
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    API_END
 }
 
 kdss_status kdss_sct_from_pairs(int64_t n, int32_t k, int64_t npairs, const int64_t *pair_off,
@@ -221,6 +252,7 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
 kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
     API_BEGIN
     if (!s || !state) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
     Ctx c = make_ctx(opts);
     bool created = false;
@@ -256,6 +288,7 @@ kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacit
                                   int64_t *count) {
     API_BEGIN
     if (!s || !count) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (capacity < 0 || (capacity > 0 && !cliques)) fail(KDSS_ERR_INVALID_ARG, "bad output buffer");
     if (s->nclq < 0) expand_cliques(s->ctx, s->s, s->cliques, s->nclq);
     *count = s->nclq;
@@ -267,6 +300,7 @@ kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacit
 kdss_status kdss_fw_cliques(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
     API_BEGIN
     if (!s || !state) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
     Ctx c = make_ctx(opts);
     if (s->nclq < 0) expand_cliques(s->ctx, s->s, s->cliques, s->nclq);
@@ -338,6 +372,7 @@ kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opt
                          kdss_result *out) {
     API_BEGIN
     if (!s || !st || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (st->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
     Ctx c = make_ctx(opts);
     extract_prefix(c, s->s, st->st, out);

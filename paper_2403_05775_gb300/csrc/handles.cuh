@@ -11,6 +11,7 @@ struct kdss_sct {
     int64_t m = 0;
     int degeneracy = 0;
     int max_out = 0;
+    int kmax_multi = 0;           // > 0: a k-agnostic SCT for k <= kmax_multi (restrict first)
     kdss::DBuf<int32_t> cliques;  // explicit k-clique list (expanded on first use)
     int64_t nclq = -1;            // its length, -1 before expansion
 };

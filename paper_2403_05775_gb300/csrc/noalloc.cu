@@ -58,6 +58,7 @@ extern "C" kdss_status kdss_fw_iterate_noalloc(const kdss_sct *s, uint64_t *r, i
                                                int32_t T, void *stream) {
     try {
         if (!s || !r) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+        if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
         if (T < 0 || t_done < 0) fail(KDSS_ERR_INVALID_ARG, "T and t_done must be >= 0");
         const SctDev &sd = s->s;
         int dev = 0;

@@ -98,7 +98,7 @@ struct PassOut {
 template <int MODE>
 __global__ void __launch_bounds__(SCT_THREADS)
 k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_adj,
-      const int32_t *__restrict__ vert, int k, int dmax, int S,
+      const int32_t *__restrict__ vert, int k, int klo, int dmax, int S,
       const uint64_t *__restrict__ binom, int bcols, uint32_t *gws, int use_shared,
       unsigned long long *next_item, ItemsIn items, PassOut po, int *err) {
     extern __shared__ uint32_t smem[];
@@ -135,7 +135,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
         const int64_t root = rec ? (int64_t)rec[0] : item;
         const int64_t o0 = out_off[root];
         const int d = (int)(out_off[root + 1] - o0);
-        if (!rec && d + 1 < k) continue;
+        if (!rec && d + 1 < klo) continue;
         const int W = (d + 31) >> 5;
 
         // local vertex list and its adjacency bitsets
@@ -204,13 +204,15 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
             if (fph[depth] == 0) {
                 const uint32_t cw = lane < W ? cd[lane] : 0u;
                 const int nc = (int)__reduce_add_sync(FULL, (unsigned)__popc(cw));
-                if (h > k || h + p + nc < k) { --depth; continue; }
+                if (h > k || h + p + nc < klo) { --depth; continue; }
                 if (nc == 0) {
-                    if (h <= k && k <= h + p) {
+                    if (h <= k && klo <= h + p) {
                         const int len = h + p;
                         const int cls = dev_class(len);
-                        const uint64_t nC = binom[(size_t)p * bcols + (k - h)];
-                        if (cls < 0 || nC == ~0ull) {
+                        // c_k of the hold cap k; a k-agnostic build (klo < k) keeps
+                        // pairs with fewer than k nodes and ignores the count's range
+                        const uint64_t nC = p >= k - h ? binom[(size_t)p * bcols + (k - h)] : 0ull;
+                        if (cls < 0 || (klo == k && nC == ~0ull)) {
                             if (lane == 0) atomicOr(err, cls < 0 ? DERR_CAPACITY : DERR_OVERFLOW);
                         } else if (MODE == MODE_COUNT) {
                             int over = 0;
@@ -332,7 +334,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 }
                 const int ncc = (int)__reduce_add_sync(FULL, (unsigned)__popc(child));
                 // big hold branch: becomes an item of the next level
-                if (h + 1 < k && ncc >= SPLIT_MIN && h + 1 + p + ncc >= k) {
+                if (h + 1 < k && ncc >= SPLIT_MIN && h + 1 + p + ncc >= klo) {
                     // the count pass also writes the record, at a slot taken
                     // from a cursor, while the slots last; if they run out,
                     // a spawn pass writes every record in item order
@@ -480,7 +482,8 @@ void upload_binom(const Ctx &c, int rows, int k, SctDev &out) {
 
 }  // namespace
 
-void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
+void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
+    if (klo < 0) klo = k;
     const int64_t n = g.n;
     out.k = k;
     out.n = n;
@@ -540,7 +543,7 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out) {
         zero(c, ctr.p, sizeof(unsigned long long));
         int gsz = (int)std::min<int64_t>(grid, std::max<int64_t>(1, ceil_div(L.nitems, SCT_WARPS)));
         ItemsIn in{L.nitems, L.rec.p, stride};
-        kern<<<gsz, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k, dmax,
+        kern<<<gsz, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k, klo, dmax,
                                                  S, out.binom.p, bcols, gws.p, use_shared,
                                                  ctr.p, in, po, ints.p + 1);
         KDSS_LAUNCH_CHECK();
@@ -750,6 +753,92 @@ void sct_from_pairs(const Ctx &c, int64_t n, int k, int64_t np, const int64_t *p
     out.ck_lo = hc[0];
     out.ck_hi = hc[1];
     out.max_len = maxlen;
+}
+
+namespace {
+__global__ void k_keep_flags(int64_t np, const int64_t *off, const uint8_t *h, int k, int64_t *keep,
+                             int64_t *klen) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = off[q + 1] - off[q];
+        const bool in = (int)h[q] <= k && (int64_t)k <= len;
+        keep[q] = in ? 1 : 0;
+        klen[q] = in ? len : 0;
+    }
+}
+
+// warp per kept pair: nodes (ids ascending, hold bit kept) and h to their new place
+__global__ void k_keep_copy(int64_t np, const int64_t *off, const int32_t *nodes, const uint8_t *h,
+                            const int64_t *keep, const int64_t *pidx, const int64_t *noff,
+                            int64_t *ooff, int32_t *onodes, uint8_t *oh) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = warp; q < np; q += nw) {
+        if (!keep[q]) continue;
+        const int64_t b = off[q], len = off[q + 1] - b, o = noff[q];
+        for (int64_t t = lane; t < len; t += 32) onodes[o + t] = nodes[b + t];
+        if (lane == 0) {
+            ooff[pidx[q]] = o;
+            oh[pidx[q]] = h[q];
+        }
+    }
+}
+}  // namespace
+
+void sct_restrict(const Ctx &c, const SctDev &all, int k, SctDev &out) {
+    const int64_t np = all.npairs;
+    out.k = k;
+    out.n = all.n;
+    const int B = 256;
+    DBuf<int64_t> keep(c, (size_t)std::max<int64_t>(np, 1)), klen(c, (size_t)std::max<int64_t>(np, 1));
+    DBuf<int64_t> pidx(c, (size_t)std::max<int64_t>(np, 1)), noff(c, (size_t)std::max<int64_t>(np, 1));
+    int64_t kept = 0, nn = 0;
+    if (np > 0) {
+        k_keep_flags<<<grid_for(c, np, B), B, 0, c.stream>>>(np, all.pair_off.p, all.h.p, k, keep.p, klen.p);
+        KDSS_LAUNCH_CHECK();
+        kept = exclusive_scan_i64(c, keep.p, pidx.p, np);
+        nn = exclusive_scan_i64(c, klen.p, noff.p, np);
+    }
+    out.npairs = kept;
+    out.nnodes = nn;
+    out.pair_off = DBuf<int64_t>(c, (size_t)kept + 1);
+    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nn, 1));
+    out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(kept, 1));
+    if (kept > 0) {
+        k_keep_copy<<<grid_for(c, np * 32, B), B, 0, c.stream>>>(np, all.pair_off.p, all.nodes.p, all.h.p,
+                                                               keep.p, pidx.p, noff.p, out.pair_off.p,
+                                                               out.nodes.p, out.h.p);
+        KDSS_LAUNCH_CHECK();
+    }
+    to_device(c, out.pair_off.p + kept, &nn, 1);
+    // class boundaries: kept pairs before each boundary of the source
+    for (int cl = 0; cl < NCLASS; ++cl) {
+        const int64_t b = all.class_begin[cl];
+        int64_t v = kept;
+        if (b < np) to_host(c, &v, pidx.p + b, 1);
+        out.class_begin[cl] = v;
+    }
+    out.class_begin[NCLASS] = kept;
+    // binomials for k, then c_k and the longest pair
+    upload_binom(c, std::max(all.max_len, 1) + 2, k, out);
+    DBuf<unsigned long long> ck(c, 2);
+    DBuf<int> ml(c, 2);
+    zero(c, ck.p, 2 * sizeof(unsigned long long));
+    zero(c, ml.p, 2 * sizeof(int));
+    if (kept > 0) {
+        k_pair_ck<<<grid_for(c, kept, B), B, 0, c.stream>>>(kept, out.pair_off.p, out.h.p, out.binom.p,
+                                                           k + 1, k, ck.p, ml.p, ml.p + 1);
+        KDSS_LAUNCH_CHECK();
+    }
+    unsigned long long hc[2];
+    int hm[2];
+    to_host(c, hc, ck.p, 2);
+    to_host(c, hm, ml.p, 2);
+    if (hm[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs 63 bits or more");
+    out.ck_lo = hc[0];
+    out.ck_hi = hc[1];
+    out.max_len = hm[0];
 }
 
 }  // namespace kdss

@@ -39,7 +39,11 @@ struct SctDev {
 // 63 bits or more hold ~0ull (treated as overflow by the kernels).
 std::vector<uint64_t> host_binom_table(int rows, int k);
 
-void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out);
+// klo < k: the k-agnostic form -- every pair with |V_h| <= k and at least
+// klo nodes (the pruning of Lemma 2.5 for the sizes klo..k at once).
+void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo = -1);
+// P_k of a k-agnostic SCT: the pairs with |V_h| <= k <= |V(P)|, in order.
+void sct_restrict(const Ctx &c, const SctDev &all, int k, SctDev &out);
 void sct_from_pairs(const Ctx &c, int64_t n, int k, int64_t npairs, const int64_t *pair_off,
                     const int32_t *nodes, const int32_t *h, SctDev &out);
 
