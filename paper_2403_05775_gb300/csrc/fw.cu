@@ -580,7 +580,9 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
                         continue;
                     }
                     const uint32_t qd = rem / na;
-                    if (ev == INF32 || qd < ev - L) {
+                    // the units end before the next event, or exactly at it
+                    // (then nothing is left over and L* = ev allocates the same)
+                    if (ev == INF32 || qd < ev - L || (qd == ev - L && rem == qd * na)) {
                         Ls = L + qd;
                         R = rem - qd * na;
                         done = true;
@@ -900,7 +902,7 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
                     continue;
                 }
                 const float qd = rem / (float)na;
-                if (ev == INF || L + qd < ev) {
+                if (ev == INF || L + qd <= ev) {
                     Ls = L + qd;
                     done = true;
                     break;
