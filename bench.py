@@ -380,7 +380,8 @@ def large_rmat_report(K, torch, dev):
     return out
 
 
-def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01, every=5):
+def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01, every=5,
+            flags=0):
     """The serving workload: a Poisson stream (rate 200/s, seed 5) of k-DSS
     queries on a pool of Chung-Lu graphs (the n = 1e5 workload's generator
     with n log-uniform in [1e3, 1e6]) with k uniform in {3..10}, through the
@@ -393,7 +394,8 @@ def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01,
     dpool = [(n, torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for n, s, d in pool]
     torch.cuda.synchronize()
     tickets = [None] * count
-    with K.Server(precision=PRECISIONS["fp64"], check_every=every, eps_stop=eps) as srv:
+    with K.Server(precision=PRECISIONS["fp64"], check_every=every, eps_stop=eps,
+                  flags=flags) as srv:
         t0 = time.perf_counter()
 
         def feed():
@@ -694,6 +696,10 @@ def main():
             extras["serving"] = serving(K, torch, dev)
         except K.KdssError as e:
             extras["serving"] = {"error": str(e)}
+        try:   # the same stream, queries iterating in place
+            extras["serving_in_place"] = serving(K, torch, dev, flags=K.KDSS_FLAG_ASYNC)
+        except K.KdssError as e:
+            extras["serving_in_place"] = {"error": str(e)}
         line["extras"] = extras
 
     if rank == 0:

@@ -16,7 +16,9 @@
  * 1 - rho'_max / max r-hat (Thms 3.5-3.6) is <= eps_stop, evaluated after
  * every check_every of its own iterations -- the rule of kdss_solve with the
  * same options, so a query's result does not depend on the other queries it
- * ran with (bit for bit for KDSS_INT64 / KDSS_FP64).
+ * ran with (bit for bit for KDSS_INT64 / KDSS_FP64).  With KDSS_FLAG_ASYNC
+ * the queries iterate in place (kdss_fw_iterate's in-place form), which
+ * reaches the gap in fewer iterations; results then depend on the schedule.
  * All device memory comes from cudaMallocAsync on the server's streams
  * (allocator callbacks in the options are not used); the caller's stream in
  * the options is not used either.
@@ -40,6 +42,9 @@ typedef struct kdss_server_opts {
     double eps_stop;        /* certificate gap to stop at (0: run T iterations) */
     int64_t hbm_budget;     /* bytes of SCTs + states resident at once
                                (0: 80% of the device memory free at creation) */
+    uint32_t flags;         /* KDSS_FLAG_ASYNC: in-place iterations (integer rule
+                               only; results then depend on the schedule) */
+    int32_t reserved;
 } kdss_server_opts;
 
 typedef struct kdss_query_timing {

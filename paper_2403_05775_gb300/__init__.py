@@ -71,7 +71,8 @@ class kdss_result(C.Structure):
 
 class kdss_server_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("order", C.c_int32), ("check_every", C.c_int32),
-                ("max_active", C.c_int32), ("eps_stop", C.c_double), ("hbm_budget", C.c_int64)]
+                ("max_active", C.c_int32), ("eps_stop", C.c_double), ("hbm_budget", C.c_int64),
+                ("flags", C.c_uint32), ("reserved", C.c_int32)]
 
 
 class kdss_query_timing(C.Structure):
@@ -507,10 +508,11 @@ class Server:
     ticket, wait() returns the result dict with a ``timing`` entry."""
 
     def __init__(self, precision=KDSS_INT64, order=KDSS_ORDER_PEEL, check_every=5,
-                 eps_stop=0.0, max_active=0, hbm_budget=0):
+                 eps_stop=0.0, max_active=0, hbm_budget=0, flags=0):
         L = load()
         o = kdss_server_opts(precision=precision, order=order, check_every=check_every,
-                             max_active=max_active, eps_stop=eps_stop, hbm_budget=int(hbm_budget))
+                             max_active=max_active, eps_stop=eps_stop, hbm_budget=int(hbm_budget),
+                             flags=int(flags))
         p = C.c_void_p()
         _check(L.kdss_server_create(C.byref(o), C.byref(p)))
         self.ptr = p

@@ -1446,6 +1446,20 @@ void fw_run_async(const Ctx &c, const SctDev &s, StateDev &st, int T) {
     st.t += T;
 }
 
+// One in-place iteration's launches for a query of the server (slow-list
+// reset and PBUpdate scattering into r itself); the server refreshes the max
+// of r with a step over the zero delta before it extracts.
+void fw_enqueue_inplace(const Ctx &c, const SctDev &s, StateDev &st) {
+    if (st.precision == KDSS_FP32K)
+        fail(KDSS_ERR_UNSUPPORTED, "in-place iterations exist for the integer rule only");
+    KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), c.stream));
+    if (st.precision == KDSS_FP64)
+        launch_pbupdate_int<double>(c, s, (double *)st.r.p, (double *)st.r.p, st.ovf_list.p,
+                                    st.ovf_count.p, st.err.p);
+    else
+        launch_pbupdate_int<uint64_t>(c, s, st.r.p, st.r.p, st.ovf_list.p, st.ovf_count.p, st.err.p);
+}
+
 // ---- several SCTs over disjoint node ranges sharing one state (batches) ----
 
 void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, StateDev &st) {

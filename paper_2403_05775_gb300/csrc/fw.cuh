@@ -40,6 +40,7 @@ void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st);
 void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile);
 // in-place (asynchronous) iterations of the integer rule: pairs add into r
 void fw_run_async(const Ctx &c, const SctDev &s, StateDev &st, int T);
+void fw_enqueue_inplace(const Ctx &c, const SctDev &s, StateDev &st);
 // batches: several SCTs over disjoint node ranges of one state
 void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, StateDev &st);
 void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off);

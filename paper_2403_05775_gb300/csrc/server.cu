@@ -181,6 +181,7 @@ void kdss_server::iterate_loop() {
     long long nk = 0;
     bool dirty = true;
     const int every = o.check_every;
+    const bool inplace = (o.flags & KDSS_FLAG_ASYNC) != 0;
     auto drop_exec = [&] {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
@@ -221,8 +222,12 @@ void kdss_server::iterate_loop() {
                     drop_exec();
                     nk = fw_capture(wctx, &exec, [&](const Ctx &cc) {
                         for (Query *q : active) {
-                            fw_enqueue_group(cc, q->sct->s, *q->st, 0);
-                            fw_enqueue_step_range(cc, *q->st, 0, q->sct->s.n, true);
+                            if (inplace) {
+                                fw_enqueue_inplace(cc, q->sct->s, *q->st);
+                            } else {
+                                fw_enqueue_group(cc, q->sct->s, *q->st, 0);
+                                fw_enqueue_step_range(cc, *q->st, 0, q->sct->s.n, true);
+                            }
                         }
                     });
                     dirty = false;
@@ -261,6 +266,8 @@ void kdss_server::iterate_loop() {
                         kdss_result r;
                         memset(&r, 0, sizeof r);
                         try {
+                            // in place: the max of r for the bound (zero delta)
+                            if (inplace) fw_enqueue_step_range(wctx, *q->st, 0, q->sct->s.n, true);
                             extract_prefix(wctx, q->sct->s, *q->st, &r);
                         } catch (const Error &e) {
                             qs = e.code;
@@ -332,6 +339,8 @@ kdss_status kdss_server_create(const kdss_server_opts *o, kdss_server **out) {
         if (o->order != KDSS_ORDER_PEEL && o->order != KDSS_ORDER_CORE)
             fail(KDSS_ERR_INVALID_ARG, "unknown vertex order");
         if (o->check_every < 1) fail(KDSS_ERR_INVALID_ARG, "check_every must be >= 1");
+        if ((o->flags & KDSS_FLAG_ASYNC) && o->precision == KDSS_FP32K)
+            fail(KDSS_ERR_INVALID_ARG, "in-place iterations need the integer rule");
         if (o->max_active < 0 || o->hbm_budget < 0 || o->eps_stop < 0.0)
             fail(KDSS_ERR_INVALID_ARG, "negative max_active, hbm_budget or eps_stop");
         std::unique_ptr<kdss_server> s(new kdss_server());

@@ -146,3 +146,22 @@ def test_solve_stop_rule_matches_fixed_T_prefix():
     b = K.kdss_solve(n, s, d, 5, a["t_used"])
     for f in ("istar", "count", "upper_bound", "rho_prime", "gap"):
         assert a[f] == b[f]
+
+
+def test_in_place_server_keeps_the_invariants():
+    """KDSS_FLAG_ASYNC: queries iterate in place; the schedule decides the
+    exact r, so the checks are the facts that hold for any schedule: every
+    query runs T iterations (no stop rule), its bound covers its rho', and
+    it extracts the density of the synchronous solve within 1%."""
+    qs = _queries()[:9]
+    with K.Server(precision=K.KDSS_INT64, check_every=5, flags=K.KDSS_FLAG_ASYNC) as srv:
+        got = [srv.wait(t) for t in [srv.submit(*q) for q in qs]]
+    for q, g in zip(qs, got):
+        assert g["status"] == K.KDSS_OK and g["t_used"] == q[4]
+        assert g["rho_prime"] <= g["upper_bound"] * (1 + 1e-12)
+        a = K.kdss_solve(*q)
+        if a["density"] > 0:
+            assert g["density"] >= 0.99 * a["density"]
+    with pytest.raises(K.KdssError) as e:
+        K.Server(precision=K.KDSS_FP32K, flags=K.KDSS_FLAG_ASYNC)
+    assert e.value.code == K.KDSS_ERR_INVALID_ARG
