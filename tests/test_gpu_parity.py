@@ -158,6 +158,43 @@ def test_fw_every_length_class_is_bit_exact(maxlen):
     assert res["ids"].tolist() == want["ids"].tolist()
 
 
+def _many_short_pairs(n, npairs, k, seed):
+    """npairs pairs of k..32 distinct nodes of [0, n), n prime: pair q is the
+    progression a_q + j b_q (mod n), j < len_q, with b_q != 0."""
+    rng = np.random.default_rng(seed)
+    ln = rng.integers(k, 33, size=npairs)
+    a = np.repeat(rng.integers(0, n, size=npairs), ln)
+    b = np.repeat(rng.integers(1, n, size=npairs), ln)
+    po = np.zeros(npairs + 1, np.int64)
+    po[1:] = np.cumsum(ln)
+    j = np.arange(po[-1]) - np.repeat(po[:-1], ln)
+    nodes = ((a + j * b) % n).astype(np.int32)
+    h = rng.integers(0, k + 1, size=npairs).astype(np.int32)
+    return dict(pair_off=po, nodes=nodes, h=h)
+
+
+def test_fw_pipelined_slow_walk_is_bit_exact():
+    """With at least 64 short pairs per warp of the slow kernels' grid (152
+    SMs x 8 blocks x 8 warps) the slow kernels pipeline their loads across
+    pairs: r_T bit-exact for INT64 and FP64, the FP32 rule within 1e-5 of the
+    FP64 continuous oracle over a short horizon."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n, k, T = 20011, 4, 6
+    sc = _many_short_pairs(n, 64 * 8 * 8 * sms + 12345, k, 5)
+    sct = K.kdss_sct_from_pairs(n, k, sc["pair_off"], sc["nodes"], sc["h"])
+    want = O.fw_sync_par(n, sc, k, T)
+    for prec in (K.KDSS_INT64, K.KDSS_FP64):
+        st = K.kdss_fw_iterate(sct, None, T, K.make_opts(precision=prec))
+        r, _ = K.kdss_state_copy_r(st, n, prec)
+        assert np.array_equal(r.astype(np.uint64), want)
+    T32 = 3
+    r32, _ = K.kdss_state_copy_r(_fp32_state(sct, T32), n, K.KDSS_FP32K)
+    r64 = O.fw_cont(n, sc, k, T32) / T32
+    err = np.max(np.abs(r32.astype(np.float64) - r64)) / max(np.max(np.abs(r64)), 1e-300)
+    assert err <= FP32_RTOL, err
+
+
 def test_fw_large_counts_are_bit_exact():
     """Pairs of 24-32 nodes sharing a hub with k = 14: per-pair counts up to
     C(31, 13) ~ 2e8 push r beyond 2^32 within the run (64-bit arithmetic in
