@@ -599,13 +599,11 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
         // levels relative to the lowest node that can receive: 32-bit when
         // the spread and n_C fit in 31 bits (the usual case).  64-bit min and
         // max as two 32-bit warp reductions (high word, then low word).
-        const uint64_t vb = cj > 0 ? rj : ~0ull, vt = cj > 0 ? rj : 0ull;
+        const uint64_t vb = cj > 0 ? rj : ~0ull;
         const uint32_t bh = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32));
         const uint32_t bl = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32) == bh ? (uint32_t)vb : 0xffffffffu);
-        const uint32_t th = __reduce_max_sync(FULL_, (uint32_t)(vt >> 32));
-        const uint32_t tl = __reduce_max_sync(FULL_, (uint32_t)(vt >> 32) == th ? (uint32_t)vt : 0u);
-        const uint64_t base = ((uint64_t)bh << 32) | bl, top = ((uint64_t)th << 32) | tl;
-        if (top - base < (1ull << 31) && nC < (1ull << 31)) {
+        const uint64_t base = ((uint64_t)bh << 32) | bl;
+        if (__all_sync(FULL_, cj == 0 || rj - base < (1ull << 31)) && nC < (1ull << 31)) {
             const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
             // The walk of Alg. 3 with warp-uniform state: at water level L the
             // receiving nodes are those with rl <= L < rl + cl; the level rises
@@ -630,16 +628,19 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
                         L = ev;
                         continue;
                     }
-                    const uint32_t qd = rem / na;
                     // the units end before the next event, or exactly at it
-                    // (then nothing is left over and L* = ev allocates the same)
-                    if (ev == INF32 || qd < ev - L || (qd == ev - L && rem == qd * na)) {
+                    // (then nothing is left over and L* = ev allocates the
+                    // same): floor(rem / na) < ev - L, or rem = (ev - L) na,
+                    // which is rem <= (ev - L) na; one division at the end
+                    const uint64_t span = (uint64_t)(ev - L) * na;
+                    if (ev == INF32 || rem <= span) {
+                        const uint32_t qd = rem / na;
                         Ls = L + qd;
                         R = rem - qd * na;
                         done = true;
                         break;
                     }
-                    rem -= (ev - L) * na;
+                    rem -= (uint32_t)span;
                     L = ev;
                 }
                 if (done) {
