@@ -66,6 +66,11 @@ typedef int32_t kdss_status;
 #define KDSS_FLAG_PROFILE 1u        /* time the FW kernels of every 8th iteration with CUDA events */
 #define KDSS_FLAG_KEEP_GRAPH 2u     /* keep the CSR, cores and order in the SCT handle */
 #define KDSS_FLAG_ASYNC 4u          /* kdss_fw_iterate: pairs update r in place (see there) */
+/* Failure injection for tests of the bounded device waits: the peeling
+ * kernel's grid barriers wait for one block more than the grid holds, with a
+ * 1 ms limit, so every block gives up at its first barrier, the kernel returns
+ * and the build fails with KDSS_ERR_TIMEOUT.  Nothing else is affected. */
+#define KDSS_FLAG_TEST_BARRIER_TIMEOUT 8u
 
 typedef void *(*kdss_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*kdss_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
@@ -380,11 +385,15 @@ int64_t kdss_kernel_launches(void);
  *            the current device.
  *   r      : caller-owned device array of n uint64, the cumulative r after
  *            t_done iterations (zeros for t_done = 0); updated in place to r
- *            after t_done + T iterations.
+ *            after t_done + T iterations.  Its first and last elements must
+ *            be device (or managed) memory of the current device
+ *            (cudaPointerGetAttributes); otherwise INVALID_ARG, before any
+ *            launch.
  *   t_done : iterations already in r (only bounds the exact range of r).
  *   T      : iterations to run, T >= 0.
- *   stream : cudaStream_t the work is ordered on; the call returns after that
- *            stream has finished it.
+ *   stream : cudaStream_t the work is ordered on.  The call is synchronous:
+ *            it reads the device error word back and waits for the stream
+ *            before it returns.
  * Scratch: the per-iteration delta and the work lists live in one fixed
  * device array of 16 MiB inside the library, which every GPU that loads the
  * library holds until the process exits.  It fits graphs with
@@ -394,8 +403,10 @@ int64_t kdss_kernel_launches(void);
  * contents; each call clears what must start at zero.  All calls share it:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  No cudaMalloc, cudaFree or
+ * array's device address (cudaGetSymbolAddress) and caches it with the
+ * device's current context; make that first call before any stream capture.
+ * A call in a new context of the device (after cudaDeviceReset) looks the
+ * address up again.  No cudaMalloc, cudaFree or
  * allocating library routine is called.
  * Errors: INVALID_ARG (NULL, T < 0, sizes above the scratch, another device),
  *   OVERFLOW, CUDA.

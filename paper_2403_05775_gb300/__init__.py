@@ -38,6 +38,7 @@ KDSS_ORDER_CORE = 1
 KDSS_FLAG_PROFILE = 1
 KDSS_FLAG_KEEP_GRAPH = 2
 KDSS_FLAG_ASYNC = 4
+KDSS_FLAG_TEST_BARRIER_TIMEOUT = 8
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -487,9 +488,17 @@ def kdss_fw_iterate_noalloc(s: Sct, r_dev, t_done: int, T: int, stream=None) -> 
     values, given as a CUDA tensor of 8-byte elements or a raw device
     pointer), using only the library's fixed scratch area -- for callers that
     cannot allocate device memory while they iterate."""
-    ptr = r_dev.data_ptr() if hasattr(r_dev, "data_ptr") else int(r_dev)
-    if hasattr(r_dev, "element_size") and r_dev.element_size() != 8:
-        raise ValueError("r must hold 8-byte elements")
+    if hasattr(r_dev, "data_ptr"):
+        n = kdss_sct_info(s)["n"]
+        if not getattr(r_dev, "is_cuda", False):
+            raise KdssError(KDSS_ERR_INVALID_ARG, "r must be a CUDA tensor")
+        if r_dev.element_size() != 8 or not r_dev.is_contiguous():
+            raise KdssError(KDSS_ERR_INVALID_ARG, "r must be contiguous with 8-byte elements")
+        if r_dev.numel() < n:
+            raise KdssError(KDSS_ERR_INVALID_ARG, f"r holds {r_dev.numel()} values, the SCT has n = {n}")
+        ptr = r_dev.data_ptr()
+    else:
+        ptr = int(r_dev)   # a raw device pointer: the library checks where it points
     if stream is None:
         t = _torch()
         stream = t.cuda.current_stream() if t is not None else None

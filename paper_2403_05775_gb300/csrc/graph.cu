@@ -79,10 +79,12 @@ constexpr int PEEL_THREADS = 1024;
 __global__ void __launch_bounds__(PEEL_THREADS, 1)
 k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
        int32_t *deg, int32_t *rnd, int32_t *core, int32_t *fa, int32_t *fb, PeelCtl *ctl,
-       uint64_t timeout_ns) {
+       uint64_t timeout_ns, unsigned int phantom) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const unsigned int nb = gridDim.x;
+    // phantom > 0 (failure-injection test only): the barriers wait for blocks
+    // that do not exist, so the first wait expires in every block
+    const unsigned int nb = gridDim.x + phantom;
     int32_t *cur = fa, *nxt = fb;
     int level = 0, round = 0;
     int64_t removed = 0;
@@ -309,12 +311,18 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
         int grid = (int)std::min<int64_t>((int64_t)c.num_sms,
                                           std::max<int64_t>(1, ceil_div(n, PEEL_THREADS)));
         uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per barrier wait
+        unsigned int phantom = 0;
+        if (c.flags & KDSS_FLAG_TEST_BARRIER_TIMEOUT) {  // failure injection: 1 ms waits that expire
+            timeout_ns = 1000ull * 1000;
+            phantom = 1;
+        }
         int64_t nn = n;
         const int64_t *offp = out.off.p;
         const int32_t *adjp = out.adj.p;
         int32_t *degp = deg.p, *rndp = out.rnd.p, *corep = out.core.p, *fap = fa.p, *fbp = fb.p;
         PeelCtl *ctlp = ctl.p;
-        void *args[] = {&nn, &offp, &adjp, &degp, &rndp, &corep, &fap, &fbp, &ctlp, &timeout_ns};
+        void *args[] = {&nn, &offp, &adjp, &degp, &rndp, &corep, &fap, &fbp, &ctlp, &timeout_ns,
+                        &phantom};
         KDSS_CUDA(cudaLaunchCooperativeKernel((const void *)k_peel, dim3(grid), dim3(PEEL_THREADS),
                                               args, 0, c.stream));
         KDSS_LAUNCH_CHECK();

@@ -54,6 +54,7 @@ struct Ctx {
     void *actx = nullptr;
     int num_sms = 0;
     int device = 0;
+    uint32_t flags = 0;   // kdss_opts.flags of the call
 };
 
 Ctx make_ctx(const kdss_opts *o);

@@ -26,14 +26,37 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void *g_addr[MAX_DEVICES] = {};
+void *g_addr_ctx[MAX_DEVICES] = {};  // the context each cached address belongs to
+
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent,
+// reached through the runtime's entry-point query so that the library needs
+// no link against the driver library); nullptr when it cannot be queried.
+void *current_context() {
+    using fn_t = int (*)(void **);
+    static fn_t fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (fn_t) nullptr;
+        }
+        return reinterpret_cast<fn_t>(f);
+    }();
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 // Device address of the scratch array on `dev` (the current device).  In host
 // code the array's name stands for a host-side shadow, not device memory, so
-// the address is looked up once per device and cached.
+// the address is looked up once per device and context and cached; a new
+// context on the device (after cudaDeviceReset) triggers a new lookup.
 void *scratch_address(int dev) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (dev < 0 || dev >= MAX_DEVICES) fail(KDSS_ERR_UNSUPPORTED, "device index out of range");
-    if (!g_addr[dev]) {
+    void *ctx = current_context();
+    if (!g_addr[dev] || g_addr_ctx[dev] != ctx) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -42,8 +65,34 @@ void *scratch_address(int dev) {
                                     cudaGetErrorString(e));
         }
         g_addr[dev] = p;
+        g_addr_ctx[dev] = ctx;
     }
     return g_addr[dev];
+}
+
+// r must be device (or managed) memory of `dev` from its first to its last
+// element; a host pointer or another device's memory would make the kernels
+// fault or write where they must not.
+void check_r_on_device(const uint64_t *r, int64_t n, int dev) {
+    if (n <= 0) return;
+    for (const uint64_t *p : {r, r + (n - 1)}) {
+        cudaPointerAttributes a{};
+        const cudaError_t e = cudaPointerGetAttributes(&a, p);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(KDSS_ERR_INVALID_ARG, std::string("r: cudaPointerGetAttributes failed: ") +
+                                           cudaGetErrorString(e));
+        }
+        const bool dev_mem = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+        if (!dev_mem || a.device != dev) {
+            char buf[200];
+            snprintf(buf, sizeof buf,
+                     "r must be device memory of device %d holding n = %lld uint64 values "
+                     "(element %s is %s)", dev, (long long)n, p == r ? "0" : "n - 1",
+                     dev_mem ? "on another device" : "not device memory");
+            fail(KDSS_ERR_INVALID_ARG, buf);
+        }
+    }
 }
 
 inline size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -65,6 +114,7 @@ extern "C" kdss_status kdss_fw_iterate_noalloc(const kdss_sct *s, uint64_t *r, i
         KDSS_CUDA(cudaGetDevice(&dev));
         if (dev != s->ctx.device)
             fail(KDSS_ERR_INVALID_ARG, "the SCT lives on another device than the current one");
+        check_r_on_device(r, sd.n, dev);
         // exactness of the cumulative r: r_t(u) <= t * c_k
         const long double ck = (long double)sd.ck_lo + (long double)sd.ck_hi * 18446744073709551616.0L;
         if ((long double)((int64_t)t_done + T) * ck >= 9.2e18L)

@@ -37,6 +37,7 @@ Ctx make_ctx(const kdss_opts *o) {
         c.alloc = o->alloc;
         c.free = o->free;
         c.actx = o->alloc_ctx;
+        c.flags = o->flags;
         if ((c.alloc == nullptr) != (c.free == nullptr))
             fail(KDSS_ERR_INVALID_ARG, "opts.alloc and opts.free must be set together");
     }

@@ -45,6 +45,25 @@ MUTANTS = {
     "binomial_off_by_one": (
         "v = v * (u128)(a - b + i) / (u128)i;",
         "v = v * (u128)(a - b + i + 1) / (u128)i;"),
+    "cont_delta_not_cleared_between_iterations": (
+        "memset(dr, 0, sizeof(double) * (size_t)n);", ""),
+    "cont_pairs_update_r_in_place": (
+        "rc = orc_pbupdate_cont(len, ids, rv, hcnt[q], k, dv);\n            if (rc) break;\n"
+        "            for (int i = 0; i < len; ++i) dr[ids[i]] += dv[i];",
+        "rc = orc_pbupdate_cont(len, ids, rv, hcnt[q], k, dv);\n            if (rc) break;\n"
+        "            for (int i = 0; i < len; ++i) r[ids[i]] += dv[i];"),
+    "seq_reads_the_previous_iterate": (
+        "            for (int i = 0; i < len; ++i) rv[i] = r[ids[i]];\n"
+        "            rc = orc_pbupdate_alg3(len, ids, rv, hcnt[q], k, dv);\n"
+        "            if (rc) break;\n"
+        "            for (int i = 0; i < len; ++i) r[ids[i]] += dv[i];",
+        "            if (q == 0) { static uint64_t *snap; snap = (uint64_t *)realloc(snap, "
+        "sizeof(uint64_t) * (size_t)(n + 1)); memcpy(snap, r, sizeof(uint64_t) * (size_t)n); "
+        "g_snap = snap; }\n"
+        "            for (int i = 0; i < len; ++i) rv[i] = g_snap[ids[i]];\n"
+        "            rc = orc_pbupdate_alg3(len, ids, rv, hcnt[q], k, dv);\n"
+        "            if (rc) break;\n"
+        "            for (int i = 0; i < len; ++i) r[ids[i]] += dv[i];"),
     "plateau_gap_ignored": (
         "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
         "if (nC / (uint64_t)na < w)"),
@@ -63,6 +82,10 @@ PINS = [
     P.test_argmax_takes_the_largest_prefix_on_ties,
     lambda: P.test_brute_force_small_graphs(3),
     P.test_alg1_synchronous_over_explicit_cliques,
+    P.test_g1_inplace_iterations_match_hand_trace,
+    P.test_g1_continuous_iterations_match_hand_trace,
+    P.test_g1_continuous_rule_converges_to_sct_cp_optimum,
+    P.test_fw_cont_and_fw_seq_invariants_and_weak_duality,
 ]
 
 
@@ -72,7 +95,10 @@ def test_pins_catch_planted_mistake(name, tmp_path, monkeypatch):
     src = open(O.SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not unique"
     path = tmp_path / "mutant.c"
-    path.write_text(src.replace(old, new))
+    mutated = src.replace(old, new)
+    if "g_snap" in new:   # the stale-read mutant keeps its snapshot pointer at file scope
+        mutated = mutated.replace("int orc_fw_seq(", "static const uint64_t *g_snap;\nint orc_fw_seq(", 1)
+    path.write_text(mutated)
     so = tmp_path / "libmutant.so"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", str(so),
                            str(path), "-lm"])

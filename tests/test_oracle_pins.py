@@ -17,6 +17,7 @@ import synth
 from conftest import load_golden
 
 G = load_golden("g1_example.txt")
+GI = load_golden("g1_iterations.txt")
 
 
 def _pairs_from_golden(lines):
@@ -104,6 +105,56 @@ def test_g1_converges_to_sct_cp_optimum():
     sc = O.sct(n, off, adj, rank, vert, 3)
     T = 3000
     r = O.fw_sync(n, sc, 3, T) / T
+    assert abs(r[0] - 1.0) < 1e-3
+    assert np.all(np.abs(r[1:] - 4.0 / 3.0) < 1e-3)
+
+
+def _g1_pairs_in_listed_order():
+    """The five pairs of Example 2.2 as arrays, in the order listed there,
+    hold nodes first (the oracle's pair layout)."""
+    po, nodes, h = [0], [], []
+    for ln in G["pair"]:
+        a, b = ln.split("|")
+        hold, piv = [int(x) for x in a.split()], [int(x) for x in b.split()]
+        nodes += hold + piv
+        h.append(len(hold))
+        po.append(len(nodes))
+    return {"pair_off": np.array(po, np.int64), "nodes": np.array(nodes, np.int32),
+            "h": np.array(h, np.int32)}
+
+
+def test_g1_inplace_iterations_match_hand_trace():
+    """Alg. 2 as printed (each pair reads r as the pairs before it in the
+    same iteration left it), Alg. 3 with the remainder to the lowest ids: the
+    first two iterations on G1 equal the trace derived by hand in
+    tests/golden/g1_iterations.txt, which differs from the synchronous form
+    already at t = 1."""
+    sc = _g1_pairs_in_listed_order()
+    for t, key in ((1, "seq_r1"), (2, "seq_r2")):
+        want = [int(x) for x in GI[key][0].split()]
+        assert O.fw_seq(7, sc, 3, t).tolist() == want
+    assert O.fw_sync(7, sc, 3, 1).tolist() != [int(x) for x in GI["seq_r1"][0].split()]
+
+
+def test_g1_continuous_iterations_match_hand_trace():
+    """Synchronous iterations of the continuous water-filling rule (reading
+    R11 of the FP32 path): r_1 and r_2 on G1 equal the exact fractions
+    derived by hand in tests/golden/g1_iterations.txt."""
+    sc = _g1_pairs_in_listed_order()
+    for t, key in ((1, "cont_r1"), (2, "cont_r2")):
+        want = np.array([float(Fraction(x)) for x in GI[key][0].split()])
+        got = O.fw_cont(7, sc, 3, t)
+        assert np.max(np.abs(got - want)) <= 1e-12 * np.max(want)
+
+
+def test_g1_continuous_rule_converges_to_sct_cp_optimum():
+    """The continuous rule reaches the same SCT-CP optimum of G1 as the
+    integer rule: r_T / T -> r* = (1, 4/3 x 6)."""
+    n, s, d = _g1()
+    off, adj, core, rnd, dg, rank, vert = _graph(n, s, d, O.ORDER_CORE)
+    sc = O.sct(n, off, adj, rank, vert, 3)
+    T = 3000
+    r = O.fw_cont(n, sc, 3, T) / T
     assert abs(r[0] - 1.0) < 1e-3
     assert np.all(np.abs(r[1:] - 4.0 / 3.0) < 1e-3)
 
@@ -292,6 +343,70 @@ def test_fw_invariants_and_weak_duality():
                 assert best_rp <= Fraction(int(r.max()), t)
                 i = O.argmax_density(lo, hi)
                 assert Fraction(int(lo[i]), i) <= Fraction(int(rcp.max()), 50)
+
+
+def test_fw_cont_and_fw_seq_invariants_and_weak_duality():
+    """Lemma 3.1 and Thms 3.5-3.6 for the continuous rule (synchronous) and
+    for the in-place integer iterations: sum_u r_t(u) = t c_k (to 1e-9
+    relative in FP64, exactly for the integers), r_t(u) <= t cnt_k(u) with
+    cnt_k(u) from the explicit clique list, and max_u r_t(u)/t >= the best
+    rho'(S) over all subsets S (brute force) at every t."""
+    for seed in range(4):
+        n, s, d = _planted(13 + seed % 2, 0.25, 6, 700 + seed)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        for k in (3, 4):
+            sc = O.sct(n, off, adj, rank, vert, k)
+            cl = O.list_cliques(n, off, adj, k)
+            ck = len(cl)
+            if ck == 0:
+                continue
+            cnt = np.bincount(cl.reshape(-1), minlength=n)
+            pm, ph = sc["pair_off"], sc["h"]
+            pmasks, pw = [], []
+            for q in range(len(ph)):
+                seg = sc["nodes"][pm[q]:pm[q + 1]]
+                pmasks.append(sum(1 << int(v) for v in seg))
+                pw.append(O.binom(len(seg) - ph[q], k - ph[q]))
+            _, pn, pd, _ = O.brute_best(n, pmasks, pw)
+            rho_p = Fraction(pn, pd)
+            for t in (1, 2, 3, 6, 25):
+                rc = O.fw_cont(n, sc, k, t)
+                assert abs(rc.sum() - t * ck) <= 1e-9 * t * ck
+                assert np.all(rc <= t * cnt * (1 + 1e-12) + 1e-9)
+                assert rc.max() / t >= float(rho_p) * (1 - 1e-12)
+                rs = O.fw_seq(n, sc, k, t)
+                assert int(rs.astype(object).sum()) == t * ck
+                assert np.all(rs.astype(np.int64) <= t * cnt)
+                assert Fraction(int(rs.max()), t) >= rho_p
+            # both reach the SCT-CP bound: max r / T tends to max rho'(S)
+            T = 3000
+            assert float(O.fw_cont(n, sc, k, T).max()) / T <= float(rho_p) * 1.02 + 1e-9
+            assert float(O.fw_seq(n, sc, k, T).max()) / T <= float(rho_p) * 1.02 + 1e-9
+
+
+def test_fw_seq_equals_synchronous_on_node_disjoint_pairs():
+    """When no two pairs share a node, no pair can see another's update, so
+    the in-place and synchronous iterations coincide (integer rule)."""
+    rng = random.Random(21)
+    po, nodes, h = [0], [], []
+    nxt = 0
+    for _ in range(40):
+        ln = rng.randint(3, 9)
+        hh = rng.randint(1, 3)
+        nodes += list(range(nxt, nxt + ln))
+        nxt += ln
+        h.append(hh)
+        po.append(len(nodes))
+    sc = {"pair_off": np.array(po, np.int64), "nodes": np.array(nodes, np.int32),
+          "h": np.array(h, np.int32)}
+    for k in (3, 4):
+        ok = [q for q in range(len(h)) if h[q] <= k <= po[q + 1] - po[q]]
+        sub = {"pair_off": np.array([0] + list(np.cumsum([po[q + 1] - po[q] for q in ok])),
+                                    np.int64),
+               "nodes": np.concatenate([sc["nodes"][po[q]:po[q + 1]] for q in ok]),
+               "h": np.array([h[q] for q in ok], np.int32)}
+        r0 = np.array([rng.randint(0, 5) for _ in range(nxt)], np.uint64)
+        assert np.array_equal(O.fw_seq(nxt, sub, k, 9, r0), O.fw_sync(nxt, sub, k, 9, r0))
 
 
 def test_prefix_counts_from_pairs_equal_explicit_list():

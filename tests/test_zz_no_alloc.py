@@ -10,6 +10,7 @@ scratch array.  This file is collected last on purpose.
 import numpy as np
 import pytest
 
+import oracle as O
 import paper_2403_05775_gb300 as K
 import synth
 
@@ -28,6 +29,14 @@ def _r_of(tensor):
     return tensor.cpu().numpy().view(np.uint64)
 
 
+def _oracle_r(n, s, d, k, T):
+    """r_T of the oracle's synchronous iterations (rule I) on its own SCT."""
+    off, adj = O.csr(n, s, d)
+    core, rnd, _ = O.peel(n, off, adj)
+    rank, vert = O.order(n, core, rnd)
+    return O.fw_sync(n, O.sct(n, off, adj, rank, vert, k), k, T)
+
+
 def test_noalloc_matches_fw_iterate_on_consecutive_calls(torch_cuda):
     torch = torch_cuda
     n, s, d, _ = synth.chung_lu(3000, 12.0, 2.4, 9, plant_size=25, plant_prob=0.85)
@@ -35,6 +44,10 @@ def test_noalloc_matches_fw_iterate_on_consecutive_calls(torch_cuda):
     sct = K.kdss_build_sct(n, s, d, k)
     ref_T = K.kdss_state_copy_r(K.kdss_fw_iterate(sct, None, T), n, K.KDSS_INT64)[0]
     ref_2T = K.kdss_state_copy_r(K.kdss_fw_iterate(sct, None, 2 * T), n, K.KDSS_INT64)[0]
+    # the existing entry point and the oracle agree, so both calls below are
+    # checked against the oracle as well
+    assert np.array_equal(ref_T, _oracle_r(n, s, d, k, T))
+    assert np.array_equal(ref_2T, _oracle_r(n, s, d, k, 2 * T))
     r = torch.zeros(n, dtype=torch.int64, device="cuda")
     K.kdss_fw_iterate_noalloc(sct, r, 0, T)                  # first call
     assert np.array_equal(_r_of(r), ref_T)
@@ -75,3 +88,25 @@ def test_noalloc_rejects_inputs_beyond_its_scratch(torch_cuda):
     K.kdss_fw_iterate_noalloc(sct2, r2, 0, 10)
     ref = K.kdss_state_copy_r(K.kdss_fw_iterate(sct2, None, 10), n2, K.KDSS_INT64)[0]
     assert np.array_equal(_r_of(r2), ref)
+
+
+def test_noalloc_rejects_r_outside_device_memory(torch_cuda):
+    """A host buffer, a CPU tensor or a tensor shorter than n is refused with
+    INVALID_ARG before any kernel runs, and the entry point stays usable."""
+    torch = torch_cuda
+    n, s, d = synth.g1()
+    sct = K.kdss_build_sct(n, s, d, 3)
+    host = np.zeros(n, np.uint64)
+    with pytest.raises(K.KdssError) as e:        # raw host pointer: checked by the library
+        K.kdss_fw_iterate_noalloc(sct, host.ctypes.data, 0, 1)
+    assert e.value.code == K.KDSS_ERR_INVALID_ARG and "device memory" in str(e.value)
+    with pytest.raises(K.KdssError) as e:        # CPU tensor
+        K.kdss_fw_iterate_noalloc(sct, torch.zeros(n, dtype=torch.int64), 0, 1)
+    assert e.value.code == K.KDSS_ERR_INVALID_ARG
+    with pytest.raises(K.KdssError) as e:        # too short
+        K.kdss_fw_iterate_noalloc(sct, torch.zeros(n - 1, dtype=torch.int64, device="cuda"), 0, 1)
+    assert e.value.code == K.KDSS_ERR_INVALID_ARG
+    assert not host.any()
+    r = torch.zeros(n, dtype=torch.int64, device="cuda")
+    K.kdss_fw_iterate_noalloc(sct, r, 0, 10)
+    assert np.array_equal(_r_of(r), _oracle_r(n, s, d, 3, 10))
