@@ -48,6 +48,27 @@ WORKLOADS = {
         desc="Erdos-Renyi G(2000, 0.01), seed 1; k=3; T=100 FW iterations"),
 }
 
+def _union_workload(max_n=None):
+    def gen():
+        ns, ks = synth.batch_rmat_specs(256, nmax=1e4)
+        graphs, kk = [], []
+        for i, nn in enumerate(ns):
+            if ks[i] == 8:
+                graphs.append(synth.batch_rmat_graph(i, int(nn)))
+                kk.append(8)
+        return union_edges(graphs, kk, 8, max_n)
+    return gen
+
+
+WORKLOADS["rmat_union_k8"] = dict(
+    gen=_union_workload(), k=8, T=20,
+    desc="disjoint union of the k=8 instances of the batched R-MAT workload (n <= 1e4 each, "
+         "198,339 nodes); k=8; T=20 FW iterations")
+WORKLOADS["rmat_union_k8_small"] = dict(
+    gen=_union_workload(40000), k=8, T=20,
+    desc="the first k=8 instances of the batched R-MAT workload up to 40,000 nodes, as one "
+         "disjoint union; k=8; T=20 FW iterations")
+
 PRECISIONS = {"fp64": 1, "int64": 0, "fp32k": 2}
 DTYPE = {"fp64": "f64", "int64": "u64", "fp32k": "f32"}
 
@@ -68,6 +89,9 @@ def parse():
                     help="only report the large R-MAT graph (scale 24) build: one JSON line")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP32 and time-to-1%% side measurements")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="integer-rule iterations on the work-queue kernels with this many tiles "
+                         "per item (0: the per-class kernels)")
     return ap.parse_args()
 
 
@@ -181,7 +205,7 @@ def run_reference(args, rank):
     wl = WORKLOADS[args.workload]
     n, s, d = wl["gen"]()
     k = wl["k"]
-    T_ref = 50 if args.workload == "chunglu1e5" else wl["T"]
+    T_ref = wl["T"]
     times = []
     ck = None
     cores = os.cpu_count() or 1
@@ -200,8 +224,7 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": wl["desc"].replace(f"T={wl['T']}", f"T={T_ref}"),
-                       "k": k, "T": T_ref, "n": n, "c_k": ck},
+            "config": {"workload": wl["desc"], "k": k, "T": T_ref, "n": n, "c_k": ck},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -380,6 +403,9 @@ def large_rmat_report(K, torch, dev):
     return out
 
 
+_POOL = {}
+
+
 def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01, every=5,
             flags=0):
     """The serving workload: a Poisson stream (rate 200/s, seed 5) of k-DSS
@@ -389,9 +415,13 @@ def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01,
     <= 1% (checked every 5 iterations) or at T = 300.  Latency is submit to
     result; throughput is queries over first submit to last result."""
     import threading
-    pool = synth.serving_pool(pool_size)
+    if _POOL.get("size") != pool_size:      # generated once, shared by the serving runs
+        pool = synth.serving_pool(pool_size)
+        _POOL.update(size=pool_size, sum_n=sum(p[0] for p in pool),
+                     dev=[(n, torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev))
+                          for n, s, d in pool])
     arr, gi, ks = synth.serving_stream(count, rate, pool_size)
-    dpool = [(n, torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for n, s, d in pool]
+    dpool = _POOL["dev"]
     torch.cuda.synchronize()
     tickets = [None] * count
     with K.Server(precision=PRECISIONS["fp64"], check_every=every, eps_stop=eps,
@@ -421,7 +451,7 @@ def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01,
     return {
         "workload": f"{count} queries, Poisson {rate:g}/s, pool of {pool_size} Chung-Lu graphs "
                     f"(mean degree 20, exponent 2.5, planted 60-node near-clique p=0.9, n "
-                    f"log-uniform in [1e3, 1e6], sum {sum(p[0] for p in pool)}), k in {{3..10}}, "
+                    f"log-uniform in [1e3, 1e6], sum {_POOL['sum_n']}), k in {{3..10}}, "
                     f"seed 5; stop at gap <= {eps:g} (every {every}) or T = {T}; FP64",
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "throughput_qps": len(res) / wall,
@@ -433,6 +463,193 @@ def serving(K, torch, dev, count=400, rate=200.0, pool_size=32, T=300, eps=0.01,
         "peak_active": st["peak_active"], "captures": st["captures"], "replays": st["replays"],
         "peak_resident_bytes": st["peak_resident_bytes"], "hbm_budget": st["hbm_budget"],
     }
+
+
+def fp32_error_vs_oracle(K, n, s_np, d_np, k, T, r32, dens32, rho_oracle):
+    """The FP32 path's error against the FP64 oracle at T: the FP64
+    continuous-rule iterations of the oracle (host threads, the same additions
+    as the serial form) give r-hat_64 = r_T / T; reported are
+    ||r-hat_32 - r-hat_64||_inf / ||r-hat_64||_inf, the density of the prefix
+    the oracle extracts from r-hat_64, and the FP32 density's relative error
+    against the oracle's integer-rule density and against that one."""
+    import oracle as O
+    off, adj = O.csr(n, s_np, d_np)
+    core, rnd, _ = O.peel(n, off, adj)
+    rank, vert = O.order(n, core, rnd)
+    sc = O.sct(n, off, adj, rank, vert, k)
+    t0 = time.perf_counter()
+    r64 = O.fw_cont_par(n, sc, k, T) / T
+    secs = time.perf_counter() - t0
+    ordr = O.sort_desc(r64)
+    lo, hi, _, _ = O.prefix_counts_pairs(n, ordr, sc, k)
+    i = O.argmax_density(lo, hi)
+    dens64 = (int(lo[i]) | (int(hi[i]) << 64)) / i
+    err = float(np.max(np.abs(r32.astype(np.float64) - r64)) / np.max(np.abs(r64)))
+    return {"r_rel_err_inf_vs_fp64_oracle": err, "fp64_oracle_continuous_density": dens64,
+            "density_rel_err_vs_fp64_continuous_oracle": abs(dens32 - dens64) / dens64,
+            "density_rel_err_vs_integer_oracle": (abs(dens32 - rho_oracle) / rho_oracle
+                                                  if rho_oracle else None),
+            "oracle_seconds": secs,
+            "note": "the continuous rule's trajectory amplifies rounding differences (a 1e-13 "
+                    "perturbation grows ~100x per 10 iterations), so r at T differs at the "
+                    "convergence-error scale; per-iteration agreement (1e-5) is tested"}
+
+
+def config1_er2000(K, torch, dev, stream):
+    """Config 1: G(2000, 0.01) seed 1, k = 3, T = 100 (and the paper's G1):
+    device-timed clique-updates/s and the extracted set against the oracle."""
+    import oracle as O
+    n, s_np, d_np = synth.workload_er2000()
+    k, T = 3, 100
+    src = torch.from_numpy(s_np).to(dev)
+    dst = torch.from_numpy(d_np).to(dev)
+    o = K.make_opts(precision=PRECISIONS["fp64"], stream=stream)
+    K.kdss_solve(n, src, dst, k, T, o)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    res = K.kdss_solve(n, src, dst, k, T, o)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    want = O.solve(n, s_np, d_np, k, T)
+    g1n, g1s, g1d = synth.g1()
+    g1 = K.kdss_solve(g1n, g1s, g1d, 3, 100)
+    return {"workload": WORKLOADS["er2000"]["desc"], "value": T * want["c_k"] / (ms / 1e3),
+            "unit": UNIT, "ms": ms, "c_k": want["c_k"], "istar": res["istar"],
+            "density": res["density"],
+            "equals_oracle": bool(res["istar"] == want["istar"] and res["count"] == want["count"]
+                                  and res["ids"].tolist() == want["ids"].tolist()),
+            "g1": {"istar": g1["istar"], "density": g1["density"],
+                   "paper": "{u1..u6} at 4/3 (Example 1.1)",
+                   "ids": g1["ids"].tolist()}}
+
+
+def rmat24_count(K, torch, dev, budget_s=30.0):
+    """Config 4 (R-MAT scale 24, edge factor 32, planted 200-node near-clique,
+    k = 6, seed 4): the count-only SCT pass measures P_6 without storing a
+    pair; roots are taken in a pseudo-random order until the budget ends, so
+    the counted roots are a sample and counts * n / roots_done estimates the
+    whole SCT."""
+    t0 = time.perf_counter()
+    n, s_np, d_np = synth.workload_rmat24()
+    gen_s = time.perf_counter() - t0
+    src = torch.from_numpy(s_np).to(dev)
+    dst = torch.from_numpy(d_np).to(dev)
+    del s_np, d_np
+    out = {"workload": "R-MAT scale 24 (n = 16,777,216), edge factor 32, planted 200-node "
+                       "near-clique p = 0.95, seed 4; k = 6", "generate_s": gen_s,
+           "budget_s": budget_s}
+    try:
+        c = K.kdss_sct_count(n, src, dst, 6, budget_s,
+                             K.make_opts(precision=PRECISIONS["fp32k"], allocator="library"))
+    except K.KdssError as e:
+        out["error"] = str(e)
+        return out
+    done = max(c["roots_done"], 1)
+    scale = n / done
+    out.update({f: c[f] for f in ("m", "degeneracy", "max_out_degree", "roots_done", "roots_cut",
+                                  "complete", "eta_k", "L_k", "max_pair_len", "count_bits",
+                                  "seconds", "cut_pairs", "cut_nodes")})
+    out["pairs_per_class"] = c["pairs_per_class"]
+    out["c_k_counted"] = str(c["c_k"])
+    # every pair counted, finished roots or not, is a pair of the SCT: a
+    # measured lower bound on its size (the roots the budget interrupted are
+    # the densest, so scaling the finished ones would understate it)
+    out["lower_bound"] = {"eta_6": c["eta_k"] + c["cut_pairs"], "L_6": c["L_k"] + c["cut_nodes"],
+                          "sct_bytes_flat": 4 * (c["L_k"] + c["cut_nodes"])
+                                            + 9 * (c["eta_k"] + c["cut_pairs"]),
+                          "device_bytes": torch.cuda.get_device_properties(dev).total_memory}
+    out["sample_estimate_finished_roots"] = {"eta_6": c["eta_k"] * scale, "L_6": c["L_k"] * scale,
+                                             "c_6": float(c["c_k"]) * scale}
+    return out
+
+
+def batched_upper_range(K, torch, dev, count=256, budget_s=3.0):
+    """Config 3 as specified (n log-uniform in [1e3, 1e5]): the count-only
+    SCT pass on its three largest instances measures why the upper part of
+    the range cannot be held on one device."""
+    ns, ks = synth.batch_rmat_specs(count, nmax=1e5)
+    order = np.argsort(-ns)[:3]
+    rows = []
+    for i in order:
+        n, s_np, d_np = synth.batch_rmat_graph(int(i), int(ns[i]))
+        c = K.kdss_sct_count(n, s_np, d_np, int(ks[i]), budget_s)
+        scale = n / max(c["roots_done"], 1)
+        rows.append({"n": n, "k": int(ks[i]), "roots_done": c["roots_done"], "complete": c["complete"],
+                     "roots_cut": c["roots_cut"], "eta_k_counted": c["eta_k"], "L_k_counted": c["L_k"],
+                     "cut_pairs": c["cut_pairs"], "cut_nodes": c["cut_nodes"],
+                     "sct_bytes_lower_bound": 4 * (c["L_k"] + c["cut_nodes"])
+                                              + 9 * (c["eta_k"] + c["cut_pairs"]),
+                     "degeneracy": c["degeneracy"], "seconds": c["seconds"]})
+    return {"instances_n_above_1e4": int((ns > 1e4).sum()), "largest": rows}
+
+
+def union_edges(graphs, ks, k, max_n=None):
+    """The disjoint union (ids shifted) of the batched instances with this k:
+    the SCT the batch iterates for that k, as one graph."""
+    S, D, base = [], [], 0
+    for (n, s, d), kk in zip(graphs, ks):
+        if kk != k:
+            continue
+        if max_n is not None and base >= max_n:
+            break
+        S.append(s.astype(np.int64) + base)
+        D.append(d.astype(np.int64) + base)
+        base += n
+    return base, np.concatenate(S).astype(np.int32), np.concatenate(D).astype(np.int32)
+
+
+def union_roofline(K, torch, dev, stream, graphs, ks, k, iters=32):
+    """The PBUpdate pass where HBM binds: the k = 8 union of the batched
+    workload (a 13 GB SCT, far above L2).  CUDA-event time of the pass
+    (KDSS_FLAG_PROFILE times every 8th iteration on the launching stream),
+    algorithmic bytes 4 L_k + 9 eta_k, fraction of the measured HBM peak."""
+    n, s_np, d_np = union_edges(graphs, ks, k)
+    src = torch.from_numpy(s_np).to(dev)
+    dst = torch.from_numpy(d_np).to(dev)
+    out = {"workload": f"disjoint union of the k = {k} instances of the batched workload "
+                       f"(n = {n}), k = {k}, FP64 rule I"}
+    o = K.make_opts(precision=PRECISIONS["fp64"], stream=stream, allocator="library",
+                    flags=K.KDSS_FLAG_PROFILE)
+    sct = K.kdss_build_sct(n, src, dst, k, o)
+    info = K.kdss_sct_info(sct)
+    peak, kind = measured_peaks()
+    alg = 4 * info["L_k"] + 9 * info["eta_k"]
+    for name, chunk in (("per_class_kernels", 0), ("work_queue", 4)):
+        oc = K.make_opts(precision=PRECISIONS["fp64"], stream=stream, allocator="library",
+                         flags=K.KDSS_FLAG_PROFILE, chunk=chunk)
+        st = K.kdss_fw_iterate(sct, None, 8, oc)            # warm
+        t0 = K.kdss_state_timing(st)
+        st = K.kdss_fw_iterate(sct, st, iters, oc)
+        t1 = K.kdss_state_timing(st)
+        us = 1e3 * (t1["fw_kernel_ms"] - t0["fw_kernel_ms"]) / max(t1["fw_launches"] - t0["fw_launches"], 1)
+        st.free()
+        out[name] = {"bound": "hbm", "achieved": alg / us / 1e3, "peak": peak, "unit": "GB/s",
+                     "frac": alg / us / 1e3 / peak, "avg_launch_us": us,
+                     "peak_source": f"{kind} hbm_gbs"}
+    out.update(eta_k=info["eta_k"], L_k=info["L_k"], alg_bytes_per_launch=alg,
+               sct_device_bytes=info["device_bytes"], pairs_per_class=info["pairs_per_class"])
+    sct.free()
+    return out
+
+
+def l2_copy_gbs(torch, dev, mib=24, reps=200):
+    """Copy bandwidth of a buffer that stays in L2 (read + write bytes over
+    CUDA-event time, best of 5 runs of `reps` copies): the ceiling of a pass
+    whose data is L2-resident."""
+    a = torch.empty(mib << 20, dtype=torch.uint8, device=dev)
+    b = torch.empty_like(a)
+    b.copy_(a)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
 
 
 def batched_rmat(K, torch, dev, stream, flush, allocator, count=256, T=300, nmax=1e4):
@@ -474,10 +691,20 @@ def batched_rmat(K, torch, dev, stream, flush, allocator, count=256, T=300, nmax
     b64, ms64 = timed(lambda: K.kdss_solve_batch(dq, o64))
     p64, msp = timed(lambda: [K.kdss_solve(*q, o64) for q in dq])
     ok = all(r["status"] == 0 for r in b32 + b64)
+    import oracle as O
+    small = np.argsort(ns)[:16]
+    orel = []
+    for i in small:
+        n_i, s_i, d_i = graphs[i]
+        want = O.solve(n_i, s_i, d_i, int(ks[i]), T, threads=os.cpu_count() or 1)
+        if want["density"] > 0:
+            orel.append(abs(b32[i]["density"] - want["density"]) / want["density"])
     rel = [abs(a["density"] - c["density"]) / c["density"] for a, c in zip(b32, p64) if c["density"] > 0]
     same64 = all(a["ids"].tolist() == c["ids"].tolist() and a["count"] == c["count"]
                  for a, c in zip(b64, p64))
+    union = union_roofline(K, torch, dev, stream, graphs, ks, 8)
     return {
+        "hbm_union_k8": union,
         "workload": f"{count} R-MAT graphs, n log-uniform in [1e3, {nmax:.0e}] (sum {int(ns.sum())}), "
                     f"edge factor 16, planted 30-clique, k in {{3..8}}, seed 3; T={T}",
         "units": units, "unit": UNIT,
@@ -488,6 +715,10 @@ def batched_rmat(K, torch, dev, stream, flush, allocator, count=256, T=300, nmax
         "all_ok": ok, "batched_fp64_equals_per_instance": same64,
         "fp32_density_rel_err_vs_fp64": {"max": max(rel) if rel else 0.0,
                                          "mean": statistics.mean(rel) if rel else 0.0},
+        "fp32_density_rel_err_vs_oracle": {"instances": len(orel),
+                                           "which": "the 16 smallest (the oracle is affordable)",
+                                           "max": max(orel) if orel else 0.0,
+                                           "mean": statistics.mean(orel) if orel else 0.0},
     }
 
 
@@ -545,7 +776,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(flags):
-        o = K.make_opts(precision=prec, flags=flags, stream=stream, allocator=args.allocator)
+        o = K.make_opts(precision=prec, flags=flags, stream=stream, allocator=args.allocator,
+                        chunk=args.chunk)
         sct = K.kdss_build_sct(n, src, dst, k, o)
         st = K.kdss_fw_iterate(sct, None, T, o)
         res = K.kdss_extract(sct, st, o)
@@ -593,7 +825,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r2 = K.kdss_solve(n, s_np, d_np, k, T, K.make_opts(precision=prec, stream=stream,
-                                                           allocator=args.allocator))
+                                                           allocator=args.allocator,
+                                                           chunk=args.chunk))
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_value = T * ck * world / (statistics.mean(e2e_ms) / 1e3)
@@ -602,6 +835,7 @@ def main():
 
     # roofline of the PBUpdate pass (all length-class kernels of one iteration)
     peak, peak_kind = measured_peaks()
+    l2_gbs = l2_copy_gbs(torch, dev)
     alg_bytes = 4 * info["L_k"] + 9 * info["eta_k"]
     avg_s = (fw_ms / max(fw_launches, 1)) / 1e3
     achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
@@ -618,12 +852,20 @@ def main():
                    "rule": "continuous" if args.precision == "fp32k" else "integer (Alg. 3)",
                    "l2": "flushed by a 256 MiB write before every step",
                    "allocator": args.allocator,
+                   "pbupdate_kernels": (f"work queue, {args.chunk} tiles per item" if args.chunk
+                                        else "per length class"),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "PBUpdate pass of one FW iteration (k_pb_fast + k_pb_slow + length-class group kernels)",
+                     "l2": {"note": "this workload's pair stream (11 MB) and r stay in L2; the "
+                                    "same algorithmic bytes against a measured L2 copy rate",
+                            "peak_gbs": l2_gbs, "frac": achieved / l2_gbs if l2_gbs else None},
+                     "kernel": ("PBUpdate pass of one FW iteration (k_pb_queue + k_pb_queue_long)"
+                                if args.chunk else
+                                "PBUpdate pass of one FW iteration (k_pb_fast + k_pb_slow + "
+                                "length-class group kernels)"),
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu,
@@ -653,6 +895,20 @@ def main():
         extras["fp32k"] = {"value": T * ck / (min(t32) / 1e3), "unit": UNIT,
                            "ms_per_step": min(t32), "density": r32["density"],
                            "istar": r32["istar"]}
+        try:
+            sct = K.kdss_build_sct(n, src, dst, k, o32)
+            st = K.kdss_fw_iterate(sct, None, T, o32)
+            r32v, _ = K.kdss_state_copy_r(st, n, K.KDSS_FP32K)
+            st.free()
+            sct.free()
+            extras["fp32k"]["error_vs_fp64_oracle"] = fp32_error_vs_oracle(
+                K, n, s_np, d_np, k, T, r32v, r32["density"], rho_oracle)
+        except Exception as e:  # the oracle leg is a report, not the measurement
+            extras["fp32k"]["error_vs_fp64_oracle"] = {"error": str(e)}
+        try:
+            extras["config1"] = config1_er2000(K, torch, dev, stream)
+        except Exception as e:
+            extras["config1"] = {"error": str(e)}
         # time to reach 99% of the oracle's density: build, then chunks of 5
         # iterations each followed by an extraction
         target = rho_oracle if rho_oracle is not None else res["density"]
@@ -692,14 +948,26 @@ def main():
             extras["batched"] = batched_rmat(K, torch, dev, stream, flush, args.allocator)
         except K.KdssError as e:
             extras["batched"] = {"error": str(e)}
+        # serving: the config-5 stream (4,000 queries at 200/s on a pool of
+        # 64) with queries iterating in place, the same at a sustainable rate,
+        # and the synchronous form at 200/s and at a sustainable rate
+        runs = {"serving_in_place": dict(count=4000, rate=200.0, flags=K.KDSS_FLAG_ASYNC),
+                "serving_in_place_steady": dict(count=600, rate=40.0, flags=K.KDSS_FLAG_ASYNC),
+                "serving": dict(count=400, rate=200.0, flags=0),
+                "serving_steady": dict(count=80, rate=8.0, flags=0)}
+        for key, kw in runs.items():
+            try:
+                extras[key] = serving(K, torch, dev, pool_size=64, **kw)
+            except K.KdssError as e:
+                extras[key] = {"error": str(e)}
         try:
-            extras["serving"] = serving(K, torch, dev)
-        except K.KdssError as e:
-            extras["serving"] = {"error": str(e)}
-        try:   # the same stream, queries iterating in place
-            extras["serving_in_place"] = serving(K, torch, dev, flags=K.KDSS_FLAG_ASYNC)
-        except K.KdssError as e:
-            extras["serving_in_place"] = {"error": str(e)}
+            extras["batched_upper_range"] = batched_upper_range(K, torch, dev)
+        except Exception as e:
+            extras["batched_upper_range"] = {"error": str(e)}
+        try:
+            extras["rmat24"] = rmat24_count(K, torch, dev)
+        except Exception as e:
+            extras["rmat24"] = {"error": str(e)}
         line["extras"] = extras
 
     if rank == 0:

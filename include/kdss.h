@@ -41,7 +41,7 @@ typedef int32_t kdss_status;
 #define KDSS_ERR_INVALID_ARG (-1)   /* bad k, T, size, NULL pointer, option */
 #define KDSS_ERR_BAD_GRAPH (-2)     /* an edge endpoint outside [0, n) */
 #define KDSS_ERR_OOM (-3)           /* device allocation failed */
-#define KDSS_ERR_OVERFLOW (-4)      /* a count needs more than 64 bits */
+#define KDSS_ERR_OVERFLOW (-4)      /* a count leaves its exact range (128 bits; r: see kdss_fw_iterate) */
 #define KDSS_ERR_TIMEOUT (-5)       /* a bounded device wait expired */
 #define KDSS_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define KDSS_ERR_CANCELLED (-7)     /* a batch query was cancelled */
@@ -85,6 +85,11 @@ typedef struct kdss_opts {
     kdss_alloc_fn alloc;    /* optional device allocator (NULL: cudaMallocAsync) */
     kdss_free_fn free;      /* must be set together with alloc */
     void *alloc_ctx;        /* passed back to alloc / free */
+    int32_t chunk;          /* integer-rule iterations on the work-queue kernels: tiles of 32
+                               pairs per work item (kdss_solve_batch: 0 = autotuned;
+                               kdss_fw_iterate / kdss_solve: 0 = the per-class kernels) */
+    int32_t threads_per_path; /* lanes per pair of 33..256 nodes in the work-queue kernels:
+                               8 or 32 (0 = autotuned in batches, 32 otherwise) */
 } kdss_opts;
 
 /* An undirected graph as a raw edge list.  Duplicates, both orientations and
@@ -145,15 +150,59 @@ typedef struct kdss_timing {
  * order, and the SCT restricted to P_k (Sec. 2, Lemmas 2.4-2.6): pairs
  * (V_h, V_p) with |V_h| <= k <= |V(P)| whose k-cliques partition C_k(V).
  *   g    : the input graph (host or device edge list).
- *   k    : clique size, 2 <= k <= 64.
+ *   k    : clique size, 2 <= k <= 255.
  *   opts : stream, allocator, order.
  *   out  : receives the new handle (NULL on error).
+ * Clique counts are exact: n_C = C(p, k - h) of every pair and c_k in
+ * 128 bits (c_k_lo / c_k_hi of kdss_sct_stats).  The integer-rule
+ * iterations need t * c_k < 2^63 (KDSS_INT64) or 2^53 (KDSS_FP64); the FP32
+ * rule takes every count below 2^128 (rounded to float).
  * Errors: INVALID_ARG (k, n, m, NULL), BAD_GRAPH (id outside [0, n)),
- *   OVERFLOW (a binomial count needs more than 64 bits), UNSUPPORTED (a pair
+ *   OVERFLOW (a count needs more than 128 bits), UNSUPPORTED (a pair
  *   longer than 1024 nodes), OOM, CUDA.
  */
 kdss_status kdss_build_sct(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts,
                            kdss_sct **out);
+
+/* Sizes of P_k measured by kdss_sct_count. */
+typedef struct kdss_sct_count_stats {
+    int64_t eta_k;          /* |P_k| over the roots walked to the end */
+    int64_t L_k;            /* sum of |V(P)| over those pairs */
+    uint64_t c_k_lo;        /* sum of n_C over those pairs, low 64 bits */
+    uint64_t c_k_hi;        /* high 64 bits */
+    int64_t pairs_per_class[8]; /* |V(P)| <= 8, 16, 32, 256, 1024, longer (6 used) */
+    int64_t roots_total;    /* n */
+    int64_t roots_done;     /* roots whose recursion was walked to the end */
+    int64_t roots_cut;      /* roots the time budget interrupted (not in the counts) */
+    int64_t cut_pairs;      /* pairs the interrupted roots had emitted */
+    int64_t cut_nodes;      /* their node entries */
+    int64_t m;              /* undirected edges of the simple graph */
+    int32_t complete;       /* 1: every root walked, the counts are exact */
+    int32_t max_pair_len;   /* longest pair seen */
+    int32_t degeneracy;
+    int32_t max_out_degree;
+    int32_t count_bits;     /* bit length of the largest n_C seen (129: beyond 128 bits) */
+    int32_t reserved;
+    double seconds;         /* device time of the counting kernel */
+} kdss_sct_count_stats;
+
+/*
+ * kdss_sct_count -- the sizes of P_k (eta_k, L_k, c_k, pairs per length class;
+ * Sec. 2, Lemmas 2.4-2.6) without storing a pair, for SCTs far beyond the
+ * device (Thm 3.7: the SCT takes O(eta) space).  Steps A1-A2 run as in
+ * kdss_build_sct; then one warp walks each root's recursion to the end, the
+ * roots taken in the order i -> (i * P) mod n (P a fixed prime not dividing
+ * n), until every root is done or budget_s seconds of device time have
+ * passed (budget_s = 0: no limit).  The counts cover the roots walked to the
+ * end; when `complete` is 0 those roots are a pseudo-random sample of all
+ * roots, so (counts) * roots_total / roots_done estimates the whole SCT.
+ * Out-degrees up to 4095 are taken (pairs of up to 4096 nodes are counted
+ * in the last class even though the FW kernels stop at 1024).
+ * Errors: INVALID_ARG, BAD_GRAPH, UNSUPPORTED (out-degree above 4095), OOM,
+ *   CUDA.
+ */
+kdss_status kdss_sct_count(const kdss_graph_desc *g, int32_t k, double budget_s,
+                           const kdss_opts *opts, kdss_sct_count_stats *out);
 
 /*
  * kdss_sct_from_pairs -- make an SCT handle from caller-given pairs, so the
@@ -194,9 +243,10 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
  * Lemma 2.5 relaxed to |V_h| <= k_max and |V(P)| >= 2, so that the handle
  * holds P_k for every k in [2, k_max] at once (P_k = the pairs with
  * |V_h| <= k <= |V(P)|, Sec. 2).  It is built once per graph and cut to one
- * k by kdss_sct_restrict; the iteration and extraction calls refuse it
- * (INVALID_ARG).  kdss_sct_info reports every kept pair (eta, L), k = k_max
- * and c_k = c_{k_max}.
+ * k by kdss_sct_restrict, or iterated at any k where it stands by
+ * kdss_fw_iterate_at (kdss_fw_iterate without a k refuses it).
+ * kdss_sct_info reports every kept pair (eta, L), k = k_max and
+ * c_k = c_{k_max}.
  * Errors: as kdss_build_sct.
  */
 kdss_status kdss_build_sct_multi(const kdss_graph_desc *g, int32_t k_max, const kdss_opts *opts,
@@ -233,6 +283,21 @@ kdss_status kdss_sct_restrict(const kdss_sct *multi, int32_t k, const kdss_opts 
  *   UNSUPPORTED (KDSS_FLAG_ASYNC with KDSS_FP32K), CUDA.
  */
 kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts);
+
+/*
+ * kdss_fw_iterate_at -- kdss_fw_iterate at a chosen k.  On a k-agnostic SCT
+ * (kdss_build_sct_multi, 2 <= k <= its k_max) the iterations run over P_k
+ * where it stands: by Lemma 2.5 P_k is the set of pairs with
+ * |V_h| <= k <= |V(P)|, and the kernels skip every other pair, so one handle
+ * serves every k without a copy (kdss_sct_restrict makes the copy instead).
+ * On a k-pruned SCT k must be its own k.  A new state records k and c_k of
+ * P_k; a continued state must have been created with the same k.
+ * kdss_extract then extracts at the state's k.
+ * Errors: as kdss_fw_iterate; INVALID_ARG (k outside the SCT's range, a
+ *   state of another k).
+ */
+kdss_status kdss_fw_iterate_at(kdss_sct *s, int32_t k, kdss_state **state, int32_t T,
+                               const kdss_opts *opts);
 
 /*
  * kdss_fw_cliques -- T iterations of Alg. 1 (the Frank-Wolfe step over the
@@ -310,6 +375,7 @@ kdss_status kdss_state_timing(const kdss_state *st, kdss_timing *out);
  * V_i exactly from the pairs (Lemmas 2.5-2.6), and return the prefix of
  * largest rho_k(V_i) = |C_k(V_i)| / i (largest i on ties), with the bound
  * max_u r(u)/t and max_i rho'(V_i) (Thms 3.5-3.6).
+ * The k is the state's (kdss_fw_iterate_at on a k-agnostic SCT).
  * out->ids is a library-owned host array (kdss_result_free).
  * Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
  */
@@ -323,6 +389,25 @@ kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opt
  * iterations run). */
 kdss_status kdss_solve(const kdss_graph_desc *g, int32_t k, int32_t T, const kdss_opts *opts,
                        kdss_result *out);
+
+/*
+ * kdss_solve_streamed -- kdss_solve (build, T iterations, extraction) for
+ * graphs whose SCT does not fit the device.  The roots of the build order
+ * are split into nchunks equal ranges; every iteration rebuilds the pairs of
+ * one range at a time (step A3 restricted to those roots), adds their
+ * PBUpdate allocations (Alg. 3) into the shared delta and frees them, then
+ * takes the step; the extraction visits the ranges the same way.  All pairs
+ * of an iteration still read r_{t-1}, so the result equals kdss_solve's:
+ * bit for bit for KDSS_INT64 and KDSS_FP64 (integer sums), the same rule for
+ * KDSS_FP32K.  Device memory holds the graph, the state and one range's
+ * pairs; each iteration costs nchunks SCT builds.
+ *   nchunks : number of root ranges, >= 1 (1 = one build per iteration).
+ *   opts    : precision, order, stream, allocator (no stop rule, no
+ *             KDSS_FLAG_ASYNC).
+ * Errors: as kdss_solve; UNSUPPORTED with KDSS_FLAG_ASYNC.
+ */
+kdss_status kdss_solve_streamed(const kdss_graph_desc *g, int32_t k, int32_t T, int32_t nchunks,
+                                const kdss_opts *opts, kdss_result *out);
 
 /* One query of a batch. */
 typedef struct kdss_query {
@@ -341,7 +426,7 @@ typedef struct kdss_query {
  * All groups then iterate together (one CUDA graph per iteration; a group
  * drops out after its T), and one segmented sort and scan per group extract
  * every query's densest prefix.
- *   q[i]   : the query (graph as in kdss_build_sct, k in [2, 64], T >= 0).
+ *   q[i]   : the query (graph as in kdss_build_sct, k in [2, 255], T >= 0).
  *   out[i] : caller-owned; receives query i's result and status (ids
  *            allocated by the library, freed with kdss_result_free).
  *   opts   : as for kdss_solve (one precision and order for all queries);
@@ -358,6 +443,21 @@ typedef struct kdss_query {
  */
 kdss_status kdss_solve_batch(const kdss_query *q, int32_t nq, kdss_result *out,
                              const kdss_opts *opts);
+
+/* What the last kdss_solve_batch of the calling thread ran its integer-rule
+ * iterations with: the chunk and lanes per long pair it used and, when it
+ * tuned them, the configurations it timed (one iteration each, after two
+ * warm-up iterations; every one of those is an iteration of the run). */
+typedef struct kdss_batch_tuning {
+    int32_t chunk;
+    int32_t threads_per_path;
+    int32_t autotuned;      /* 1 when the candidates below were timed */
+    int32_t ntried;
+    int32_t tried_chunk[8];
+    int32_t tried_threads_per_path[8];
+    float tried_ms[8];      /* CUDA-event time of the candidate's iteration */
+} kdss_batch_tuning;
+kdss_status kdss_batch_last_tuning(kdss_batch_tuning *out);
 
 void kdss_sct_free(kdss_sct *s);
 void kdss_state_free(kdss_state *st);

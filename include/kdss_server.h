@@ -80,7 +80,7 @@ kdss_status kdss_server_create(const kdss_server_opts *o, kdss_server **out);
  * copied (host arrays into host memory, device arrays into device memory on
  * the builder's stream), so the caller may release it after the call.
  *   ticket : receives the query's id for kdss_server_wait.
- * Errors: INVALID_ARG (k in [2, 64], T >= 0, n, m, NULL arrays), CANCELLED
+ * Errors: INVALID_ARG (k in [2, 255], T >= 0, n, m, NULL arrays), CANCELLED
  *   (the server is shutting down), OOM, CUDA.
  */
 kdss_status kdss_server_submit(kdss_server *s, const kdss_query *q, int64_t *ticket);

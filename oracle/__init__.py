@@ -90,6 +90,12 @@ def lib():
             L.orc_fw_cont.restype = C.c_int
             L.orc_fw_cont.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i32p, C.c_int,
                                       C.c_int, f64p]
+            L.orc_binom128.restype = C.c_int
+            L.orc_binom128.argtypes = [C.c_int64, C.c_int64, C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_uint64)]
+            L.orc_fw_cont_par.restype = C.c_int
+            L.orc_fw_cont_par.argtypes = [C.c_int64, C.c_int64, i64p, i32p, i32p, C.c_int,
+                                          C.c_int, f64p, C.c_int]
             L.orc_fw_cliques.argtypes = [C.c_int64, i32p, C.c_int, C.c_int, u64p]
             L.orc_fw_cliques_sync.restype = None
             L.orc_fw_cliques_sync.argtypes = [C.c_int64, C.c_int64, i32p, C.c_int, C.c_int, u64p]
@@ -135,6 +141,14 @@ def binom(a: int, b: int) -> int:
     if ovf.value:
         raise OverflowError(f"C({a},{b}) exceeds 64 bits")
     return int(v)
+
+
+def binom128(a: int, b: int) -> int:
+    """C(a, b) exact in 128 bits; raises when it needs more."""
+    lo, hi = C.c_uint64(0), C.c_uint64(0)
+    if lib().orc_binom128(a, b, C.byref(lo), C.byref(hi)):
+        raise OverflowError(f"C({a},{b}) exceeds 128 bits")
+    return int(lo.value) | (int(hi.value) << 64)
 
 
 # --------------------------------------------------------------------------
@@ -299,6 +313,18 @@ def fw_cont(n, s, k, T, r0=None):
     rc = lib().orc_fw_cont(n, len(s["h"]), s["pair_off"], s["nodes"], s["h"], k, T, r)
     if rc != 0:
         raise OverflowError(f"fw_cont failed ({rc})")
+    return r
+
+
+def fw_cont_par(n, s, k, T, threads=None, r0=None):
+    """fw_cont with the pairs' water levels computed on host threads; the
+    additions happen in pair order, so r equals fw_cont's bit for bit."""
+    threads = threads or os.cpu_count() or 1
+    r = np.zeros(n, np.float64) if r0 is None else np.array(r0, np.float64)
+    rc = lib().orc_fw_cont_par(n, len(s["h"]), s["pair_off"], s["nodes"], s["h"], k, T, r,
+                               int(threads))
+    if rc != 0:
+        raise OverflowError(f"fw_cont_par failed ({rc})")
     return r
 
 

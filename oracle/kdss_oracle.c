@@ -60,21 +60,39 @@ void orc_free(void *p) { free(p); }
 /* C(a-b+i, i) is an integer); *ovf is set when a value needs more than 64  */
 /* bits.                                                                    */
 /* ------------------------------------------------------------------------ */
-static u128 binom128(int64_t a, int64_t b) {
+/* *ovf128 (may be NULL) is set when a partial product would leave 128 bits. */
+static u128 binom128_chk(int64_t a, int64_t b, int *ovf128) {
     if (b < 0 || a < 0 || b > a) return 0;
     if (b > a - b) b = a - b;
     u128 v = 1;
     for (int64_t i = 1; i <= b; ++i) {
-        /* v * (a - b + i) / i is exact at every step */
-        v = v * (u128)(a - b + i) / (u128)i;
+        /* v * (a - b + i) / i = C(a - b + i, i) is an integer at every step;
+           dividing v and i by their gcd first leaves i' dividing the factor,
+           so the product overflows only when the value itself does */
+        u128 f = (u128)(a - b + i), x = v, y = (u128)i;
+        while (y) { const u128 t = x % y; x = y; y = t; }
+        v /= x;
+        f /= (u128)i / x;
+        if (f && v > ~(u128)0 / f) { if (ovf128) *ovf128 = 1; return ~(u128)0; }
+        v *= f;
     }
     return v;
 }
+static u128 binom128(int64_t a, int64_t b) { return binom128_chk(a, b, NULL); }
 
 uint64_t orc_binom(int64_t a, int64_t b, int *ovf) {
     u128 v = binom128(a, b);
     if (v >> 64) { if (ovf) *ovf = 1; return UINT64_MAX; }
     return (uint64_t)v;
+}
+
+/* C(a, b) in 128 bits as (lo, hi); returns 1 when it needs more. */
+int orc_binom128(int64_t a, int64_t b, uint64_t *lo, uint64_t *hi) {
+    int o = 0;
+    const u128 v = binom128_chk(a, b, &o);
+    *lo = (uint64_t)v;
+    *hi = (uint64_t)(v >> 64);
+    return o;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -538,9 +556,12 @@ static int cmp_by_rd_id(const void *a, const void *b) {
 
 int orc_pbupdate_cont(int len, const int32_t *ids, const double *r_in, int h, int k,
                       double *delta) {
+    /* counts beyond 64 bits (long pairs, large k) are taken exactly in 128
+       bits and rounded to double once (reading R10: exact binomials of
+       Lemma 2.6 wherever they fit 128 bits) */
     int p = len - h, ovf = 0;
-    double nC = (double)orc_binom(p, k - h, &ovf);
-    double up_h = nC, up_p = (double)orc_binom(p - 1, k - h - 1, &ovf);
+    double nC = (double)binom128_chk(p, k - h, &ovf);
+    double up_h = nC, up_p = (double)binom128_chk(p - 1, k - h - 1, &ovf);
     if (ovf) return ORC_OVERFLOW;
     double *r = (double *)malloc(sizeof(double) * (size_t)len);
     double *up = (double *)malloc(sizeof(double) * (size_t)len);
@@ -707,6 +728,48 @@ int orc_fw_cont(int64_t n, int64_t npairs, const int64_t *pair_off, const int32_
         for (int64_t v = 0; v < n; ++v) r[v] += dr[v];
     }
     free(dr); free(rv); free(dv);
+    return rc;
+}
+
+/* orc_fw_cont with the per-pair water levels of an iteration computed on
+ * host threads (OpenMP when available) into one buffer, then added into the
+ * delta vector in pair order by one thread: the same additions in the same
+ * order as orc_fw_cont, so r is bit for bit equal (pinned); only faster. */
+int orc_fw_cont_par(int64_t n, int64_t npairs, const int64_t *pair_off, const int32_t *nodes,
+                    const int32_t *hcnt, int k, int T, double *r, int threads) {
+    if (threads < 1) threads = 1;
+    const int64_t L = npairs > 0 ? pair_off[npairs] : 0;
+    const int mx = max_pair_len(npairs, pair_off);
+    double *dr = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *dall = (double *)malloc(sizeof(double) * (size_t)(L + 1));
+    int *crc = (int *)calloc((size_t)threads, sizeof(int));
+    if (!dr || !dall || !crc) { free(dr); free(dall); free(crc); return ORC_OVERFLOW; }
+    int rc = ORC_OK;
+    for (int t = 1; t <= T && rc == ORC_OK; ++t) {
+#pragma omp parallel for num_threads(threads) schedule(static, 1)
+        for (int c = 0; c < threads; ++c) {
+            double *rv = (double *)malloc(sizeof(double) * (size_t)(mx + 1));
+            const int64_t q0 = npairs * c / threads, q1 = npairs * (c + 1) / threads;
+            for (int64_t q = q0; q < q1 && crc[c] == ORC_OK; ++q) {
+                const int len = (int)(pair_off[q + 1] - pair_off[q]);
+                const int32_t *ids = nodes + pair_off[q];
+                for (int i = 0; i < len; ++i) rv[i] = r[ids[i]];
+                crc[c] = orc_pbupdate_cont(len, ids, rv, hcnt[q], k, dall + pair_off[q]);
+            }
+            free(rv);
+        }
+        for (int c = 0; c < threads; ++c) if (crc[c]) rc = crc[c];
+        if (rc) break;
+        memset(dr, 0, sizeof(double) * (size_t)n);
+        for (int64_t q = 0; q < npairs; ++q) {
+            const int len = (int)(pair_off[q + 1] - pair_off[q]);
+            const int32_t *ids = nodes + pair_off[q];
+            const double *dv = dall + pair_off[q];
+            for (int i = 0; i < len; ++i) dr[ids[i]] += dv[i];
+        }
+        for (int64_t v = 0; v < n; ++v) r[v] += dr[v];
+    }
+    free(dr); free(dall); free(crc);
     return rc;
 }
 

@@ -47,7 +47,14 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 class kdss_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("order", C.c_int32), ("flags", C.c_uint32),
                 ("check_every", C.c_int32), ("eps_stop", C.c_double), ("stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("chunk", C.c_int32), ("threads_per_path", C.c_int32)]
+
+
+class kdss_batch_tuning(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("threads_per_path", C.c_int32), ("autotuned", C.c_int32),
+                ("ntried", C.c_int32), ("tried_chunk", C.c_int32 * 8),
+                ("tried_threads_per_path", C.c_int32 * 8), ("tried_ms", C.c_float * 8)]
 
 
 class kdss_graph_desc(C.Structure):
@@ -61,6 +68,16 @@ class kdss_sct_stats(C.Structure):
                 ("degeneracy", C.c_int32), ("max_out_degree", C.c_int32),
                 ("max_pair_len", C.c_int32), ("device_bytes", C.c_int64),
                 ("pairs_per_class", C.c_int64 * 8)]
+
+
+class kdss_sct_count_stats(C.Structure):
+    _fields_ = [("eta_k", C.c_int64), ("L_k", C.c_int64), ("c_k_lo", C.c_uint64),
+                ("c_k_hi", C.c_uint64), ("pairs_per_class", C.c_int64 * 8),
+                ("roots_total", C.c_int64), ("roots_done", C.c_int64), ("roots_cut", C.c_int64),
+                ("cut_pairs", C.c_int64), ("cut_nodes", C.c_int64), ("m", C.c_int64),
+                ("complete", C.c_int32), ("max_pair_len", C.c_int32), ("degeneracy", C.c_int32),
+                ("max_out_degree", C.c_int32), ("count_bits", C.c_int32), ("reserved", C.c_int32),
+                ("seconds", C.c_double)]
 
 
 class kdss_result(C.Structure):
@@ -136,10 +153,15 @@ def load(build_if_missing: bool = False):
         sig = {
             "kdss_build_sct": (i32, [P(kdss_graph_desc), i32, P(kdss_opts), P(vp)]),
             "kdss_sct_from_pairs": (i32, [i64, i32, i64, vp, vp, vp, i32, P(kdss_opts), P(vp)]),
+            "kdss_solve_streamed": (i32, [P(kdss_graph_desc), i32, i32, i32, P(kdss_opts),
+                                          P(kdss_result)]),
+            "kdss_sct_count": (i32, [P(kdss_graph_desc), i32, C.c_double, P(kdss_opts),
+                                     P(kdss_sct_count_stats)]),
             "kdss_sct_info": (i32, [vp, P(kdss_sct_stats)]),
             "kdss_sct_copy_pairs": (i32, [vp, vp, vp, vp]),
             "kdss_sct_copy_graph": (i32, [vp, vp, vp, vp, vp, vp]),
             "kdss_fw_iterate": (i32, [vp, P(vp), i32, P(kdss_opts)]),
+            "kdss_fw_iterate_at": (i32, [vp, i32, P(vp), i32, P(kdss_opts)]),
             "kdss_state_copy_r": (i32, [vp, vp, P(i32)]),
             "kdss_state_timing": (i32, [vp, P(kdss_timing)]),
             "kdss_extract": (i32, [vp, vp, P(kdss_opts), P(kdss_result)]),
@@ -151,6 +173,7 @@ def load(build_if_missing: bool = False):
             "kdss_last_error": (C.c_char_p, []),
             "kdss_version": (C.c_char_p, []),
             "kdss_kernel_launches": (i64, []),
+            "kdss_batch_last_tuning": (i32, [P(kdss_batch_tuning)]),
             "kdss_fw_iterate_noalloc": (i32, [vp, vp, i32, i32, vp]),
             "kdss_fw_cliques": (i32, [vp, P(vp), i32, P(kdss_opts)]),
             "kdss_build_sct_multi": (i32, [P(kdss_graph_desc), i32, P(kdss_opts), P(vp)]),
@@ -212,13 +235,15 @@ _FREE_CB = FREE_FN(_torch_free)
 
 
 def make_opts(precision=KDSS_INT64, order=KDSS_ORDER_PEEL, flags=0, stream=None,
-              allocator="torch", check_every=0, eps_stop=0.0) -> kdss_opts:
+              allocator="torch", check_every=0, eps_stop=0.0, chunk=0,
+              threads_per_path=0) -> kdss_opts:
     """Build a kdss_opts.  stream: a torch.cuda.Stream, a raw cudaStream_t
     (int) or None (torch's current stream when torch is present).
     allocator: 'torch' (caching allocator) or 'library' (cudaMallocAsync)."""
     o = kdss_opts()
     o.precision, o.order, o.flags = precision, order, flags
     o.check_every, o.eps_stop = check_every, eps_stop
+    o.chunk, o.threads_per_path = int(chunk), int(threads_per_path)
     t = _torch()
     if stream is None and t is not None:
         stream = t.cuda.current_stream()
@@ -322,6 +347,21 @@ def kdss_sct_restrict(multi: Sct, k, opts: kdss_opts | None = None) -> Sct:
     return Sct(out.value)
 
 
+def kdss_sct_count(n, src, dst, k, budget_s=0.0, opts: kdss_opts | None = None) -> dict:
+    """Sizes of P_k from the count-only pass (nothing stored); see
+    include/kdss.h for the sampling order when the budget cuts it short."""
+    L = load()
+    g, keep = _graph_desc(n, src, dst)
+    st = kdss_sct_count_stats()
+    _check(L.kdss_sct_count(C.byref(g), int(k), float(budget_s), C.byref(opts or make_opts()),
+                            C.byref(st)))
+    del keep
+    d = {f: getattr(st, f) for f, _ in kdss_sct_count_stats._fields_ if f != "pairs_per_class"}
+    d["pairs_per_class"] = list(st.pairs_per_class)[:6]
+    d["c_k"] = int(st.c_k_lo) | (int(st.c_k_hi) << 64)
+    return d
+
+
 def kdss_sct_from_pairs(n, k, pair_off, nodes, h, opts: kdss_opts | None = None) -> Sct:
     L = load()
     po = np.ascontiguousarray(pair_off, np.int64)
@@ -361,6 +401,18 @@ def kdss_sct_copy_graph(s: Sct) -> dict:
                                       out["core"].ctypes.data, out["round"].ctypes.data,
                                       out["rank"].ctypes.data))
     return out
+
+
+def kdss_fw_iterate_at(s: Sct, k: int, state: State | None, T: int,
+                       opts: kdss_opts | None = None) -> State:
+    """kdss_fw_iterate over P_k of a k-agnostic SCT (pairs outside P_k
+    skipped by the kernels)."""
+    L = load()
+    p = C.c_void_p(state.ptr.value if state is not None else None)
+    _check(L.kdss_fw_iterate_at(s.ptr, int(k), C.byref(p), int(T), C.byref(opts or make_opts())))
+    if state is None:
+        return State(p.value)
+    return state
 
 
 def kdss_fw_iterate(s: Sct, state: State | None, T: int, opts: kdss_opts | None = None) -> State:
@@ -437,6 +489,22 @@ def kdss_extract(s: Sct, st: State, opts: kdss_opts | None = None) -> dict:
         L.kdss_result_free(C.byref(r))
 
 
+def kdss_solve_streamed(n, src, dst, k, T, nchunks, opts: kdss_opts | None = None) -> dict:
+    """kdss_solve with the SCT rebuilt root range by root range inside every
+    iteration (for SCTs that do not fit the device)."""
+    L = load()
+    g, keep = _graph_desc(n, src, dst)
+    r = kdss_result()
+    rc = L.kdss_solve_streamed(C.byref(g), int(k), int(T), int(nchunks),
+                               C.byref(opts or make_opts()), C.byref(r))
+    try:
+        _check(rc)
+        return _result_dict(r)
+    finally:
+        L.kdss_result_free(C.byref(r))
+        del keep
+
+
 def kdss_solve(n, src, dst, k, T, opts: kdss_opts | None = None) -> dict:
     L = load()
     g, keep = _graph_desc(n, src, dst)
@@ -473,6 +541,18 @@ def kdss_solve_batch(queries, opts: kdss_opts | None = None) -> list:
     if rc != KDSS_OK and all(o["status"] != KDSS_OK for o in out):
         _check(rc)
     return out
+
+
+def kdss_batch_last_tuning() -> dict:
+    """The work-queue configuration of this thread's last kdss_solve_batch and
+    the candidates its autotuner timed."""
+    t = kdss_batch_tuning()
+    _check(load().kdss_batch_last_tuning(C.byref(t)))
+    n = t.ntried
+    return {"chunk": t.chunk, "threads_per_path": t.threads_per_path,
+            "autotuned": bool(t.autotuned),
+            "tried": [{"chunk": t.tried_chunk[i], "threads_per_path": t.tried_threads_per_path[i],
+                       "ms": float(t.tried_ms[i])} for i in range(n)]}
 
 
 def kdss_version() -> str:

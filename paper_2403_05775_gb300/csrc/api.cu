@@ -17,6 +17,8 @@ using namespace kdss;
 
 namespace kdss {
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
+void solve_streamed(const Ctx &c, const kdss_graph_desc &g, int k, int T, int nchunks, int precision,
+                    int order, kdss_result *out);
 void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts *opts,
                  std::vector<kdss_status> &status, std::vector<std::string> &msgs);
 void cpsample_run(const Ctx &c, const kdss_graph_desc &g, int k, int64_t t, int T, uint64_t seed,
@@ -60,7 +62,7 @@ void check_graph(const kdss_graph_desc *g) {
 }
 
 void check_k(int32_t k) {
-    if (k < 2 || k > 64) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, 64]");
+    if (k < 2 || k > 255) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, 255]");
 }
 
 int64_t sct_bytes(const kdss_sct *h) {
@@ -68,7 +70,7 @@ int64_t sct_bytes(const kdss_sct *h) {
     const SctDev &s = h->s;
     return (int64_t)(g.off.bytes() + g.adj.bytes() + g.core.bytes() + g.rnd.bytes() +
                      g.rank.bytes() + g.vert.bytes() + g.out_off.bytes() + g.out_adj.bytes() +
-                     s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + s.binom.bytes());
+                     s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + binom_bytes(s));
 }
 
 kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts, kdss_sct **out,
@@ -151,6 +153,68 @@ kdss_status kdss_sct_restrict(const kdss_sct *multi, int32_t k, const kdss_opts 
         throw;
     }
     *out = h;
+    API_END
+}
+
+kdss_status kdss_solve_streamed(const kdss_graph_desc *g, int32_t k, int32_t T, int32_t nchunks,
+                                const kdss_opts *opts, kdss_result *out) {
+    API_BEGIN
+    if (!out) fail(KDSS_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof *out);
+    check_graph(g);
+    check_k(k);
+    if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
+    if (nchunks < 1) fail(KDSS_ERR_INVALID_ARG, "nchunks must be >= 1");
+    const int prec = opts ? opts->precision : KDSS_INT64;
+    if (prec != KDSS_INT64 && prec != KDSS_FP64 && prec != KDSS_FP32K)
+        fail(KDSS_ERR_INVALID_ARG, "unknown precision");
+    if (opts && (opts->flags & KDSS_FLAG_ASYNC))
+        fail(KDSS_ERR_UNSUPPORTED, "the streamed solve runs the synchronous iterations only");
+    const int order = opts ? opts->order : KDSS_ORDER_PEEL;
+    if (order != KDSS_ORDER_PEEL && order != KDSS_ORDER_CORE)
+        fail(KDSS_ERR_INVALID_ARG, "unknown vertex order");
+    Ctx c = make_ctx(opts);
+    solve_streamed(c, *g, k, T, nchunks, prec, order, out);
+    sync(c);
+    API_END
+}
+
+kdss_status kdss_sct_count(const kdss_graph_desc *g, int32_t k, double budget_s,
+                           const kdss_opts *opts, kdss_sct_count_stats *out) {
+    API_BEGIN
+    if (!out) fail(KDSS_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof *out);
+    check_graph(g);
+    check_k(k);
+    if (!(budget_s >= 0)) fail(KDSS_ERR_INVALID_ARG, "budget_s must be >= 0");
+    const int order = opts ? opts->order : KDSS_ORDER_PEEL;
+    if (order != KDSS_ORDER_PEEL && order != KDSS_ORDER_CORE)
+        fail(KDSS_ERR_INVALID_ARG, "unknown vertex order");
+    Ctx c = make_ctx(opts);
+    GraphDev gd;
+    build_graph(c, *g, order, gd);
+    out->m = gd.nadj / 2;
+    out->degeneracy = gd.degeneracy;
+    out->max_out_degree = gd.max_out;
+    gd.off.reset();
+    gd.adj.reset();
+    SctCount sc;
+    count_sct(c, gd, k, budget_s, sc);
+    out->eta_k = sc.eta;
+    out->L_k = sc.L;
+    out->c_k_lo = sc.ck_lo;
+    out->c_k_hi = sc.ck_hi;
+    for (int cl = 0; cl <= NCLASS; ++cl) out->pairs_per_class[cl] = sc.pairs_per_class[cl];
+    out->roots_total = sc.roots_total;
+    out->roots_done = sc.roots_done;
+    out->roots_cut = sc.roots_cut;
+    out->cut_pairs = sc.cut_pairs;
+    out->cut_nodes = sc.cut_nodes;
+    out->complete = sc.complete;
+    out->max_pair_len = sc.max_len;
+    out->count_bits = sc.count_bits;
+    out->seconds = sc.seconds;
+    sync(c);
     API_END
 }
 
@@ -249,11 +313,21 @@ kdss_status kdss_sct_copy_graph(const kdss_sct *s, int64_t *off, int32_t *adj, i
     API_END
 }
 
-kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
+namespace {
+kdss_status fw_iterate_impl(kdss_sct *s, int32_t k, kdss_state **state, int32_t T,
+                            const kdss_opts *opts) {
     API_BEGIN
     if (!s || !state) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
-    if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
+    if (k < 0 && s->kmax_multi)
+        fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: name the k (kdss_fw_iterate_at) or restrict it");
+    if (k >= 0) {
+        const int kmax = s->kmax_multi ? s->kmax_multi : s->s.k;
+        if (k < 2 || k > kmax || (!s->kmax_multi && k != s->s.k))
+            fail(KDSS_ERR_INVALID_ARG, "k outside the P_k the SCT holds");
+    }
     if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
+    if (*state && k >= 0 && (*state)->st.k != k)
+        fail(KDSS_ERR_INVALID_ARG, "the state iterates another k");
     Ctx c = make_ctx(opts);
     bool created = false;
     if (!*state) {
@@ -261,8 +335,12 @@ kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kd
         if (prec != KDSS_INT64 && prec != KDSS_FP64 && prec != KDSS_FP32K)
             fail(KDSS_ERR_INVALID_ARG, "unknown precision");
         kdss_state *st = new kdss_state();
+        if (opts && opts->chunk > 0) {
+            st->st.qchunk = opts->chunk;
+            st->st.qtpp = opts->threads_per_path == 8 ? 8 : 32;
+        }
         try {
-            fw_init(c, s->s, prec, st->st);
+            fw_init(c, s->s, prec, st->st, k);
         } catch (...) {
             delete st;
             throw;
@@ -282,6 +360,16 @@ kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kd
         throw;
     }
     API_END
+}
+}  // namespace
+
+kdss_status kdss_fw_iterate(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
+    return fw_iterate_impl(s, -1, state, T, opts);
+}
+
+kdss_status kdss_fw_iterate_at(kdss_sct *s, int32_t k, kdss_state **state, int32_t T,
+                               const kdss_opts *opts) {
+    return fw_iterate_impl(s, k, state, T, opts);
 }
 
 kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacity,
@@ -372,8 +460,8 @@ kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opt
                          kdss_result *out) {
     API_BEGIN
     if (!s || !st || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
-    if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (st->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
+    if (st->st.k < 2 || st->st.k > s->s.k) fail(KDSS_ERR_INVALID_ARG, "the state's k is not in the SCT");
     Ctx c = make_ctx(opts);
     extract_prefix(c, s->s, st->st, out);
     API_END

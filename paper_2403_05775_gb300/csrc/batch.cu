@@ -29,6 +29,20 @@ namespace kdss {
 
 void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out);
 
+// What the batch autotuner tried (chunk, lanes per long pair, ms of one
+// iteration) and what it chose; kept per host thread for kdss_batch_tuning.
+struct BatchTuning {
+    bool done = false;
+    int chunk = 0, tpp = 0;
+    struct Tried { int chunk, tpp; float ms; };
+    std::vector<Tried> tried;
+};
+namespace {
+thread_local BatchTuning g_last_tuning;
+}
+void set_last_batch_tuning(const BatchTuning &t) { g_last_tuning = t; }
+const BatchTuning &last_batch_tuning() { return g_last_tuning; }
+
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -309,11 +323,11 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
     std::map<std::pair<int, int>, Group> groups;
     for (int i = 0; i < nq; ++i) {
         const kdss_query &x = q[i];
-        if (x.k < 2 || x.k > 64 || x.T < 0 || x.graph.n < 0 || x.graph.n >= (int64_t)INT32_MAX ||
+        if (x.k < 2 || x.k > 255 || x.T < 0 || x.graph.n < 0 || x.graph.n >= (int64_t)INT32_MAX ||
             x.graph.m < 0 || x.graph.m > ((int64_t)1 << 30) ||
             (x.graph.m > 0 && (!x.graph.src || !x.graph.dst))) {
             status[i] = KDSS_ERR_INVALID_ARG;
-            msgs[i] = "bad query: k in [2, 64], T >= 0, n in [0, 2^31 - 1), m in [0, 2^30], edge arrays";
+            msgs[i] = "bad query: k in [2, 255], T >= 0, n in [0, 2^31 - 1), m in [0, 2^30], edge arrays";
             continue;
         }
         Group &g = groups[{x.k, x.T}];
@@ -401,26 +415,110 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
     for (Group *g : gl) Ts.push_back(g->T);
     std::sort(Ts.begin(), Ts.end());
     Ts.erase(std::unique(Ts.begin(), Ts.end()), Ts.end());
+    // The integer rule runs one work-queue pass per iteration over every
+    // active group (k_pb_queue + k_pb_queue_long), the FP32 rule one set of
+    // per-group launches; either way an iteration is one replayed CUDA graph.
+    const bool queue = prec != KDSS_FP32K;
+    int chunk = opts ? opts->chunk : 0, tpp = opts ? opts->threads_per_path : 0;
+    BatchTuning tune;
     int done = 0;
     for (int Tp : Ts) {
         if (Tp <= done) continue;
         std::vector<Group *> act;
         for (Group *g : gl) if (g->T >= Tp) act.push_back(g);
-        cudaGraphExec_t exec = nullptr;
-        const long long nk = fw_capture(c, &exec, [&](const Ctx &cc) {
-            for (Group *g : act) fw_enqueue_group(cc, g->s, st, g->node_off);
+        std::vector<std::pair<const SctDev *, int64_t>> sets;
+        for (Group *g : act) sets.push_back({&g->s, g->node_off});
+        auto steps = [&](const Ctx &cc) {
             for (size_t j = 0; j < act.size(); ++j)
                 fw_enqueue_step_range(cc, st, act[j]->node_off, act[j]->n, j + 1 == act.size());
-        });
-        cudaError_t e = cudaSuccess;
-        for (int it = done; it < Tp && e == cudaSuccess; ++it) {
-            e = cudaGraphLaunch(exec, c.stream);
-            add_launches(nk);
+        };
+        auto run = [&](cudaGraphExec_t exec, long long nk, int iters, float *ms) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ms) {
+                KDSS_CUDA(cudaEventCreate(&e0));
+                KDSS_CUDA(cudaEventCreate(&e1));
+                KDSS_CUDA(cudaEventRecord(e0, c.stream));
+            }
+            cudaError_t e = cudaSuccess;
+            for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+                e = cudaGraphLaunch(exec, c.stream);
+                add_launches(nk);
+            }
+            check_cuda(e, "batch FW graph launch", __FILE__, __LINE__);
+            if (ms) {
+                KDSS_CUDA(cudaEventRecord(e1, c.stream));
+                KDSS_CUDA(cudaEventSynchronize(e1));
+                cudaEventElapsedTime(ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+            }
+        };
+        if (!queue) {
+            cudaGraphExec_t exec = nullptr;
+            const long long nk = fw_capture(c, &exec, [&](const Ctx &cc) {
+                for (Group *g : act) fw_enqueue_group(cc, g->s, st, g->node_off);
+                steps(cc);
+            });
+            run(exec, nk, Tp - done, nullptr);
+            cudaGraphExecDestroy(exec);
+            done = Tp;
+            continue;
         }
-        cudaGraphExecDestroy(exec);
-        check_cuda(e, "batch FW graph launch", __FILE__, __LINE__);
+        auto graph_for = [&](int ch, int tp, QueuePlan &qp, cudaGraphExec_t *exec) {
+            queue_plan(c, sets, ch, tp, qp);
+            return fw_capture(c, exec, [&](const Ctx &cc) {
+                queue_enqueue(cc, qp, st);
+                steps(cc);
+            });
+        };
+        // autotuner: after two warm-up iterations, one iteration per candidate
+        // (each is a real iteration of the run; the integer results do not
+        // depend on the configuration), then the fastest for the rest
+        if ((chunk <= 0 || tpp <= 0) && !tune.done) {
+            std::vector<std::pair<int, int>> cand;
+            bool has_long = false;
+            for (Group *g : act) has_long |= g->s.class_begin[4] > g->s.class_begin[3];
+            for (int ch : {1, 4, 16})
+                for (int tp : {32, 8})
+                    if ((chunk <= 0 || ch == chunk) && (tpp <= 0 || tp == tpp) && (tp == 32 || has_long))
+                        cand.push_back({ch, tp});
+            const int warm = 2;
+            if (Tp - done >= warm + (int)cand.size() + 1 && cand.size() > 1) {
+                QueuePlan qp;
+                cudaGraphExec_t exec = nullptr;
+                long long nk = graph_for(4, 32, qp, &exec);
+                run(exec, nk, warm, nullptr);
+                cudaGraphExecDestroy(exec);
+                done += warm;
+                float best = 1e30f;
+                for (auto &cf : cand) {
+                    QueuePlan qc;
+                    cudaGraphExec_t ex2 = nullptr;
+                    nk = graph_for(cf.first, cf.second, qc, &ex2);
+                    float ms = 0.f;
+                    run(ex2, nk, 1, &ms);
+                    cudaGraphExecDestroy(ex2);
+                    ++done;
+                    tune.tried.push_back({cf.first, cf.second, ms});
+                    if (ms < best) { best = ms; tune.chunk = cf.first; tune.tpp = cf.second; }
+                }
+                tune.done = true;
+            }
+        }
+        const int ch = chunk > 0 ? chunk : (tune.done ? tune.chunk : 4);
+        const int tp = tpp > 0 ? tpp : (tune.done ? tune.tpp : 32);
+        if (done < Tp) {
+            QueuePlan qp;
+            cudaGraphExec_t exec = nullptr;
+            const long long nk = graph_for(ch, tp, qp, &exec);
+            run(exec, nk, Tp - done, nullptr);
+            cudaGraphExecDestroy(exec);
+        }
+        tune.chunk = ch;
+        tune.tpp = tp;
         done = Tp;
     }
+    set_last_batch_tuning(queue ? tune : BatchTuning{});
     int herr = 0;
     to_host(c, &herr, st.err.p, 1);
     if (herr) fail(KDSS_ERR_CUDA, "batch FW: water-filling invariant failed on the device");
@@ -441,3 +539,19 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
 }
 
 }  // namespace kdss
+
+extern "C" kdss_status kdss_batch_last_tuning(kdss_batch_tuning *out) {
+    if (!out) return KDSS_ERR_INVALID_ARG;
+    memset(out, 0, sizeof *out);
+    const kdss::BatchTuning &t = kdss::last_batch_tuning();
+    out->chunk = t.chunk;
+    out->threads_per_path = t.tpp;
+    out->autotuned = t.done ? 1 : 0;
+    out->ntried = (int32_t)std::min<size_t>(t.tried.size(), 8);
+    for (int i = 0; i < out->ntried; ++i) {
+        out->tried_chunk[i] = t.tried[i].chunk;
+        out->tried_threads_per_path[i] = t.tried[i].tpp;
+        out->tried_ms[i] = t.tried[i].ms;
+    }
+    return KDSS_OK;
+}

@@ -83,12 +83,38 @@ __device__ __forceinline__ int gsum_i32(int v) {
 }
 
 // Prefix-count increments of the pairs [b, e): a group of G lanes per pair.
-template <int G, int NPL>
+// 128-bit atomic add: the carry of each low-word add goes to the high word,
+// so concurrent adds sum exactly.
+__device__ __forceinline__ void atomic_add_u128(U128 *a, U128 x) {
+    if (x.lo == 0 && x.hi == 0) return;
+    const unsigned long long old = atomicAdd(&a->lo, x.lo);
+    const unsigned long long carry = (old + x.lo < old) ? 1ull : 0ull;
+    if (x.hi + carry) atomicAdd(&a->hi, x.hi + carry);
+}
+
+// Counts of the narrow form (every count below 2^64: 64-bit table and
+// histograms) or the wide form (128-bit).
+template <bool WIDE>
+struct EventTables {
+    const uint64_t *binom;
+    const U128 *binom128;
+    unsigned long long *hist, *fhist;
+    U128 *hist128, *fhist128;
+    __device__ __forceinline__ void add(bool full, int row, int bcols, int col, int at) const {
+        if constexpr (WIDE) {
+            atomic_add_u128((full ? fhist128 : hist128) + at, binom128[(size_t)row * bcols + col]);
+        } else {
+            const uint64_t v = __ldg(binom + (size_t)row * bcols + col);
+            if (v) atomicAdd((full ? fhist : hist) + at, (unsigned long long)v);
+        }
+    }
+};
+
+template <int G, int NPL, bool WIDE>
 __global__ void __launch_bounds__(256)
 k_prefix_events(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
                 const uint8_t *__restrict__ hcnt, int64_t b, int64_t e,
-                const int32_t *__restrict__ pos, const uint64_t *__restrict__ binom, int bcols,
-                int k, unsigned long long *hist, unsigned long long *fhist) {
+                const int32_t *__restrict__ pos, EventTables<WIDE> tb, int bcols, int k) {
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -107,6 +133,8 @@ k_prefix_events(const int64_t *__restrict__ pair_off, const int32_t *__restrict_
             len = (int)(pair_off[q + 1] - off0);
             h = hcnt[q];
         }
+        // pairs outside P_k (a k-agnostic SCT extracted at k) hold no k-clique
+        const bool inpk = active && h <= k && k <= len;
         const int p = len - h;
         int ps[NPL];
         bool hold[NPL], valid[NPL];
@@ -114,7 +142,7 @@ k_prefix_events(const int64_t *__restrict__ pair_off, const int32_t *__restrict_
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int j = s * G + gl;
-            valid[s] = active && j < len;
+            valid[s] = inpk && j < len;
             const int32_t raw = valid[s] ? __ldg(nodes + off0 + j) : 0;
             hold[s] = raw < 0;
             ps[s] = valid[s] ? __ldg(pos + (raw & 0x7fffffff)) : -1;
@@ -141,22 +169,16 @@ k_prefix_events(const int64_t *__restrict__ pair_off, const int32_t *__restrict_
                     if (pv >= 0 && pv < ps[s]) ++rk[s];
             }
         }
-        if (active) {
+        if (inpk) {
             const int kh = k - h;
             if (gl == 0) {
-                const uint64_t first = __ldg(binom + (size_t)c0 * bcols + kh);
-                if (first) atomicAdd(hist + (mh + 1), (unsigned long long)first);
-                const uint64_t nC = __ldg(binom + (size_t)p * bcols + kh);
-                atomicAdd(fhist + (mall + 1), (unsigned long long)nC);
+                tb.add(false, c0, bcols, kh, mh + 1);     // C(c0, k - h) once V_h is inside
+                tb.add(true, p, bcols, kh, mall + 1);     // n_C once the whole pair is inside
             }
             if (kh >= 1) {
 #pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    if (valid[s] && !hold[s] && ps[s] > mh) {
-                        const uint64_t inc = __ldg(binom + (size_t)rk[s] * bcols + (kh - 1));
-                        if (inc) atomicAdd(hist + (ps[s] + 1), (unsigned long long)inc);
-                    }
-                }
+                for (int s = 0; s < NPL; ++s)
+                    if (valid[s] && !hold[s] && ps[s] > mh) tb.add(false, rk[s], bcols, kh - 1, ps[s] + 1);
             }
         }
     }
@@ -171,102 +193,122 @@ __device__ __forceinline__ int frac_cmp(unsigned long long a, unsigned long long
     if (alo != blo) return alo > blo ? 1 : -1;
     return 0;
 }
+// the same for 128-bit counts (i, j < 2^63): 192-bit cross products
+__device__ __forceinline__ void mul_u128_u64(U128 a, unsigned long long j, unsigned long long &w2,
+                                             unsigned long long &w1, unsigned long long &w0) {
+    w0 = a.lo * j;
+    const unsigned long long c0 = __umul64hi(a.lo, j);
+    const unsigned long long t = a.hi * j;
+    w1 = t + c0;
+    w2 = __umul64hi(a.hi, j) + (w1 < t ? 1ull : 0ull);
+}
+__device__ __forceinline__ int frac_cmp(U128 a, unsigned long long i, U128 b, unsigned long long j) {
+    unsigned long long a2, a1, a0, b2, b1, b0;
+    mul_u128_u64(a, j, a2, a1, a0);
+    mul_u128_u64(b, i, b2, b1, b0);
+    if (a2 != b2) return a2 > b2 ? 1 : -1;
+    if (a1 != b1) return a1 > b1 ? 1 : -1;
+    if (a0 != b0) return a0 > b0 ? 1 : -1;
+    return 0;
+}
+__device__ __forceinline__ unsigned long long shfl_xor_ct(unsigned long long v, int o) {
+    return __shfl_xor_sync(FULL, v, o);
+}
+__device__ __forceinline__ U128 shfl_xor_ct(U128 v, int o) {
+    return U128(__shfl_xor_sync(FULL, v.lo, o), __shfl_xor_sync(FULL, v.hi, o));
+}
 
 // Best prefix of a scanned count array: largest ratio, ties to the larger i.
-__device__ __forceinline__ void better(unsigned long long &a, long long &i,
-                                       unsigned long long b, long long j) {
+template <class CT>
+__device__ __forceinline__ void better(CT &a, long long &i, CT b, long long j) {
     if (j <= 0) return;
     if (i <= 0) { a = b; i = j; return; }
     int c = frac_cmp(b, (unsigned long long)j, a, (unsigned long long)i);
     if (c > 0 || (c == 0 && j > i)) { a = b; i = j; }
 }
 
-__global__ void k_argmax_partial(int64_t n, const unsigned long long *cnt,
-                                 unsigned long long *pa, long long *pi) {
-    unsigned long long a = 0;
+template <class CT>
+__device__ __forceinline__ void block_best(CT &a, long long &i, CT *sa, long long *si) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        CT b = shfl_xor_ct(a, o);
+        long long j = __shfl_xor_sync(FULL, i, o);
+        better(a, i, b, j);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sa[w] = a; si[w] = i; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : CT(0);
+        i = lane < nw ? si[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            CT b = shfl_xor_ct(a, o);
+            long long j = __shfl_xor_sync(FULL, i, o);
+            better(a, i, b, j);
+        }
+    }
+}
+
+template <class CT>
+__global__ void k_argmax_partial(int64_t n, const CT *cnt, CT *pa, long long *pi) {
+    CT a = CT(0);
     long long i = 0;
     for (int64_t x = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x <= n;
          x += (int64_t)gridDim.x * blockDim.x)
         better(a, i, cnt[x], x);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long b = __shfl_xor_sync(FULL, a, o);
-        long long j = __shfl_xor_sync(FULL, i, o);
-        better(a, i, b, j);
-    }
-    __shared__ unsigned long long sa[32];
+    __shared__ CT sa[32];
     __shared__ long long si[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { sa[w] = a; si[w] = i; }
-    __syncthreads();
-    if (w == 0) {
-        const int nw = blockDim.x >> 5;
-        a = lane < nw ? sa[lane] : 0ull;
-        i = lane < nw ? si[lane] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long b = __shfl_xor_sync(FULL, a, o);
-            long long j = __shfl_xor_sync(FULL, i, o);
-            better(a, i, b, j);
-        }
-        if (lane == 0) { pa[blockIdx.x] = a; pi[blockIdx.x] = i; }
-    }
+    block_best(a, i, sa, si);
+    if (threadIdx.x == 0) { pa[blockIdx.x] = a; pi[blockIdx.x] = i; }
 }
 
-__global__ void k_argmax_final(int nb, const unsigned long long *pa, const long long *pi,
-                               unsigned long long *oa, long long *oi) {
-    unsigned long long a = 0;
+template <class CT>
+__global__ void k_argmax_final(int nb, const CT *pa, const long long *pi, CT *oa, long long *oi) {
+    CT a = CT(0);
     long long i = 0;
     for (int x = threadIdx.x; x < nb; x += blockDim.x) better(a, i, pa[x], pi[x]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long b = __shfl_xor_sync(FULL, a, o);
-        long long j = __shfl_xor_sync(FULL, i, o);
-        better(a, i, b, j);
-    }
-    __shared__ unsigned long long sa[32];
+    __shared__ CT sa[32];
     __shared__ long long si[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { sa[w] = a; si[w] = i; }
-    __syncthreads();
-    if (w == 0) {
-        const int nw = blockDim.x >> 5;
-        a = lane < nw ? sa[lane] : 0ull;
-        i = lane < nw ? si[lane] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long b = __shfl_xor_sync(FULL, a, o);
-            long long j = __shfl_xor_sync(FULL, i, o);
-            better(a, i, b, j);
-        }
-        if (lane == 0) { *oa = a; *oi = i; }
-    }
+    block_best(a, i, sa, si);
+    if (threadIdx.x == 0) { *oa = a; *oi = i; }
 }
 
-void best_prefix(const Ctx &c, int64_t n, const unsigned long long *cnt, unsigned long long *a,
-                 long long *i) {
+template <class CT>
+void best_prefix(const Ctx &c, int64_t n, const CT *cnt, CT *a, long long *i) {
     const int B = 256;
     const int nb = std::min(grid_for(c, n, B, 4), 1024);
-    DBuf<unsigned long long> pa(c, (size_t)nb), oa(c, 1);
+    DBuf<CT> pa(c, (size_t)nb), oa(c, 1);
     DBuf<long long> pi(c, (size_t)nb), oi(c, 1);
-    k_argmax_partial<<<nb, B, 0, c.stream>>>(n, cnt, pa.p, pi.p);
+    k_argmax_partial<CT><<<nb, B, 0, c.stream>>>(n, cnt, pa.p, pi.p);
     KDSS_LAUNCH_CHECK();
-    k_argmax_final<<<1, 1024, 0, c.stream>>>(nb, pa.p, pi.p, oa.p, oi.p);
+    k_argmax_final<CT><<<1, 1024, 0, c.stream>>>(nb, pa.p, pi.p, oa.p, oi.p);
     KDSS_LAUNCH_CHECK();
     to_host(c, a, oa.p, 1);
     to_host(c, i, oi.p, 1);
 }
 
-template <int G, int NPL>
-void launch_events(const Ctx &c, const SctDev &s, int cls, const int32_t *pos,
-                   unsigned long long *hist, unsigned long long *fhist) {
+template <int G, int NPL, bool WIDE>
+void launch_events(const Ctx &c, const SctDev &s, int k, int cls, const int32_t *pos,
+                   const EventTables<WIDE> &tb) {
     const int64_t b = s.class_begin[cls], e = s.class_begin[cls + 1];
     if (e <= b) return;
     const int64_t gpb = 8 * (32 / G);
     int grid = (int)std::min<int64_t>(ceil_div(e - b, gpb), (int64_t)c.num_sms * 16);
-    k_prefix_events<G, NPL><<<grid, 256, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, pos,
-                                                        s.binom.p, s.k + 1, s.k, hist, fhist);
+    k_prefix_events<G, NPL, WIDE><<<grid, 256, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
+                                                              pos, tb, s.bcols(), k);
     KDSS_LAUNCH_CHECK();
+}
+
+template <bool WIDE>
+void launch_events_all(const Ctx &c, const SctDev &s, int k, const int32_t *pos,
+                       const EventTables<WIDE> &tb) {
+    launch_events<8, 1, WIDE>(c, s, k, 0, pos, tb);
+    launch_events<8, 2, WIDE>(c, s, k, 1, pos, tb);
+    launch_events<8, 4, WIDE>(c, s, k, 2, pos, tb);
+    launch_events<32, 8, WIDE>(c, s, k, 3, pos, tb);
+    launch_events<32, 32, WIDE>(c, s, k, 4, pos, tb);
 }
 
 }  // namespace
@@ -275,11 +317,8 @@ void launch_events(const Ctx &c, const SctDev &s, int cls, const int32_t *pos,
 // segmented extraction of batches, whose positions index query segments).
 void launch_prefix_events_all(const Ctx &c, const SctDev &s, const int32_t *pos,
                               unsigned long long *hist, unsigned long long *fhist) {
-    launch_events<8, 1>(c, s, 0, pos, hist, fhist);
-    launch_events<8, 2>(c, s, 1, pos, hist, fhist);
-    launch_events<8, 4>(c, s, 2, pos, hist, fhist);
-    launch_events<32, 8>(c, s, 3, pos, hist, fhist);
-    launch_events<32, 32>(c, s, 4, pos, hist, fhist);
+    EventTables<false> tb{s.binom.p, nullptr, hist, fhist, nullptr, nullptr};
+    launch_events_all<false>(c, s, s.k, pos, tb);
 }
 
 namespace {
@@ -340,17 +379,17 @@ void extract_from_cliques(const Ctx &c, const StateDev &st, const int32_t *cl, i
     }
 }
 
-void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out) {
-    const int64_t n = s.n;
-    memset(out, 0, sizeof *out);
-    out->t_used = st.t;
-    if (n == 0) return;
-    if (s.ck_hi) fail(KDSS_ERR_OVERFLOW, "prefix clique counts above 2^64 are not supported");
+// Extraction in three phases, so that the pairs can come in pieces (the
+// streamed solve rebuilds the SCT root range by root range): the order and
+// positions from r, the prefix-count increments of each piece of pairs, and
+// the scans and the best prefix.
+void prefix_begin(const Ctx &c, int64_t n, const StateDev &st, bool wide, PrefixAcc &a) {
+    a.n = n;
+    a.wide = wide;
     const int B = 256;
     DBuf<uint64_t> keys(c, (size_t)n);
-    DBuf<int32_t> order(c, (size_t)n);
+    a.order = DBuf<int32_t>(c, (size_t)n);
     int bits;
-    double rmax_val;
     if (st.precision == KDSS_FP32K) {
         DBuf<unsigned long long> mx(c, 1);
         zero(c, mx.p, 8);
@@ -361,8 +400,8 @@ void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_resu
         uint32_t m32 = (uint32_t)mb;
         float mf;
         memcpy(&mf, &m32, 4);
-        rmax_val = (double)mf;
-        k_keys_f32<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r32.p, m32, keys.p, order.p);
+        a.rmax = (double)mf;
+        k_keys_f32<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r32.p, m32, keys.p, a.order.p);
         bits = bit_length(m32);
     } else {
         unsigned long long mb = 0;
@@ -370,43 +409,85 @@ void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_resu
         if (st.precision == KDSS_FP64) {
             double md;
             memcpy(&md, &mb, 8);
-            rmax_val = st.t > 0 ? md / st.t : 0.0;
+            a.rmax = st.t > 0 ? md / st.t : 0.0;
         } else {
-            rmax_val = st.t > 0 ? (double)mb / st.t : 0.0;
+            a.rmax = st.t > 0 ? (double)mb / st.t : 0.0;
         }
-        k_keys_u64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mb, keys.p, order.p);
+        k_keys_u64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mb, keys.p, a.order.p);
         bits = bit_length(mb);
     }
     KDSS_LAUNCH_CHECK();
-    radix_sort_u64(c, keys.p, order.p, n, {{0, bits}});
+    radix_sort_u64(c, keys.p, a.order.p, n, {{0, bits}});
     keys.reset();
-    DBuf<int32_t> pos(c, (size_t)n);
-    k_positions<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, order.p, pos.p);
+    a.pos = DBuf<int32_t>(c, (size_t)n);
+    k_positions<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, a.order.p, a.pos.p);
     KDSS_LAUNCH_CHECK();
-    DBuf<unsigned long long> hist(c, (size_t)n + 2), fhist(c, (size_t)n + 2);
-    zero(c, hist.p, (n + 2) * 8);
-    zero(c, fhist.p, (n + 2) * 8);
-    launch_prefix_events_all(c, s, pos.p, hist.p, fhist.p);
-    inclusive_scan_u64_async(c, (const uint64_t *)hist.p, (uint64_t *)hist.p, n + 1);
-    inclusive_scan_u64_async(c, (const uint64_t *)fhist.p, (uint64_t *)fhist.p, n + 1);
-    unsigned long long best = 0, fbest = 0;
+    if (!wide) {
+        a.hist = DBuf<unsigned long long>(c, (size_t)n + 2);
+        a.fhist = DBuf<unsigned long long>(c, (size_t)n + 2);
+        zero(c, a.hist.p, (n + 2) * 8);
+        zero(c, a.fhist.p, (n + 2) * 8);
+    } else {
+        a.hist128 = DBuf<U128>(c, (size_t)n + 2);
+        a.fhist128 = DBuf<U128>(c, (size_t)n + 2);
+        zero(c, a.hist128.p, (n + 2) * 16);
+        zero(c, a.fhist128.p, (n + 2) * 16);
+    }
+}
+
+void prefix_add(const Ctx &c, const SctDev &s, int k, PrefixAcc &a) {
+    if (!a.wide) {
+        EventTables<false> tb{s.binom.p, nullptr, a.hist.p, a.fhist.p, nullptr, nullptr};
+        launch_events_all<false>(c, s, k, a.pos.p, tb);
+    } else {
+        EventTables<true> tb{nullptr, s.binom128.p, nullptr, nullptr, a.hist128.p, a.fhist128.p};
+        launch_events_all<true>(c, s, k, a.pos.p, tb);
+    }
+}
+
+void prefix_end(const Ctx &c, PrefixAcc &a, const StateDev &st, kdss_result *out) {
+    const int64_t n = a.n;
     long long istar = 0, fi = 0;
-    best_prefix(c, n, hist.p, &best, &istar);
-    best_prefix(c, n, fhist.p, &fbest, &fi);
+    U128 best(0), fbest(0);
+    if (!a.wide) {
+        inclusive_scan_u64_async(c, (const uint64_t *)a.hist.p, (uint64_t *)a.hist.p, n + 1);
+        inclusive_scan_u64_async(c, (const uint64_t *)a.fhist.p, (uint64_t *)a.fhist.p, n + 1);
+        unsigned long long b64 = 0, f64 = 0;
+        best_prefix(c, n, a.hist.p, &b64, &istar);
+        best_prefix(c, n, a.fhist.p, &f64, &fi);
+        best = U128(b64, 0ull);
+        fbest = U128(f64, 0ull);
+    } else {
+        inclusive_scan_u128_async(c, a.hist128.p, a.hist128.p, n + 1);
+        inclusive_scan_u128_async(c, a.fhist128.p, a.fhist128.p, n + 1);
+        best_prefix(c, n, a.hist128.p, &best, &istar);
+        best_prefix(c, n, a.fhist128.p, &fbest, &fi);
+    }
     out->istar = istar;
-    out->count_lo = best;
-    out->count_hi = 0;
-    out->density = istar > 0 ? (double)best / (double)istar : 0.0;
-    out->upper_bound = rmax_val;
-    out->rho_prime = fi > 0 ? (double)fbest / (double)fi : 0.0;
-    out->gap = rmax_val > 0 ? 1.0 - out->rho_prime / rmax_val : 0.0;
+    out->count_lo = best.lo;
+    out->count_hi = best.hi;
+    out->density = istar > 0 ? u128_to_double(best) / (double)istar : 0.0;
+    out->upper_bound = a.rmax;
+    out->rho_prime = fi > 0 ? u128_to_double(fbest) / (double)fi : 0.0;
+    out->gap = a.rmax > 0 ? 1.0 - out->rho_prime / a.rmax : 0.0;
     out->T = st.t;
+    out->t_used = st.t;
     if (istar > 0) {
         out->ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)istar);
         if (!out->ids) fail(KDSS_ERR_OOM, "host allocation of the result ids");
-        to_host(c, out->ids, order.p, (size_t)istar);
+        to_host(c, out->ids, a.order.p, (size_t)istar);
         std::sort(out->ids, out->ids + istar);
     }
+}
+
+void extract_prefix(const Ctx &c, const SctDev &s, const StateDev &st, kdss_result *out) {
+    memset(out, 0, sizeof *out);
+    out->t_used = st.t;
+    if (s.n == 0) return;
+    PrefixAcc a;
+    prefix_begin(c, s.n, st, st.ck_hi != 0, a);
+    prefix_add(c, s, st.k, a);
+    prefix_end(c, a, st, out);
 }
 
 }  // namespace kdss

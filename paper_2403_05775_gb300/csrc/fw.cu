@@ -30,6 +30,7 @@
 // error-free (TwoSum) compensated atomics and folded into r/t by a Kahan
 // update in the step kernel.
 #include <algorithm>
+#include <cstdlib>
 #include <functional>
 
 #include "fw.cuh"
@@ -222,6 +223,120 @@ template <class RT> struct AccV;
 template <> struct AccV<uint64_t> { using T = unsigned long long; };
 template <> struct AccV<double> { using T = double; };
 
+// Rule I PBUpdate of one pair by a group of G lanes (lane gl holds slots
+// gl, gl + G, ...): the walk of Alg. 3 with group reductions.  Every lane of
+// the warp calls it; `active` is false for lanes whose group has no pair.
+// scatter(id, amount) receives each node's allocation.
+template <int G, int NPL, class RT, class Scatter>
+__device__ __forceinline__ void group_pair_walk(bool active, int64_t q,
+                                                const int64_t *__restrict__ pair_off,
+                                                const int32_t *__restrict__ nodes,
+                                                const uint8_t *__restrict__ hcnt,
+                                                const RT *__restrict__ r,
+                                                const uint64_t *__restrict__ binom, int bcols,
+                                                int k, int *err, Scatter scatter) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gbase = lane & ~(G - 1);
+    const unsigned lowmask = (G == 32) ? FULL : ((1u << G) - 1u);
+    int64_t off0 = 0;
+    int len = 0, h = 0;
+    if (active) {
+        off0 = pair_off[q];
+        len = (int)(pair_off[q + 1] - off0);
+        h = hcnt[q];
+    }
+    // pairs outside P_k (a k-agnostic SCT iterated at k) take no part
+    const bool inpk = active && h <= k && k <= len;
+    const int p = len - h;
+    uint64_t nC = 0, cap_h = 0, cap_p = 0;
+    if (inpk) {
+        nC = __ldg(binom + (size_t)p * bcols + (k - h));
+        cap_h = nC;
+        cap_p = (p >= 1 && k - h - 1 >= 0) ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+    }
+    uint64_t r0[NPL], cur[NPL], up[NPL];
+    int32_t id[NPL];
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const int j = s * G + gl;
+        const bool valid = inpk && j < len;
+        const int32_t raw = valid ? __ldg(nodes + off0 + j) : 0;
+        id[s] = raw & 0x7fffffff;
+        r0[s] = valid ? load_r<RT>(r, id[s]) : ~0ull;
+        up[s] = valid ? (raw < 0 ? cap_h : cap_p) : 0ull;
+        cur[s] = r0[s];
+    }
+    uint64_t rem = inpk ? nC : 0ull;
+    uint64_t lev;
+    {
+        uint64_t m = ~0ull;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s)
+            if (up[s] > 0 && cur[s] < m) m = cur[s];
+        lev = gmin_u64<G>(m);
+    }
+    int guard = 0;
+    const int guard_max = 4 * G * NPL + 8;
+    while (__any_sync(FULL, rem > 0)) {
+        uint64_t nx = ~0ull, mu = ~0ull;
+        int na = 0;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            if (up[s] > 0) {
+                if (cur[s] == lev) { ++na; mu = up[s] < mu ? up[s] : mu; }
+                else if (cur[s] > lev && cur[s] < nx) nx = cur[s];
+            }
+        }
+        na = gsum_i32<G>(na);
+        mu = gmin_u64<G>(mu);
+        nx = gmin_u64<G>(nx);
+        bool do_rem = false;
+        if (rem > 0) {
+            if (na == 0) {
+                if (nx == ~0ull) { atomicOr(err, DERR_LOGIC); rem = 0; }
+                else lev = nx;
+            } else {
+                const uint64_t gap = nx == ~0ull ? ~0ull : nx - lev;
+                uint64_t w = mu < gap ? mu : gap;
+                const uint64_t share = rem / (uint64_t)na;
+                w = share < w ? share : w;
+                if (w > 0) {
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s)
+                        if (up[s] > 0 && cur[s] == lev) { cur[s] += w; up[s] -= w; }
+                    rem -= w * (uint64_t)na;
+                    lev += w;
+                } else {
+                    do_rem = true;
+                }
+            }
+        }
+        if (__any_sync(FULL, do_rem)) {
+            int before = 0;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const bool inA = do_rem && up[s] > 0 && cur[s] == lev;
+                const unsigned gb = (__ballot_sync(FULL, inA) >> gbase) & lowmask;
+                const int rk = before + __popc(gb & ((1u << gl) - 1u));
+                if (inA && (uint64_t)rk < rem) { cur[s] += 1; up[s] -= 1; }
+                before += __popc(gb);
+            }
+            if (do_rem) rem = 0;
+        }
+        if (++guard > guard_max) {
+            if (rem > 0) atomicOr(err, DERR_LOGIC);
+            break;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const int j = s * G + gl;
+        if (inpk && j < len && cur[s] > r0[s])
+            scatter(id[s], cur[s] - r0[s]);
+    }
+}
+
 // Rule I (integer) PBUpdate over the pairs [p_begin, p_end).
 template <int G, int NPL, class RT>
 __global__ void __launch_bounds__(FW_THREADS)
@@ -231,9 +346,6 @@ k_pbupdate_int(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
                int k, const int32_t *list, const int *list_count, int *err) {
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
-    const int gbase = lane & ~(G - 1);
-    const unsigned lowmask = (G == 32) ? FULL : ((1u << G) - 1u);
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // pairs [p_begin, p_end), or p_begin + list[i] for i < *list_count; each
@@ -254,100 +366,8 @@ k_pbupdate_int(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
         const int64_t qi = wb + lane / G;
         const bool active = qi < ce;
         const int64_t q = p_begin + (list ? (active ? (int64_t)list[qi] : 0) : qi);
-        int64_t off0 = 0;
-        int len = 0, h = 0;
-        if (active) {
-            off0 = pair_off[q];
-            len = (int)(pair_off[q + 1] - off0);
-            h = hcnt[q];
-        }
-        const int p = len - h;
-        uint64_t nC = 0, cap_h = 0, cap_p = 0;
-        if (active) {
-            nC = __ldg(binom + (size_t)p * bcols + (k - h));
-            cap_h = nC;
-            cap_p = (p >= 1 && k - h - 1 >= 0) ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
-        }
-        uint64_t r0[NPL], cur[NPL], up[NPL];
-        int32_t id[NPL];
-#pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int j = s * G + gl;
-            const bool valid = active && j < len;
-            const int32_t raw = valid ? __ldg(nodes + off0 + j) : 0;
-            id[s] = raw & 0x7fffffff;
-            r0[s] = valid ? load_r<RT>(r, id[s]) : ~0ull;
-            up[s] = valid ? (raw < 0 ? cap_h : cap_p) : 0ull;
-            cur[s] = r0[s];
-        }
-        uint64_t rem = active ? nC : 0ull;
-        uint64_t lev;
-        {
-            uint64_t m = ~0ull;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s)
-                if (up[s] > 0 && cur[s] < m) m = cur[s];
-            lev = gmin_u64<G>(m);
-        }
-        int guard = 0;
-        const int guard_max = 4 * G * NPL + 8;
-        while (__any_sync(FULL, rem > 0)) {
-            uint64_t nx = ~0ull, mu = ~0ull;
-            int na = 0;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                if (up[s] > 0) {
-                    if (cur[s] == lev) { ++na; mu = up[s] < mu ? up[s] : mu; }
-                    else if (cur[s] > lev && cur[s] < nx) nx = cur[s];
-                }
-            }
-            na = gsum_i32<G>(na);
-            mu = gmin_u64<G>(mu);
-            nx = gmin_u64<G>(nx);
-            bool do_rem = false;
-            if (rem > 0) {
-                if (na == 0) {
-                    if (nx == ~0ull) { atomicOr(err, DERR_LOGIC); rem = 0; }
-                    else lev = nx;
-                } else {
-                    const uint64_t gap = nx == ~0ull ? ~0ull : nx - lev;
-                    uint64_t w = mu < gap ? mu : gap;
-                    const uint64_t share = rem / (uint64_t)na;
-                    w = share < w ? share : w;
-                    if (w > 0) {
-#pragma unroll
-                        for (int s = 0; s < NPL; ++s)
-                            if (up[s] > 0 && cur[s] == lev) { cur[s] += w; up[s] -= w; }
-                        rem -= w * (uint64_t)na;
-                        lev += w;
-                    } else {
-                        do_rem = true;
-                    }
-                }
-            }
-            if (__any_sync(FULL, do_rem)) {
-                int before = 0;
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    const bool inA = do_rem && up[s] > 0 && cur[s] == lev;
-                    const unsigned gb = (__ballot_sync(FULL, inA) >> gbase) & lowmask;
-                    const int rk = before + __popc(gb & ((1u << gl) - 1u));
-                    if (inA && (uint64_t)rk < rem) { cur[s] += 1; up[s] -= 1; }
-                    before += __popc(gb);
-                }
-                if (do_rem) rem = 0;
-            }
-            if (++guard > guard_max) {
-                if (rem > 0) atomicOr(err, DERR_LOGIC);
-                break;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int j = s * G + gl;
-            if (active && j < len && cur[s] > r0[s])
-                agg_add(tbl, id[s], (AV)(cur[s] - r0[s]), (AV *)acc);
-        }
+        group_pair_walk<G, NPL, RT>(active, q, pair_off, nodes, hcnt, r, binom, bcols, k, err,
+                                    [&](int32_t id, uint64_t x) { agg_add(tbl, id, (AV)x, (AV *)acc); });
     }
     agg_flush(tbl, (AV *)acc);
 }
@@ -374,6 +394,26 @@ __device__ __forceinline__ void warp_seg_add(int32_t id, V x, V *gacc) {
     if (tail && id >= 0 && x != V(0)) atomicAdd(gacc + id, x);
 }
 
+// The list of pairs the first-step kernels leave to the slow kernels.  The
+// unsettled pairs of a tile take their slots with one atomic on the list's
+// counter (lane ranks from a ballot), not one atomic each.
+// Every lane of the warp calls this; lanes with `want` append `value`.
+__device__ __forceinline__ void slow_append(bool want, int32_t value, int32_t *slow, int *slow_count,
+                                            int64_t cap, int *err) {
+    const unsigned FULL_ = 0xffffffffu;
+    const unsigned m = __ballot_sync(FULL_, want);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if ((threadIdx.x & 31) == leader) base = atomicAdd(slow_count, __popc(m));
+    base = __shfl_sync(FULL_, base, leader);
+    if (want) {
+        const int64_t slot = (int64_t)base + __popc(m & lanemask_lt());
+        if (slot < cap) slow[slot] = value;
+        else atomicOr(err, DERR_CAPACITY);
+    }
+}
+
 // First step of Alg. 3 for pairs of at most 32 nodes.  A warp takes 32
 // consecutive pairs: their node ids are copied to shared memory (coalesced)
 // and then the r words they address (gathers), both as asynchronous copies so
@@ -396,7 +436,7 @@ __global__ void __launch_bounds__(FA_WARPS * 32)
 k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
           const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
           const RT *__restrict__ r, RT *acc, const uint64_t *__restrict__ binom, int bcols,
-          int k, int32_t *slow, int *slow_count, int *err) {
+          int k, int32_t *slow, int *slow_count, int64_t slow_cap, int *err) {
     __shared__ int32_t sidv[FA_WARPS][FA_CAP];
     __shared__ uint64_t sval[FA_WARPS][FA_CAP];
     using AV = typename AccV<RT>::T;
@@ -428,12 +468,15 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
         cp_async_wait_all();
         __syncwarp();
         uint32_t rmask = 0;     // receivers (slot bits)
+        bool want_slow = false;
         uint64_t w = 0, R = 0;
         int o = 0;
-        if (valid) {
+        // pairs outside P_k (a k-agnostic SCT iterated at k) take no part
+        const int hq = valid ? (int)hcnt[q] : 0;
+        if (valid && hq <= k && k <= (int)(mye - myb)) {
             o = (int)(myb - B);
             const int len = (int)(mye - myb);
-            const int h = hcnt[q];
+            const int h = hq;
             const int p = len - h;
             const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
             const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
@@ -467,14 +510,11 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
                 w = nC / na;
                 R = nC - w * na;
                 const uint64_t lim = mu < gap ? mu : gap;
-                if (!(R == 0 ? w > lim : w >= lim)) {
-                    rmask = mask1;  // settled by the first step
-                } else {
-                    const int slot = atomicAdd(slow_count, 1);
-                    if (slot < np) slow[slot] = (int32_t)qi;
-                }
+                if (!(R == 0 ? w > lim : w >= lim)) rmask = mask1;  // settled by the first step
+                else want_slow = true;
             }
         }
+        slow_append(want_slow, (int32_t)qi, slow, slow_count, slow_cap, err);
         // scatter the allocation, one receiver per lane per round
         uint64_t rank = 0;
         while (__any_sync(0xffffffffu, rmask != 0)) {
@@ -510,6 +550,193 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
 constexpr int SB_WARPS = 8;
 constexpr int SB_ROUNDS = 24;
 
+// The water level of one pair of at most 32 nodes by one warp (the closed
+// form of Alg. 3's walk): lane j holds node j (raw id with the V_h mark in
+// rawc, its integer level rjc); lanes >= len hold nothing.  Used by the slow
+// kernel and by the work-queue kernel for the pairs the first step leaves.
+// sr_w, sc_w: 32 words of this warp's shared memory each.
+template <class AV>
+__device__ __forceinline__ void slow_pair_walk(int len, int h, int32_t rawc, uint64_t rjc, int k,
+                                               const uint64_t *__restrict__ binom, int bcols,
+                                               void *acc, uint64_t *sr_w, uint64_t *sc_w,
+                                               int *err) {
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int p = len - h;
+    const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
+    const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                               ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+    int32_t id = -1;
+    uint64_t rj = 0, cj = 0;
+    if (lane < len) {
+        id = rawc & 0x7fffffff;
+        rj = rjc;
+        cj = rawc < 0 ? nC : cap_p;
+    }
+    // levels relative to the lowest node that can receive: 32-bit when
+    // the spread and n_C fit in 31 bits (the usual case).  64-bit min and
+    // max as two 32-bit warp reductions (high word, then low word).
+    const uint64_t vb = cj > 0 ? rj : ~0ull;
+    const uint32_t bh = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32));
+    const uint32_t bl = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32) == bh ? (uint32_t)vb : 0xffffffffu);
+    const uint64_t base = ((uint64_t)bh << 32) | bl;
+    if (__all_sync(FULL_, cj == 0 || rj - base < (1ull << 31)) && nC < (1ull << 31)) {
+        const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
+        // The walk of Alg. 3 with warp-uniform state: at water level L the
+        // receiving nodes are those with rl <= L < rl + cl; the level rises
+        // to the next event (a node's level, or a receiving node's level
+        // plus cap) while the units last, and stops at
+        // L* = L + floor(rem / na) with R = rem mod na units left for the
+        // lowest ids receiving at L*.  A level where every node is capped
+        // jumps to the next node.  Pairs that cross more than SB_ROUNDS
+        // events take the closed form below.
+        {
+            const uint32_t nC32 = (uint32_t)nC, INF32 = 0xffffffffu;
+            uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
+            bool done = false;
+            for (int round = 0; round < SB_ROUNDS; ++round) {
+                const bool act = cl > 0 && rl <= L && L - rl < cl;
+                const uint32_t na = (uint32_t)__popc(__ballot_sync(FULL_, act));
+                const uint32_t e1 = (cl > 0 && rl > L) ? rl : INF32;
+                const uint32_t e2 = act ? rl + cl : INF32;
+                const uint32_t ev = __reduce_min_sync(FULL_, e1 < e2 ? e1 : e2);
+                if (na == 0) {
+                    if (ev == INF32) break;
+                    L = ev;
+                    continue;
+                }
+                // the units end before the next event, or exactly at it
+                // (then nothing is left over and L* = ev allocates the
+                // same): floor(rem / na) < ev - L, or rem = (ev - L) na,
+                // which is rem <= (ev - L) na; one division at the end
+                const uint64_t span = (uint64_t)(ev - L) * na;
+                if (ev == INF32 || rem <= span) {
+                    const uint32_t qd = rem / na;
+                    Ls = L + qd;
+                    R = rem - qd * na;
+                    done = true;
+                    break;
+                }
+                rem -= (uint32_t)span;
+                L = ev;
+            }
+            if (done) {
+                uint32_t dj = 0;
+                bool elig = false;
+                if (cl > 0) {
+                    if (Ls > rl) dj = min(Ls - rl, cl);
+                    elig = rl <= Ls && Ls - rl < cl;
+                }
+                const unsigned eb = __ballot_sync(FULL_, elig);
+                if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+                if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+                __syncwarp();
+                return;
+            }
+        }
+        // (level, cap) of every node as one 64-bit word; a zero cap adds
+        // nothing below (min(d, 0) = 0), so no special case
+        uint2 *sp = (uint2 *)sr_w;
+        sp[lane] = make_uint2(rl, cl);
+        __syncwarp();
+        const uint32_t b1 = rl, b2 = rl + cl, lim = (uint32_t)nC + 1u, nC32 = (uint32_t)nC;
+        uint32_t g1 = 0, g2 = 0;
+#pragma unroll 4
+        for (int i = 0; i < len; ++i) {
+            const uint2 e = sp[i];
+            if (b1 > e.x) g1 = min(g1 + min(b1 - e.x, e.y), lim);
+            if (b2 > e.x) g2 = min(g2 + min(b2 - e.x, e.y), lim);
+        }
+        uint32_t key = 0, bg = 0;
+        int hv = 0;
+        if (cl > 0) {
+            if (g1 <= nC32) { key = b1; bg = g1; hv = 1; }
+            if (g2 <= nC32) { key = b2; bg = g2; hv = 1; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(FULL_, key, o);
+            const int oh = __shfl_xor_sync(FULL_, hv, o);
+            const uint32_t og = __shfl_xor_sync(FULL_, bg, o);
+            if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; }
+        }
+        // right slope of g at the winning breakpoint
+        const int bs = __popc(__ballot_sync(FULL_, cl > 0 && key >= rl && key - rl < cl));
+        if (!hv || bs <= 0) {
+            if (lane == 0) atomicOr(err, DERR_LOGIC);
+            return;
+        }
+        const uint32_t L = key + (nC32 - bg) / (uint32_t)bs;
+        uint32_t dj = 0;
+        bool elig = false;
+        if (cl > 0) {
+            if (L > rl) dj = min(L - rl, cl);
+            elig = rl <= L && L - rl < cl;
+        }
+        uint32_t tot = __reduce_add_sync(FULL_, dj);
+        const uint32_t R = nC32 - tot;
+        const unsigned eb = __ballot_sync(FULL_, elig);
+        if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+        if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+        __syncwarp();
+        return;
+    }
+    sr_w[lane] = rj;
+    sc_w[lane] = cj;
+    __syncwarp();
+    // g and right slope at my breakpoints rj and rj + cj
+    const uint64_t b1 = rj, b2 = rj + cj, lim = nC + 1;
+    uint64_t g1 = 0, g2 = 0;
+    int s1 = 0, s2 = 0;
+    for (int i = 0; i < len; ++i) {
+        const uint64_t ri = sr_w[i], ci = sc_w[i];
+        if (ci == 0) continue;
+        if (b1 > ri) { const uint64_t d = b1 - ri; g1 += d < ci ? d : ci; }
+        if (b2 > ri) { const uint64_t d = b2 - ri; g2 += d < ci ? d : ci; }
+        g1 = g1 < lim ? g1 : lim;
+        g2 = g2 < lim ? g2 : lim;
+        s1 += (ri <= b1 && b1 - ri < ci) ? 1 : 0;
+        s2 += (ri <= b2 && b2 - ri < ci) ? 1 : 0;
+    }
+    // best breakpoint of this lane: the larger one with g <= n_C
+    uint64_t bb = 0, bg = 0;
+    int bs = 0;
+    bool have = false;
+    if (cj > 0) {
+        if (g1 <= nC) { bb = b1; bg = g1; bs = s1; have = true; }
+        if (g2 <= nC) { bb = b2; bg = g2; bs = s2; have = true; }
+    }
+    unsigned long long key = have ? (unsigned long long)bb : 0ull;
+    int hv = have ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(FULL_, key, o);
+        const int oh = __shfl_xor_sync(FULL_, hv, o);
+        const uint64_t og = __shfl_xor_sync(FULL_, bg, o);
+        const int os = __shfl_xor_sync(FULL_, bs, o);
+        if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; bs = os; }
+    }
+    if (!hv || bs <= 0) {  // no room below n_C: invariant broken
+        if (lane == 0) atomicOr(err, DERR_LOGIC);
+        return;
+    }
+    const uint64_t L = key + (nC - bg) / (uint64_t)bs;
+    uint64_t dj = 0;
+    bool elig = false;
+    if (cj > 0) {
+        if (L > rj) { const uint64_t d = L - rj; dj = d < cj ? d : cj; }
+        elig = rj <= L && L - rj < cj;
+    }
+    uint64_t tot = dj;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL_, tot, o);
+    const uint64_t R = nC - tot;
+    const unsigned eb = __ballot_sync(FULL_, elig);
+    if (elig && (uint64_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+    if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+    __syncwarp();
+}
+
 template <class RT, bool PIPE>
 __global__ void __launch_bounds__(SB_WARPS * 32, 5)
 k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
@@ -518,8 +745,6 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
           const int32_t *__restrict__ list, const int *list_count, int64_t list_cap, int *err) {
     __shared__ uint64_t sr[SB_WARPS][32];
     __shared__ uint64_t sc[SB_WARPS][32];
-    using AV = typename AccV<RT>::T;
-    const unsigned FULL_ = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int64_t np = *list_count;
     np = np < list_cap ? np : list_cap;
@@ -533,7 +758,12 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
     // per warp, where the prologue would not pay).
     const int64_t st = (int64_t)gridDim.x * SB_WARPS;
     const int64_t li0 = blockIdx.x * (int64_t)SB_WARPS + wib;
-    auto pair_of = [&](int64_t x) -> int64_t { return x < np ? p_begin + list[x] : -1; };
+    // slots marked -1 (claimed by a first-step warp, not used) are skipped
+    auto pair_of = [&](int64_t x) -> int64_t {
+        if (x >= np) return -1;
+        const int32_t l = list[x];
+        return l >= 0 ? p_begin + l : -1;
+    };
     int64_t q3 = -1, q2 = -1, off2 = 0, q1 = -1;
     int len2 = 0, h2 = 0, len1 = 0, h1 = 0, len0 = 0, h0 = 0;
     int32_t raw1 = 0, raw0 = 0;
@@ -553,12 +783,15 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
     for (int64_t li = li0; li < np; li += st) {
         if (!PIPE || li == li0) {  // this pair's own chain
             const int64_t q = pair_of(li);
-            const int64_t o = pair_off[q];
-            len0 = (int)(pair_off[q + 1] - o);
-            h0 = hcnt[q];
-            if (lane < len0 && len0 <= 32) {
-                raw0 = __ldg(nodes + o + lane);
-                r0 = load_r<RT>(r, raw0 & 0x7fffffff);
+            len0 = 0;
+            if (q >= 0) {
+                const int64_t o = pair_off[q];
+                len0 = (int)(pair_off[q + 1] - o);
+                h0 = hcnt[q];
+                if (lane < len0 && len0 <= 32) {
+                    raw0 = __ldg(nodes + o + lane);
+                    r0 = load_r<RT>(r, raw0 & 0x7fffffff);
+                }
             }
         }
         // the current pair
@@ -585,179 +818,172 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
             if (lane == 0) atomicOr(err, DERR_CAPACITY);
             continue;
         }
-        const int p = len - h;
-        const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
-        const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
-                                   ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
-        int32_t id = -1;
-        uint64_t rj = 0, cj = 0;
-        if (lane < len) {
-            id = rawc & 0x7fffffff;
-            rj = rjc;
-            cj = rawc < 0 ? nC : cap_p;
-        }
-        // levels relative to the lowest node that can receive: 32-bit when
-        // the spread and n_C fit in 31 bits (the usual case).  64-bit min and
-        // max as two 32-bit warp reductions (high word, then low word).
-        const uint64_t vb = cj > 0 ? rj : ~0ull;
-        const uint32_t bh = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32));
-        const uint32_t bl = __reduce_min_sync(FULL_, (uint32_t)(vb >> 32) == bh ? (uint32_t)vb : 0xffffffffu);
-        const uint64_t base = ((uint64_t)bh << 32) | bl;
-        if (__all_sync(FULL_, cj == 0 || rj - base < (1ull << 31)) && nC < (1ull << 31)) {
-            const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
-            // The walk of Alg. 3 with warp-uniform state: at water level L the
-            // receiving nodes are those with rl <= L < rl + cl; the level rises
-            // to the next event (a node's level, or a receiving node's level
-            // plus cap) while the units last, and stops at
-            // L* = L + floor(rem / na) with R = rem mod na units left for the
-            // lowest ids receiving at L*.  A level where every node is capped
-            // jumps to the next node.  Pairs that cross more than SB_ROUNDS
-            // events take the closed form below.
-            {
-                const uint32_t nC32 = (uint32_t)nC, INF32 = 0xffffffffu;
-                uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
-                bool done = false;
-                for (int round = 0; round < SB_ROUNDS; ++round) {
-                    const bool act = cl > 0 && rl <= L && L - rl < cl;
-                    const uint32_t na = (uint32_t)__popc(__ballot_sync(FULL_, act));
-                    const uint32_t e1 = (cl > 0 && rl > L) ? rl : INF32;
-                    const uint32_t e2 = act ? rl + cl : INF32;
-                    const uint32_t ev = __reduce_min_sync(FULL_, e1 < e2 ? e1 : e2);
-                    if (na == 0) {
-                        if (ev == INF32) break;
-                        L = ev;
-                        continue;
-                    }
-                    // the units end before the next event, or exactly at it
-                    // (then nothing is left over and L* = ev allocates the
-                    // same): floor(rem / na) < ev - L, or rem = (ev - L) na,
-                    // which is rem <= (ev - L) na; one division at the end
-                    const uint64_t span = (uint64_t)(ev - L) * na;
-                    if (ev == INF32 || rem <= span) {
-                        const uint32_t qd = rem / na;
-                        Ls = L + qd;
-                        R = rem - qd * na;
-                        done = true;
-                        break;
-                    }
-                    rem -= (uint32_t)span;
-                    L = ev;
-                }
-                if (done) {
-                    uint32_t dj = 0;
-                    bool elig = false;
-                    if (cl > 0) {
-                        if (Ls > rl) dj = min(Ls - rl, cl);
-                        elig = rl <= Ls && Ls - rl < cl;
-                    }
-                    const unsigned eb = __ballot_sync(FULL_, elig);
-                    if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
-                    if (dj) atomicAdd((AV *)acc + id, (AV)dj);
-                    __syncwarp();
-                    continue;
-                }
-            }
-            // (level, cap) of every node as one 64-bit word; a zero cap adds
-            // nothing below (min(d, 0) = 0), so no special case
-            uint2 *sp = (uint2 *)sr[wib];
-            sp[lane] = make_uint2(rl, cl);
-            __syncwarp();
-            const uint32_t b1 = rl, b2 = rl + cl, lim = (uint32_t)nC + 1u, nC32 = (uint32_t)nC;
-            uint32_t g1 = 0, g2 = 0;
-#pragma unroll 4
-            for (int i = 0; i < len; ++i) {
-                const uint2 e = sp[i];
-                if (b1 > e.x) g1 = min(g1 + min(b1 - e.x, e.y), lim);
-                if (b2 > e.x) g2 = min(g2 + min(b2 - e.x, e.y), lim);
-            }
-            uint32_t key = 0, bg = 0;
-            int hv = 0;
-            if (cl > 0) {
-                if (g1 <= nC32) { key = b1; bg = g1; hv = 1; }
-                if (g2 <= nC32) { key = b2; bg = g2; hv = 1; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const uint32_t ok = __shfl_xor_sync(FULL_, key, o);
-                const int oh = __shfl_xor_sync(FULL_, hv, o);
-                const uint32_t og = __shfl_xor_sync(FULL_, bg, o);
-                if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; }
-            }
-            // right slope of g at the winning breakpoint
-            const int bs = __popc(__ballot_sync(FULL_, cl > 0 && key >= rl && key - rl < cl));
-            if (!hv || bs <= 0) {
-                if (lane == 0) atomicOr(err, DERR_LOGIC);
+        if (len == 0) continue;  // an unused slot
+        using AVs = typename AccV<RT>::T;
+        slow_pair_walk<AVs>(len, h, rawc, rjc, k, binom, bcols, acc, sr[wib], sc[wib], err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Work-queue iteration (rule I) over one or several SCTs at once.  Persistent
+// warps take work items from a device counter: an item is a run of tiles
+// (32 consecutive pairs of at most 32 nodes) of one SCT, or a run of its
+// longer pairs.  A tile goes through the first step of k_pb_fast, and every
+// pair the first step leaves is walked right away by the same warp from the
+// tile already staged in shared memory (no slow list, no second read).
+// Longer pairs take the group walk, `tpp` lanes per pair.  One launch does
+// the PBUpdate pass of every SCT of the batch; the items' size (tiles per
+// item) and the lanes per long pair are the tuning knobs.
+// ---------------------------------------------------------------------------
+constexpr int QW = 4;   // warps per block of the queue kernel
+
+struct QSmem {
+    int32_t sid[QW][FA_CAP];
+    uint64_t sval[QW][FA_CAP];
+    uint64_t sr[QW][32], sc[QW][32];   // walk scratch
+};
+
+template <class RT>
+__global__ void __launch_bounds__(QW * 32)
+k_pb_queue(const QGroup *__restrict__ groups, const QItem *__restrict__ items, int nitems,
+           unsigned *cursor, RT *r_all, RT *acc_all, int *err) {
+    extern __shared__ __align__(16) unsigned char q_smem[];
+    QSmem &S = *reinterpret_cast<QSmem *>(q_smem);
+    using AV = typename AccV<RT>::T;
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t *sid = S.sid[wib];
+    uint64_t *sv = S.sval[wib];
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(cursor, 1u);
+        it = __shfl_sync(FULL_, it, 0);
+        if (it >= nitems) break;
+        const QItem I = items[it];
+        const QGroup G = groups[I.g];
+        const RT *r = r_all + G.node_off;
+        AV *acc = reinterpret_cast<AV *>(acc_all + G.node_off);
+        const int k = G.k, bcols = G.bcols;
+        const int64_t np = G.short_end;
+        for (int64_t tile = I.first; tile < I.first + I.count; ++tile) {
+            const int64_t qi = tile * 32 + lane;
+            const bool valid = qi < np;
+            const int64_t q = valid ? qi : np - 1;
+            const int64_t myb = G.pair_off[q], mye = G.pair_off[q + 1];
+            const int64_t B = __shfl_sync(FULL_, myb, 0);
+            const int64_t E = __shfl_sync(FULL_, mye, 31);
+            const int cnt = (int)(E - B);
+            if (cnt > FA_CAP) {
+                if (lane == 0) atomicOr(err, DERR_CAPACITY);
                 continue;
             }
-            const uint32_t L = key + (nC32 - bg) / (uint32_t)bs;
-            uint32_t dj = 0;
-            bool elig = false;
-            if (cl > 0) {
-                if (L > rl) dj = min(L - rl, cl);
-                elig = rl <= L && L - rl < cl;
-            }
-            uint32_t tot = __reduce_add_sync(FULL_, dj);
-            const uint32_t R = nC32 - tot;
-            const unsigned eb = __ballot_sync(FULL_, elig);
-            if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
-            if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+            for (int i = lane; i < cnt; i += 32) cp_async4(sid + i, G.nodes + B + i);
+            cp_async_wait_all();
             __syncwarp();
-            continue;
+            for (int i = lane; i < cnt; i += 32) cp_async8(sv + i, r + (sid[i] & 0x7fffffff));
+            cp_async_wait_all();
+            __syncwarp();
+            const int o = (int)(myb - B);
+            const int len = (int)(mye - myb);
+            const int h = valid ? (int)G.h[q] : 0;
+            uint32_t rmask = 0;
+            bool want_slow = false;
+            uint64_t w = 0, R = 0;
+            if (valid && h <= k && k <= len) {
+                const int p = len - h;
+                const uint64_t nC = __ldg(G.binom + (size_t)p * bcols + (k - h));
+                const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                                           ? __ldg(G.binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+                const uint64_t pm = cap_p > 0 ? 0ull : ~0ull;
+                uint64_t m1 = ~0ull, m2 = ~0ull;
+                uint32_t mask1 = 0;
+                bool piv1 = false;
+                for (int s2 = 0; s2 < len; ++s2) {
+                    const uint64_t e = sv[o + s2];
+                    const bool hold = sid[o + s2] < 0;
+                    const uint64_t v = e | (hold ? 0ull : pm);
+                    const bool lt = v < m1;
+                    const bool eq = v == m1 && v != ~0ull;
+                    const uint64_t mn = v < m2 ? v : m2;
+                    m2 = lt ? m1 : (eq ? m2 : mn);
+                    m1 = lt ? v : m1;
+                    const uint32_t bit = 1u << s2;
+                    mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                    piv1 = lt ? !hold : (piv1 || (eq && !hold));
+                }
+                if (mask1) {
+                    const uint64_t na = (uint64_t)__popc(mask1);
+                    const uint64_t mu = piv1 ? cap_p : nC;
+                    const uint64_t gap = m2 == ~0ull ? ~0ull : level_of<RT>(m2) - level_of<RT>(m1);
+                    w = nC / na;
+                    R = nC - w * na;
+                    const uint64_t lim = mu < gap ? mu : gap;
+                    if (!(R == 0 ? w > lim : w >= lim)) rmask = mask1;
+                    else want_slow = true;
+                }
+            }
+            // the pairs the first step leaves, one by one, by the whole warp
+            unsigned um = __ballot_sync(FULL_, want_slow);
+            while (um) {
+                const int src = __ffs(um) - 1;
+                um &= um - 1;
+                const int so = __shfl_sync(FULL_, o, src);
+                const int sl = __shfl_sync(FULL_, len, src);
+                const int shh = __shfl_sync(FULL_, h, src);
+                int32_t rawc = 0;
+                uint64_t rjc = 0;
+                if (lane < sl) {
+                    rawc = sid[so + lane];
+                    rjc = level_of<RT>(sv[so + lane]);
+                }
+                slow_pair_walk<AV>(sl, shh, rawc, rjc, k, G.binom, bcols, acc, S.sr[wib], S.sc[wib],
+                                   err);
+            }
+            uint64_t rank = 0;
+            while (__any_sync(FULL_, rmask != 0)) {
+                int32_t rid = -1;
+                AV amount = AV(0);
+                if (rmask) {
+                    const int sl = __ffs(rmask) - 1;
+                    rmask &= rmask - 1;
+                    const uint64_t dl = w + (rank < R ? 1ull : 0ull);
+                    ++rank;
+                    if (dl) {
+                        rid = sid[o + sl] & 0x7fffffff;
+                        amount = (AV)dl;
+                    }
+                }
+                warp_seg_add<AV>(rid, amount, acc);
+            }
+            __syncwarp();
         }
-        sr[wib][lane] = rj;
-        sc[wib][lane] = cj;
-        __syncwarp();
-        // g and right slope at my breakpoints rj and rj + cj
-        const uint64_t b1 = rj, b2 = rj + cj, lim = nC + 1;
-        uint64_t g1 = 0, g2 = 0;
-        int s1 = 0, s2 = 0;
-        for (int i = 0; i < len; ++i) {
-            const uint64_t ri = sr[wib][i], ci = sc[wib][i];
-            if (ci == 0) continue;
-            if (b1 > ri) { const uint64_t d = b1 - ri; g1 += d < ci ? d : ci; }
-            if (b2 > ri) { const uint64_t d = b2 - ri; g2 += d < ci ? d : ci; }
-            g1 = g1 < lim ? g1 : lim;
-            g2 = g2 < lim ? g2 : lim;
-            s1 += (ri <= b1 && b1 - ri < ci) ? 1 : 0;
-            s2 += (ri <= b2 && b2 - ri < ci) ? 1 : 0;
+    }
+}
+
+// The longer pairs of the work-queue pass: items of pairs of one SCT, G lanes
+// per pair (NPL slots per lane), GPW = 32 / G pairs per warp at a time.
+template <class RT, int G, int NPL>
+__global__ void __launch_bounds__(FW_THREADS)
+k_pb_queue_long(const QGroup *__restrict__ groups, const QItem *__restrict__ items, int nitems,
+                unsigned *cursor, RT *r_all, RT *acc_all, int *err) {
+    using AV = typename AccV<RT>::T;
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(cursor, 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= nitems) break;
+        const QItem I = items[it];
+        const QGroup Gd = groups[I.g];
+        const RT *r = r_all + Gd.node_off;
+        AV *acc = reinterpret_cast<AV *>(acc_all + Gd.node_off);
+        for (int64_t q0 = I.first; q0 < I.first + I.count; q0 += GPW) {
+            const int64_t q = q0 + lane / G;
+            group_pair_walk<G, NPL, RT>(q < I.first + I.count, q, Gd.pair_off, Gd.nodes, Gd.h, r,
+                                        Gd.binom, Gd.bcols, Gd.k, err,
+                                        [&](int32_t id, uint64_t x) { atomicAdd(acc + id, (AV)x); });
         }
-        // best breakpoint of this lane: the larger one with g <= n_C
-        uint64_t bb = 0, bg = 0;
-        int bs = 0;
-        bool have = false;
-        if (cj > 0) {
-            if (g1 <= nC) { bb = b1; bg = g1; bs = s1; have = true; }
-            if (g2 <= nC) { bb = b2; bg = g2; bs = s2; have = true; }
-        }
-        unsigned long long key = have ? (unsigned long long)bb : 0ull;
-        int hv = have ? 1 : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(FULL_, key, o);
-            const int oh = __shfl_xor_sync(FULL_, hv, o);
-            const uint64_t og = __shfl_xor_sync(FULL_, bg, o);
-            const int os = __shfl_xor_sync(FULL_, bs, o);
-            if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; bs = os; }
-        }
-        if (!hv || bs <= 0) {  // no room below n_C: invariant broken
-            if (lane == 0) atomicOr(err, DERR_LOGIC);
-            continue;
-        }
-        const uint64_t L = key + (nC - bg) / (uint64_t)bs;
-        uint64_t dj = 0;
-        bool elig = false;
-        if (cj > 0) {
-            if (L > rj) { const uint64_t d = L - rj; dj = d < cj ? d : cj; }
-            elig = rj <= L && L - rj < cj;
-        }
-        uint64_t tot = dj;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL_, tot, o);
-        const uint64_t R = nC - tot;
-        const unsigned eb = __ballot_sync(FULL_, elig);
-        if (elig && (uint64_t)__popc(eb & lanemask_lt()) < R) dj += 1;
-        if (dj) atomicAdd((AV *)acc + id, (AV)dj);
-        __syncwarp();
     }
 }
 
@@ -801,8 +1027,8 @@ __global__ void __launch_bounds__(FA_WARPS * 32)
 k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
                const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
                const float *__restrict__ r, float *acc, float *accc,
-               const uint64_t *__restrict__ binom, int bcols, int k, const int *t_done,
-               int32_t *slow, int *slow_count, int *err) {
+               const float *__restrict__ binomf, int bcols, int k, const int *t_done,
+               int32_t *slow, int *slow_count, int64_t slow_cap, int *err) {
     __shared__ float sval[FA_WARPS][FA_CAP];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t np = p_end - p_begin;
@@ -833,14 +1059,16 @@ k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
         uint32_t rmask = 0;
         float share = 0.f;
         int o = 0;
-        if (valid) {
+        bool want_slow = false;
+        const int hq = valid ? (int)hcnt[q] : 0;   // P_k filter, as k_pb_fast
+        if (valid && hq <= k && k <= (int)(mye - myb)) {
             o = (int)(myb - B);
             const int len = (int)(mye - myb);
-            const int h = hcnt[q];
+            const int h = hq;
             const int p = len - h;
-            const float nC = (float)__ldg(binom + (size_t)p * bcols + (k - h)) * inv_sigma;
+            const float nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
             const float cap_p = (p >= 1 && k - h - 1 >= 0)
-                                    ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                                    ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
                                     : 0.f;
             // branch-free pass as in k_pb_fast; zero-cap pivot nodes read as +inf
             const bool prx = cap_p > 0.f;
@@ -864,14 +1092,11 @@ k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
                 const float na = (float)__popc(mask1);
                 const float mu = piv1 ? cap_p : nC;
                 share = nC / na;
-                if (share <= mu && share <= m2 - m1) {
-                    rmask = mask1;
-                } else {
-                    const int slot = atomicAdd(slow_count, 1);
-                    if (slot < np) slow[slot] = (int32_t)qi;
-                }
+                if (share <= mu && share <= m2 - m1) rmask = mask1;
+                else want_slow = true;
             }
         }
+        slow_append(want_slow, (int32_t)qi, slow, slow_count, slow_cap, err);
         while (__any_sync(0xffffffffu, rmask != 0)) {
             int32_t rid = -1;
             float amount = 0.f;
@@ -896,7 +1121,7 @@ template <bool PIPE>
 __global__ void __launch_bounds__(SB_WARPS * 32, 5)
 k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
               const uint8_t *__restrict__ hcnt, int64_t p_begin, const float *__restrict__ r,
-              float *acc, float *accc, const uint64_t *__restrict__ binom, int bcols, int k,
+              float *acc, float *accc, const float *__restrict__ binomf, int bcols, int k,
               const int *t_done, const int32_t *__restrict__ list, const int *list_count,
               int64_t list_cap, int *err) {
     __shared__ float2 sp[SB_WARPS][32];
@@ -909,7 +1134,12 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
     // the load pipeline of k_pb_slow (PIPE) or one chain per pair
     const int64_t st = (int64_t)gridDim.x * SB_WARPS;
     const int64_t li0 = blockIdx.x * (int64_t)SB_WARPS + wib;
-    auto pair_of = [&](int64_t x) -> int64_t { return x < np ? p_begin + list[x] : -1; };
+    // slots marked -1 (claimed by a first-step warp, not used) are skipped
+    auto pair_of = [&](int64_t x) -> int64_t {
+        if (x >= np) return -1;
+        const int32_t l = list[x];
+        return l >= 0 ? p_begin + l : -1;
+    };
     int64_t q3 = -1, q2 = -1, off2 = 0, q1 = -1;
     int len2 = 0, h2 = 0, len1 = 0, h1 = 0, len0 = 0, h0 = 0;
     int32_t raw1 = 0, raw0 = 0;
@@ -929,12 +1159,15 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
     for (int64_t li = li0; li < np; li += st) {
         if (!PIPE || li == li0) {
             const int64_t q = pair_of(li);
-            const int64_t o = pair_off[q];
-            len0 = (int)(pair_off[q + 1] - o);
-            h0 = hcnt[q];
-            if (lane < len0 && len0 <= 32) {
-                raw0 = __ldg(nodes + o + lane);
-                x0 = __ldg(r + (raw0 & 0x7fffffff));
+            len0 = 0;
+            if (q >= 0) {
+                const int64_t o = pair_off[q];
+                len0 = (int)(pair_off[q + 1] - o);
+                h0 = hcnt[q];
+                if (lane < len0 && len0 <= 32) {
+                    raw0 = __ldg(nodes + o + lane);
+                    x0 = __ldg(r + (raw0 & 0x7fffffff));
+                }
             }
         }
         const int len = len0, h = h0;
@@ -958,10 +1191,11 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
             if (lane == 0) atomicOr(err, DERR_CAPACITY);
             continue;
         }
+        if (len == 0) continue;  // an unused slot
         const int p = len - h;
-        const float nC = (float)__ldg(binom + (size_t)p * bcols + (k - h)) * inv_sigma;
+        const float nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
         const float cap_p = (p >= 1 && k - h - 1 >= 0)
-                                ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                                ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
                                 : 0.f;
         int32_t id = -1;
         float xj = 0.f, cj = 0.f;
@@ -1056,7 +1290,7 @@ __global__ void __launch_bounds__(FW_THREADS)
 k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
                const uint8_t *__restrict__ hcnt, int64_t p_begin, int64_t p_end,
                const float *__restrict__ r, float *acc, float *accc,
-               const uint64_t *__restrict__ binom, int bcols, int k, const int *t_done,
+               const float *__restrict__ binomf, int bcols, int k, const int *t_done,
                const int32_t *list, const int *list_count, int *err) {
     constexpr int GPW = 32 / G;
     const float inv_sigma = inv_sigma_of(t_done);
@@ -1088,13 +1322,14 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
             len = (int)(pair_off[q + 1] - off0);
             h = hcnt[q];
         }
+        const bool inpk = active && h <= k && k <= len;   // P_k filter, as k_pbupdate_int
         const int p = len - h;
         float nC = 0.f, cap_h = 0.f, cap_p = 0.f;
-        if (active) {
-            nC = (float)__ldg(binom + (size_t)p * bcols + (k - h)) * inv_sigma;
+        if (inpk) {
+            nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
             cap_h = nC;
             cap_p = (p >= 1 && k - h - 1 >= 0)
-                        ? (float)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                        ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
                         : 0.f;
         }
         float r0[NPL], cur[NPL], up[NPL];
@@ -1102,14 +1337,14 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int j = s * G + gl;
-            const bool valid = active && j < len;
+            const bool valid = inpk && j < len;
             const int32_t raw = valid ? __ldg(nodes + off0 + j) : 0;
             id[s] = raw & 0x7fffffff;
             r0[s] = valid ? __ldg(r + id[s]) : INF;
             up[s] = valid ? (raw < 0 ? cap_h : cap_p) : 0.f;
             cur[s] = r0[s];
         }
-        float rem = active ? nC : 0.f;
+        float rem = inpk ? nC : 0.f;
         // Work relative to the pair's lowest active level, so that the
         // allocation (final level - start) is not a difference of two large
         // values of r.
@@ -1165,7 +1400,7 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int j = s * G + gl;
-            if (active && j < len && cur[s] > r0[s])
+            if (inpk && j < len && cur[s] > r0[s])
                 agg_add_f32(tbl, id[s], cur[s] - r0[s], acc, accc);
         }
     }
@@ -1242,28 +1477,29 @@ inline bool slow_pipelined(int64_t short_pairs, int grid) {
 // leaves take the group walk (8 lanes x 4 slots); longer pairs take the
 // 32-lane group walk directly.
 template <class RT>
-void launch_pbupdate_int(const Ctx &c, const SctDev &s, RT *r, RT *acc, int32_t *slow,
+void launch_pbupdate_int(const Ctx &c, const SctDev &s, int k, RT *r, RT *acc, int32_t *slow,
                          int *slow_count, int *err) {
-    const int bc = s.k + 1;
+    const int bc = s.bcols();
     const int64_t b = s.class_begin[0], e = s.class_begin[3];
     auto go = [&](auto kern, int G, int64_t pb, int64_t pe, const int32_t *list, const int *lc) {
         const int64_t groups_per_block = (FW_THREADS / 32) * (32 / G);
         int grid = (int)std::min<int64_t>(ceil_div(pe - pb, groups_per_block), (int64_t)c.num_sms * 4);
         kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, pb, pe, r, acc,
-                                                s.binom.p, bc, s.k, list, lc, err);
+                                                s.binom.p, bc, k, list, lc, err);
         KDSS_LAUNCH_CHECK();
     };
     if (e > b) {
         const int64_t tiles = ceil_div(e - b, 32);
+        const int64_t cap = slow_list_capacity(e - b, c.num_sms);
         int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
         k_pb_fast<RT><<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, r,
-                                                            acc, s.binom.p, bc, s.k, slow, slow_count,
-                                                            err);
+                                                            acc, s.binom.p, bc, k, slow, slow_count,
+                                                            cap, err);
         KDSS_LAUNCH_CHECK();
         int sgrid = (int)std::min<int64_t>(ceil_div(e - b, SB_WARPS), (int64_t)c.num_sms * 8);
         auto slow_kern = slow_pipelined(e - b, sgrid) ? k_pb_slow<RT, true> : k_pb_slow<RT, false>;
         slow_kern<<<sgrid, SB_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, r, acc,
-                                                         s.binom.p, bc, s.k, slow, slow_count, e - b,
+                                                         s.binom.p, bc, k, slow, slow_count, cap,
                                                          err);
         KDSS_LAUNCH_CHECK();
     }
@@ -1273,31 +1509,32 @@ void launch_pbupdate_int(const Ctx &c, const SctDev &s, RT *r, RT *acc, int32_t 
         go(k_pbupdate_int<32, 32, RT>, 32, s.class_begin[4], s.class_begin[5], nullptr, nullptr);
 }
 
-void launch_pbupdate_f32_on(const Ctx &c, const SctDev &s, StateDev &st, float *r32, float *a32,
-                            float *a32c) {
-    const int bc = s.k + 1;
+void launch_pbupdate_f32_on(const Ctx &c, const SctDev &s, int k, StateDev &st, float *r32,
+                            float *a32, float *a32c) {
+    const int bc = s.bcols();
     const int64_t b = s.class_begin[0], e = s.class_begin[3];
     auto go = [&](auto kern, int G, int64_t pb, int64_t pe, const int32_t *list, const int *lc) {
         const int64_t groups_per_block = (FW_THREADS / 32) * (32 / G);
         int grid = (int)std::min<int64_t>(ceil_div(pe - pb, groups_per_block), (int64_t)c.num_sms * 4);
         kern<<<grid, FW_THREADS, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, pb, pe, r32,
-                                                a32, a32c, s.binom.p, bc, s.k,
+                                                a32, a32c, s.binomf.p, bc, k,
                                                 st.dev_t.p, list, lc, st.err.p);
         KDSS_LAUNCH_CHECK();
     };
     if (e > b) {
         const int64_t tiles = ceil_div(e - b, 32);
+        const int64_t cap = slow_list_capacity(e - b, c.num_sms);
         int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
         k_pb_fast_f32s<<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
-                                                           r32, a32, a32c, s.binom.p, bc, s.k,
+                                                           r32, a32, a32c, s.binomf.p, bc, k,
                                                            st.dev_t.p, st.ovf_list.p,
-                                                           st.ovf_count.p, st.err.p);
+                                                           st.ovf_count.p, cap, st.err.p);
         KDSS_LAUNCH_CHECK();
         int sgrid = (int)std::min<int64_t>(ceil_div(e - b, SB_WARPS), (int64_t)c.num_sms * 8);
         auto slow_kern = slow_pipelined(e - b, sgrid) ? k_pb_slow_f32<true> : k_pb_slow_f32<false>;
         slow_kern<<<sgrid, SB_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, r32,
-                                                         a32, a32c, s.binom.p, bc, s.k, st.dev_t.p,
-                                                         st.ovf_list.p, st.ovf_count.p, e - b,
+                                                         a32, a32c, s.binomf.p, bc, k, st.dev_t.p,
+                                                         st.ovf_list.p, st.ovf_count.p, cap,
                                                          st.err.p);
         KDSS_LAUNCH_CHECK();
     }
@@ -1308,7 +1545,7 @@ void launch_pbupdate_f32_on(const Ctx &c, const SctDev &s, StateDev &st, float *
 }
 
 void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
-    launch_pbupdate_f32_on(c, s, st, st.r32.p, st.a32.p, st.a32c.p);
+    launch_pbupdate_f32_on(c, s, st.k, st, st.r32.p, st.a32.p, st.a32c.p);
 }
 
 struct EventPair {
@@ -1317,11 +1554,20 @@ struct EventPair {
 
 }  // namespace
 
-void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st) {
+int64_t slow_list_capacity(int64_t short_pairs, int) { return short_pairs; }
+
+void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st, int k) {
     st.precision = precision;
     st.n = s.n;
     st.t = 0;
     st.ctx = c;
+    st.k = k < 0 ? s.k : k;
+    if (st.k == s.k) {
+        st.ck_lo = s.ck_lo;
+        st.ck_hi = s.ck_hi;
+    } else {
+        sct_ck_at(c, s, st.k, st.ck_lo, st.ck_hi);
+    }
     const size_t n = (size_t)std::max<int64_t>(s.n, 1);
     if (precision == KDSS_FP32K) {
         st.r32 = DBuf<float>(c, n);
@@ -1343,7 +1589,7 @@ void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st) {
     st.dev_t = DBuf<int>(c, 2);  // [0] iterations done, [1] blocks-done counter
     zero(c, st.dev_t.p, 2 * sizeof(int));
     const int64_t short_pairs = std::max<int64_t>(1, s.class_begin[3] - s.class_begin[0]);
-    st.ovf_list = DBuf<int32_t>(c, (size_t)short_pairs);
+    st.ovf_list = DBuf<int32_t>(c, (size_t)slow_list_capacity(short_pairs, c.num_sms));
     st.ovf_count = DBuf<int>(c, 1);
     zero(c, st.ovf_count.p, sizeof(int));
     zero(c, st.maxr.p, 8);
@@ -1353,13 +1599,15 @@ void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st) {
 namespace {
 
 void enqueue_pbupdate(const Ctx &c, const SctDev &s, StateDev &st) {
-    if (st.precision == KDSS_FP32K) {
+    if (st.qchunk > 0 && st.precision != KDSS_FP32K) {
+        queue_enqueue(c, st.qplan, st);
+    } else if (st.precision == KDSS_FP32K) {
         launch_pbupdate_f32(c, s, st);
     } else if (st.precision == KDSS_FP64) {
-        launch_pbupdate_int<double>(c, s, (double *)st.r.p, (double *)st.acc.p, st.ovf_list.p,
+        launch_pbupdate_int<double>(c, s, st.k, (double *)st.r.p, (double *)st.acc.p, st.ovf_list.p,
                                     st.ovf_count.p, st.err.p);
     } else {
-        launch_pbupdate_int<uint64_t>(c, s, st.r.p, st.acc.p, st.ovf_list.p, st.ovf_count.p,
+        launch_pbupdate_int<uint64_t>(c, s, st.k, st.r.p, st.acc.p, st.ovf_list.p, st.ovf_count.p,
                                       st.err.p);
     }
 }
@@ -1434,7 +1682,7 @@ void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
     // exactness of the cumulative r: r_t(u) <= t * c_k
     if (st.precision != KDSS_FP32K) {
         const long double lim = st.precision == KDSS_INT64 ? 9.2e18L : 9.007199254740992e15L;
-        const long double ck = (long double)s.ck_lo + (long double)s.ck_hi * 18446744073709551616.0L;
+        const long double ck = (long double)st.ck_lo + (long double)st.ck_hi * 18446744073709551616.0L;
         if ((long double)(st.t + T) * ck >= lim)
             fail(KDSS_ERR_OVERFLOW, "T * c_k leaves the exact range of r");
     }
@@ -1442,6 +1690,8 @@ void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
     // per (state, SCT) and replayed T times on the caller's stream.
     if (st.graph_sct != &s) {
         st.release_graphs();
+        if (st.qchunk > 0 && st.precision != KDSS_FP32K)
+            queue_plan(c, {{&s, 0}}, st.qchunk, st.qtpp, st.qplan, st.k);
         st.nk_pb = capture(c, &st.g_pb, [&](const Ctx &cc) { enqueue_pbupdate(cc, s, st); });
         st.nk_step = capture(c, &st.g_step, [&](const Ctx &cc) { enqueue_step(cc, s, st); });
         capture(c, &st.g_iter, [&](const Ctx &cc) {
@@ -1504,7 +1754,7 @@ void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, 
     const int B = 256;
     const int sgrid = grid_for(c, n, B, 4);
     for (int it = 0; it < T; ++it) {
-        launch_pbupdate_int<uint64_t>(c, s, r, acc, slow, slow_count, err);
+        launch_pbupdate_int<uint64_t>(c, s, s.k, r, acc, slow, slow_count, err);
         if (n > 0) {
             k_step_int<uint64_t><<<sgrid, B, 0, c.stream>>>(n, r, acc, maxr, slow_count);
             KDSS_LAUNCH_CHECK();
@@ -1526,18 +1776,18 @@ void fw_run_async(const Ctx &c, const SctDev &s, StateDev &st, int T) {
     if (st.precision == KDSS_FP32K)
         fail(KDSS_ERR_UNSUPPORTED, "in-place iterations exist for the integer rule only");
     const long double lim = st.precision == KDSS_INT64 ? 9.2e18L : 9.007199254740992e15L;
-    const long double ck = (long double)s.ck_lo + (long double)s.ck_hi * 18446744073709551616.0L;
+    const long double ck = (long double)st.ck_lo + (long double)st.ck_hi * 18446744073709551616.0L;
     if ((long double)(st.t + T) * ck >= lim)
         fail(KDSS_ERR_OVERFLOW, "T * c_k leaves the exact range of r");
     cudaGraphExec_t exec = nullptr;
     const long long nk = capture(c, &exec, [&](const Ctx &cc) {
         KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), cc.stream));
         if (st.precision == KDSS_FP64)
-            launch_pbupdate_int<double>(cc, s, (double *)st.r.p, (double *)st.r.p, st.ovf_list.p,
-                                        st.ovf_count.p, st.err.p);
+            launch_pbupdate_int<double>(cc, s, st.k, (double *)st.r.p, (double *)st.r.p,
+                                        st.ovf_list.p, st.ovf_count.p, st.err.p);
         else
-            launch_pbupdate_int<uint64_t>(cc, s, st.r.p, st.r.p, st.ovf_list.p, st.ovf_count.p,
-                                          st.err.p);
+            launch_pbupdate_int<uint64_t>(cc, s, st.k, st.r.p, st.r.p, st.ovf_list.p,
+                                          st.ovf_count.p, st.err.p);
     });
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < T && e == cudaSuccess; ++it) {
@@ -1558,10 +1808,11 @@ void fw_enqueue_inplace(const Ctx &c, const SctDev &s, StateDev &st) {
         fail(KDSS_ERR_UNSUPPORTED, "in-place iterations exist for the integer rule only");
     KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), c.stream));
     if (st.precision == KDSS_FP64)
-        launch_pbupdate_int<double>(c, s, (double *)st.r.p, (double *)st.r.p, st.ovf_list.p,
+        launch_pbupdate_int<double>(c, s, st.k, (double *)st.r.p, (double *)st.r.p, st.ovf_list.p,
                                     st.ovf_count.p, st.err.p);
     else
-        launch_pbupdate_int<uint64_t>(c, s, st.r.p, st.r.p, st.ovf_list.p, st.ovf_count.p, st.err.p);
+        launch_pbupdate_int<uint64_t>(c, s, st.k, st.r.p, st.r.p, st.ovf_list.p, st.ovf_count.p,
+                                      st.err.p);
 }
 
 // ---- several SCTs over disjoint node ranges sharing one state (batches) ----
@@ -1578,14 +1829,15 @@ void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_
     // the slow-pair list is shared by the groups of one iteration
     KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), c.stream));
     if (st.precision == KDSS_FP32K) {
-        launch_pbupdate_f32_on(c, s, st, st.r32.p + node_off, st.a32.p + node_off,
+        launch_pbupdate_f32_on(c, s, s.k, st, st.r32.p + node_off, st.a32.p + node_off,
                                st.a32c.p + node_off);
     } else if (st.precision == KDSS_FP64) {
-        launch_pbupdate_int<double>(c, s, (double *)st.r.p + node_off, (double *)st.acc.p + node_off,
-                                    st.ovf_list.p, st.ovf_count.p, st.err.p);
+        launch_pbupdate_int<double>(c, s, s.k, (double *)st.r.p + node_off,
+                                    (double *)st.acc.p + node_off, st.ovf_list.p, st.ovf_count.p,
+                                    st.err.p);
     } else {
-        launch_pbupdate_int<uint64_t>(c, s, st.r.p + node_off, st.acc.p + node_off, st.ovf_list.p,
-                                      st.ovf_count.p, st.err.p);
+        launch_pbupdate_int<uint64_t>(c, s, s.k, st.r.p + node_off, st.acc.p + node_off,
+                                      st.ovf_list.p, st.ovf_count.p, st.err.p);
     }
 }
 
@@ -1607,6 +1859,106 @@ void fw_enqueue_step_range(const Ctx &c, StateDev &st, int64_t node_off, int64_t
                                                         st.maxr.p, st.ovf_count.p);
     }
     KDSS_LAUNCH_CHECK();
+}
+
+// ---- work-queue plans ----
+
+void queue_plan(const Ctx &c, const std::vector<std::pair<const SctDev *, int64_t>> &sets, int chunk,
+                int tpp, QueuePlan &qp, int k) {
+    qp.chunk = std::max(1, chunk);
+    qp.tpp = tpp == 8 ? 8 : 32;
+    std::vector<QGroup> hg;
+    std::vector<QItem> hi, hl[2];
+    for (size_t g = 0; g < sets.size(); ++g) {
+        const SctDev &s = *sets[g].first;
+        QGroup d{};
+        d.pair_off = s.pair_off.p;
+        d.nodes = s.nodes.p;
+        d.h = s.h.p;
+        d.binom = s.binom.p;
+        d.bcols = s.bcols();
+        d.k = k >= 0 ? k : s.k;
+        d.node_off = sets[g].second;
+        d.short_end = s.class_begin[3];
+        d.long_begin[0] = s.class_begin[3];
+        d.long_end[0] = s.class_begin[4];
+        d.long_begin[1] = s.class_begin[4];
+        d.long_end[1] = s.class_begin[5];
+        hg.push_back(d);
+        const int64_t tiles = ceil_div(d.short_end, 32);
+        for (int64_t t = 0; t < tiles; t += qp.chunk)
+            hi.push_back(QItem{(int32_t)g, 0, t, (int32_t)std::min<int64_t>(qp.chunk, tiles - t), 0});
+        for (int kind = 1; kind <= 2; ++kind) {
+            const int64_t b = d.long_begin[kind - 1], e = d.long_end[kind - 1];
+            const int64_t per = 8 * (int64_t)qp.chunk;
+            for (int64_t q = b; q < e; q += per)
+                hl[kind - 1].push_back(
+                    QItem{(int32_t)g, kind, q, (int32_t)std::min<int64_t>(per, e - q), 0});
+        }
+    }
+    qp.nitems = (int)hi.size();
+    qp.nlong[0] = (int)hl[0].size();
+    qp.nlong[1] = (int)hl[1].size();
+    qp.groups = DBuf<QGroup>(c, std::max<size_t>(hg.size(), 1));
+    qp.items = DBuf<QItem>(c, std::max<size_t>(hi.size() + hl[0].size() + hl[1].size(), 1));
+    qp.cursor = DBuf<unsigned>(c, 3);
+    if (!hg.empty()) to_device(c, qp.groups.p, hg.data(), hg.size());
+    if (!hi.empty()) to_device(c, qp.items.p, hi.data(), hi.size());
+    if (!hl[0].empty()) to_device(c, qp.items.p + hi.size(), hl[0].data(), hl[0].size());
+    if (!hl[1].empty()) to_device(c, qp.items.p + hi.size() + hl[0].size(), hl[1].data(), hl[1].size());
+    sync(c);
+}
+
+template <class RT>
+void queue_launch_long(const Ctx &c, QueuePlan &qp, StateDev &st, RT *r, RT *acc) {
+    const int64_t base1 = qp.nitems, base2 = qp.nitems + qp.nlong[0];
+    auto go = [&](auto kern, int n, int64_t base, unsigned *cur) {
+        if (n == 0) return;
+        const int grid = (int)std::min<int64_t>(ceil_div(n, FW_THREADS / 32), (int64_t)c.num_sms * 4);
+        kern<<<grid, FW_THREADS, 0, c.stream>>>(qp.groups.p, qp.items.p + base, n, cur, r, acc,
+                                                st.err.p);
+        KDSS_LAUNCH_CHECK();
+    };
+    if (qp.tpp == 8) go(k_pb_queue_long<RT, 8, 32>, qp.nlong[0], base1, qp.cursor.p + 1);
+    else go(k_pb_queue_long<RT, 32, 8>, qp.nlong[0], base1, qp.cursor.p + 1);
+    go(k_pb_queue_long<RT, 32, 32>, qp.nlong[1], base2, qp.cursor.p + 2);
+}
+
+void queue_enqueue(const Ctx &c, QueuePlan &qp, StateDev &st) {
+    if (qp.nitems + qp.nlong[0] + qp.nlong[1] == 0) return;
+    if (st.precision != KDSS_FP64 && st.precision != KDSS_INT64)
+        fail(KDSS_ERR_UNSUPPORTED, "work-queue iterations: integer rule only");
+    KDSS_CUDA(cudaMemsetAsync(qp.cursor.p, 0, 3 * sizeof(unsigned), c.stream));
+    if (st.precision == KDSS_FP64)
+        queue_launch_long<double>(c, qp, st, (double *)st.r.p, (double *)st.acc.p);
+    else
+        queue_launch_long<uint64_t>(c, qp, st, st.r.p, st.acc.p);
+    if (qp.nitems == 0) return;
+    const size_t smem = sizeof(QSmem);
+    static thread_local int attr_dev = -1;
+    if (attr_dev != c.device) {
+        KDSS_CUDA(cudaFuncSetAttribute(k_pb_queue<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_pb_queue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        attr_dev = c.device;
+    }
+    const int grid = (int)std::min<int64_t>(ceil_div(qp.nitems, QW), (int64_t)c.num_sms * 4);
+    if (st.precision == KDSS_FP64)
+        k_pb_queue<double><<<grid, QW * 32, smem, c.stream>>>(qp.groups.p, qp.items.p, qp.nitems,
+                                                             qp.cursor.p, (double *)st.r.p,
+                                                             (double *)st.acc.p, st.err.p);
+    else
+        k_pb_queue<uint64_t><<<grid, QW * 32, smem, c.stream>>>(qp.groups.p, qp.items.p, qp.nitems,
+                                                               qp.cursor.p, st.r.p, st.acc.p,
+                                                               st.err.p);
+    KDSS_LAUNCH_CHECK();
+}
+
+// The step of one iteration over the whole state, advancing its count.
+void fw_step_advance(const Ctx &c, StateDev &st, int64_t n) {
+    fw_enqueue_step_range(c, st, 0, n, true);
+    st.t += 1;
 }
 
 long long fw_capture(const Ctx &c, cudaGraphExec_t *exec, const std::function<void(const Ctx &)> &fn) {

@@ -7,10 +7,43 @@
 
 namespace kdss {
 
+// One SCT of a work-queue iteration (device copy of its arrays' addresses).
+struct QGroup {
+    const int64_t *pair_off;
+    const int32_t *nodes;
+    const uint8_t *h;
+    const uint64_t *binom;
+    int bcols, k;
+    int64_t node_off;     // its slice of the shared state
+    int64_t short_end;    // pairs [0, short_end) have at most 32 nodes
+    int64_t long_begin[2], long_end[2];   // pairs of 33..256 and 257..1024 nodes
+};
+
+// A work item of the queue kernels.
+struct QItem {
+    int32_t g;        // SCT (group) index
+    int32_t kind;     // 0: tiles of short pairs; 1: pairs of 33..256 nodes; 2: 257..1024
+    int64_t first;    // first tile (kind 0) or first pair (kinds 1, 2)
+    int32_t count;    // tiles or pairs
+    int32_t pad;
+};
+// The groups and items of one work-queue PBUpdate pass over several SCTs.
+struct QueuePlan {
+    DBuf<QGroup> groups;
+    DBuf<QItem> items;
+    DBuf<unsigned> cursor;
+    int nitems = 0;    // items of short pairs (first in `items`)
+    int nlong[2] = {0, 0};   // then items of pairs of 33..256 and of 257..1024 nodes
+    int chunk = 4;     // tiles of 32 short pairs per item (8 x chunk longer pairs)
+    int tpp = 32;      // lanes per pair of 33..256 nodes (8 or 32)
+};
+
 struct StateDev {
     int precision = KDSS_INT64;
     int64_t n = 0;
     int t = 0;                       // iterations done
+    int k = 0;                       // the k iterated (P_k of the SCT)
+    uint64_t ck_lo = 0, ck_hi = 0;   // its c_k
     DBuf<uint64_t> r;                // [n] uint64 or double bits (rule I), cumulative
     DBuf<uint64_t> acc;              // [n] per-iteration delta (same type as r)
     DBuf<float> r32;                 // [n] FP32K: normalised r / t
@@ -24,6 +57,8 @@ struct StateDev {
     DBuf<int> dev_t;                 // [0] iterations done (FP32 schedule), [1] scratch
     kdss_timing timing{};
     Ctx ctx;
+    int qchunk = 0, qtpp = 32;       // > 0: integer-rule passes on the work-queue kernels
+    QueuePlan qplan;                 // their plan, bound like the graphs to one SCT
     // one FW iteration as CUDA graphs, bound to the SCT they were captured for
     const SctDev *graph_sct = nullptr;
     cudaGraphExec_t g_iter = nullptr, g_pb = nullptr, g_step = nullptr;
@@ -36,7 +71,11 @@ struct StateDev {
     void release_graphs();
 };
 
-void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st);
+// Entries of the list of pairs the first-step kernels leave to the slow
+// kernels (at most every short pair).
+int64_t slow_list_capacity(int64_t short_pairs, int num_sms);
+// k < 0: the SCT's own k; otherwise iterate P_k of a k-agnostic SCT.
+void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st, int k = -1);
 void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile);
 // in-place (asynchronous) iterations of the integer rule: pairs add into r
 void fw_run_async(const Ctx &c, const SctDev &s, StateDev &st, int T);
@@ -46,6 +85,23 @@ void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, S
 void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off);
 void fw_enqueue_step_range(const Ctx &c, StateDev &st, int64_t node_off, int64_t n, bool advance);
 long long fw_capture(const Ctx &c, cudaGraphExec_t *exec, const std::function<void(const Ctx &)> &fn);
+// Work-queue PBUpdate: one launch over every (SCT, state slice) of `sets`.
+// k >= 0: iterate P_k of every set's SCT at that k (the P_k filter).
+void queue_plan(const Ctx &c, const std::vector<std::pair<const SctDev *, int64_t>> &sets, int chunk,
+                int tpp, QueuePlan &qp, int k = -1);
+void queue_enqueue(const Ctx &c, QueuePlan &qp, StateDev &st);
+// Extraction (A6) in phases, for pairs that come in pieces.
+struct PrefixAcc {
+    int64_t n = 0;
+    bool wide = false;           // 128-bit prefix counts
+    double rmax = 0;             // max_u r(u)/t
+    DBuf<int32_t> order, pos;
+    DBuf<unsigned long long> hist, fhist;
+    DBuf<U128> hist128, fhist128;
+};
+void prefix_begin(const Ctx &c, int64_t n, const StateDev &st, bool wide, PrefixAcc &a);
+void prefix_add(const Ctx &c, const SctDev &s, int k, PrefixAcc &a);
+void prefix_end(const Ctx &c, PrefixAcc &a, const StateDev &st, kdss_result *out);
 void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, int32_t *slow,
                      int *slow_count, int *err, unsigned long long *maxr, int T);
 

@@ -102,6 +102,40 @@ void sync(const Ctx &c);
 void zero(const Ctx &c, void *p, size_t bytes);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Unsigned 128-bit integer for clique counts beyond 64 bits (Lemma 2.6 counts
+// C(p, k - h) of long pairs, c_k and the prefix counts of the extraction).
+// Trivially default-constructible so that it can live in shared memory.
+struct U128 {
+    unsigned long long lo, hi;
+    U128() = default;
+    __host__ __device__ constexpr U128(int v)
+        : lo((unsigned long long)(long long)v), hi(v < 0 ? ~0ull : 0ull) {}
+    __host__ __device__ constexpr U128(unsigned long long l, unsigned long long h) : lo(l), hi(h) {}
+};
+__host__ __device__ inline U128 operator+(U128 a, U128 b) {
+    U128 r(a.lo + b.lo, a.hi + b.hi);
+    if (r.lo < a.lo) ++r.hi;
+    return r;
+}
+__host__ __device__ inline U128 operator-(U128 a, U128 b) {
+    U128 r(a.lo - b.lo, a.hi - b.hi);
+    if (a.lo < b.lo) --r.hi;
+    return r;
+}
+__host__ __device__ inline U128 &operator+=(U128 &a, U128 b) { a = a + b; return a; }
+__host__ __device__ inline bool operator==(U128 a, U128 b) { return a.lo == b.lo && a.hi == b.hi; }
+__host__ __device__ inline bool operator!=(U128 a, U128 b) { return !(a == b); }
+// marker of a binomial that needs more than 128 bits
+constexpr U128 U128_OVF(~0ull, ~0ull);
+inline int bit_length_u128(U128 x) {
+    int b = 0;
+    unsigned long long h = x.hi, l = x.lo;
+    if (h) { b = 64; l = h; }
+    while (l) { ++b; l >>= 1; }
+    return b;
+}
+inline double u128_to_double(U128 x) { return (double)x.hi * 18446744073709551616.0 + (double)x.lo; }
 inline int bit_length(uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return b; }
 
 // Grid size for a grid-stride kernel: a multiple of the SM count.
@@ -115,6 +149,7 @@ int64_t exclusive_scan_i64(const Ctx &c, const int64_t *in, int64_t *out, int64_
 // In-place variant that does not read the total back (stream-ordered).
 void exclusive_scan_i64_async(const Ctx &c, const int64_t *in, int64_t *out, int64_t n);
 void inclusive_scan_u64_async(const Ctx &c, const uint64_t *in, uint64_t *out, int64_t n);
+void inclusive_scan_u128_async(const Ctx &c, const U128 *in, U128 *out, int64_t n);
 
 // Stable LSD radix sort of 64-bit keys (with optional int32 payload) on the
 // digit positions that cover bits [lo, hi) of each range in `ranges`.

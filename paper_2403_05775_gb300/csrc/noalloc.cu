@@ -121,9 +121,12 @@ extern "C" kdss_status kdss_fw_iterate_noalloc(const kdss_sct *s, uint64_t *r, i
             fail(KDSS_ERR_OVERFLOW, "(t_done + T) * c_k leaves the exact range of r");
         // scratch layout: counters | delta [n] | slow-pair list [short pairs]
         const int64_t short_pairs = sd.class_begin[3] - sd.class_begin[0];
+        int num_sms = 0;
+        KDSS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
         const size_t off_acc = 256;
         const size_t off_slow = off_acc + round_up((size_t)sd.n * sizeof(uint64_t));
-        const size_t need = off_slow + round_up((size_t)short_pairs * sizeof(int32_t));
+        const size_t need =
+            off_slow + round_up((size_t)slow_list_capacity(short_pairs, num_sms) * sizeof(int32_t));
         if (need > NOALLOC_SCRATCH_BYTES) {
             char buf[256];
             snprintf(buf, sizeof buf,
@@ -135,7 +138,7 @@ extern "C" kdss_status kdss_fw_iterate_noalloc(const kdss_sct *s, uint64_t *r, i
         Ctx c;
         c.stream = static_cast<cudaStream_t>(stream);
         c.device = dev;
-        KDSS_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        c.num_sms = num_sms;
         unsigned char *base = static_cast<unsigned char *>(scratch_address(dev));
         int *slow_count = reinterpret_cast<int *>(base);
         int *err = reinterpret_cast<int *>(base + 4);

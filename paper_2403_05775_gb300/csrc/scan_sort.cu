@@ -11,11 +11,18 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 template <class T>
+__device__ __forceinline__ T shfl_up_any(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+template <>
+__device__ __forceinline__ U128 shfl_up_any<U128>(U128 v, int o) {
+    return U128(__shfl_up_sync(0xffffffffu, v.lo, o), __shfl_up_sync(0xffffffffu, v.hi, o));
+}
+
+template <class T>
 __device__ __forceinline__ T warp_inclusive(T v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        T t = __shfl_up_sync(0xffffffffu, v, o);
+        T t = shfl_up_any(v, o);
         if (lane >= o) v += t;
     }
     return v;
@@ -212,6 +219,10 @@ void exclusive_scan_i64_async(const Ctx &c, const int64_t *in, int64_t *out, int
 
 void inclusive_scan_u64_async(const Ctx &c, const uint64_t *in, uint64_t *out, int64_t n) {
     scan_impl<uint64_t, true>(c, in, out, n);
+}
+
+void inclusive_scan_u128_async(const Ctx &c, const U128 *in, U128 *out, int64_t n) {
+    scan_impl<U128, true>(c, in, out, n);
 }
 
 void radix_sort_u64(const Ctx &c, uint64_t *keys, int32_t *vals, int64_t n,

@@ -21,30 +21,59 @@
 // every (length class, root) slot, an exclusive scan turns the counts into
 // offsets, and an emit pass re-runs the same recursion and writes the pairs.
 #include <algorithm>
+#include <cmath>
 
 #include "sct.cuh"
 
 namespace kdss {
 
-std::vector<uint64_t> host_binom_table(int rows, int k) {
+namespace {
+// Correctly rounded (to nearest, ties to even) float of a 128-bit integer.
+float u128_to_float(U128 x) {
+    if (x.hi == 0 && x.lo < (1ull << 24)) return (float)x.lo;
+    const int nb = bit_length_u128(x);          // > 24
+    const int sh = nb - 24;                      // bits dropped
+    auto bit = [&](int i) -> unsigned { return i >= 64 ? (unsigned)((x.hi >> (i - 64)) & 1ull)
+                                                       : (unsigned)((x.lo >> i) & 1ull); };
+    unsigned long long m = 0;
+    for (int i = nb - 1; i >= sh; --i) m = (m << 1) | bit(i);
+    const unsigned half = bit(sh - 1);
+    bool sticky = false;
+    for (int i = sh - 2; i >= 0 && !sticky; --i) sticky = bit(i) != 0;
+    if (half && (sticky || (m & 1ull))) ++m;     // may carry into bit 24
+    return ldexpf((float)m, sh);                 // exact: m < 2^25
+}
+}  // namespace
+
+BinomTables host_binom_tables(int rows, int k) {
     const int cols = k + 1;
-    std::vector<uint64_t> t((size_t)rows * cols, 0);
-    const uint64_t LIM = 1ull << 63;
+    BinomTables t;
+    t.t128.assign((size_t)rows * cols, U128(0));
+    t.t64.assign((size_t)rows * cols, 0);
+    t.tf.assign((size_t)rows * cols, 0.f);
     for (int a = 0; a < rows; ++a) {
         for (int b = 0; b <= k; ++b) {
-            uint64_t v;
-            if (b > a) v = 0;
-            else if (b == 0 || b == a) v = 1;
+            U128 v(0);
+            if (b > a) v = U128(0);
+            else if (b == 0 || b == a) v = U128(1);
             else {
-                uint64_t x = t[(size_t)(a - 1) * cols + b - 1], y = t[(size_t)(a - 1) * cols + b];
-                if (x == ~0ull || y == ~0ull || x >= LIM - y) v = ~0ull;
-                else v = x + y;
+                const U128 x = t.t128[(size_t)(a - 1) * cols + b - 1], y = t.t128[(size_t)(a - 1) * cols + b];
+                if (x == U128_OVF || y == U128_OVF) v = U128_OVF;
+                else {
+                    v = x + y;
+                    if (v.hi < x.hi || (v.hi == x.hi && v.lo < x.lo) || v == U128_OVF) v = U128_OVF;
+                }
             }
-            t[(size_t)a * cols + b] = v;
+            const size_t i = (size_t)a * cols + b;
+            t.t128[i] = v;
+            t.t64[i] = (v.hi == 0 && v.lo < (1ull << 63)) ? v.lo : ~0ull;
+            t.tf[i] = v == U128_OVF ? INFINITY : u128_to_float(v);
         }
     }
     return t;
 }
+
+std::vector<uint64_t> host_binom_table(int rows, int k) { return host_binom_tables(rows, k).t64; }
 
 namespace {
 
@@ -67,12 +96,24 @@ __device__ __forceinline__ int dev_class(int len) {
 // Record of a spawned item (uint32 words): root, |hold|, hold[0..k) (local
 // indices; the root is -1), candidate bitset [S], pivot bitset [S].
 constexpr int SPLIT_MIN = 16;
-enum { MODE_COUNT = 0, MODE_SPAWN = 1, MODE_EMIT = 2 };
+enum { MODE_COUNT = 0, MODE_SPAWN = 1, MODE_EMIT = 2, MODE_TOTAL = 3 };
+
+// Totals of a count-only pass (MODE_TOTAL): roots in a pseudo-random order,
+// each walked to the end by one warp (no spawned items, nothing stored), until
+// a deadline.  Class NCLASS counts pairs longer than the FW kernels take.
+struct CountTotals {
+    unsigned long long pairs[NCLASS + 1], nodes[NCLASS + 1];  // roots walked to the end
+    unsigned long long ck[2];                                   // their c_k (lo, hi)
+    unsigned long long roots_done, roots_cut;                   // finished / cut by the deadline
+    unsigned long long cut_pairs, cut_nodes;                    // pairs seen in the cut roots
+    int maxlen, cbits;
+};
 
 struct ItemsIn {
     int64_t nitems;
-    const uint32_t *rec;     // nullptr: the items are the roots 0..n-1
+    const uint32_t *rec;     // nullptr: the items are the roots root_base + 0..nitems-1
     int stride;              // words per record
+    int64_t root_base = 0;
 };
 struct PassOut {
     int64_t *cntP;           // [NCLASS * nitems] class-major (COUNT)
@@ -86,6 +127,7 @@ struct PassOut {
     unsigned long long node_budget;  // more than this: stop counting (COUNT)
     int *stop;                       // set once the budget is exceeded (COUNT)
     int *maxlen;             // (COUNT)
+    int *cbits;              // bit length of the largest n_C (COUNT)
     const int64_t *spawn_off;  // [nitems] (SPAWN)
     uint32_t *spawn_rec;       // (SPAWN)
     const int64_t *baseP;    // [NCLASS * nitems] output offsets (EMIT)
@@ -93,14 +135,20 @@ struct PassOut {
     int64_t *pair_off;
     int32_t *nodes;
     uint8_t *h;
+    CountTotals *tot;                // (TOTAL)
+    unsigned long long perm_mul;     // root of item i: (i * perm_mul) mod n (TOTAL)
+    unsigned long long budget_ns;    // each warp stops this long after it started (TOTAL)
 };
 
-template <int MODE>
+// WPL: candidate-bitset words per lane (a root's out-degree is at most
+// 1024 * WPL - 1); word wi of a bitset belongs to lane wi % 32.
+template <int MODE, int WPL>
 __global__ void __launch_bounds__(SCT_THREADS)
 k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_adj,
       const int32_t *__restrict__ vert, int k, int klo, int dmax, int S,
-      const uint64_t *__restrict__ binom, int bcols, uint32_t *gws, int use_shared,
-      unsigned long long *next_item, ItemsIn items, PassOut po, int *err) {
+      const uint64_t *__restrict__ binom, const U128 *__restrict__ binom128, int bcols,
+      uint32_t *gws, int use_shared, unsigned long long *next_item, ItemsIn items, PassOut po,
+      int *err) {
     extern __shared__ uint32_t smem[];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -120,22 +168,31 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
     int32_t *fph = fnp + F;
     int32_t *ids = fph + F;
     const int64_t NI = items.nitems;
+    const uint64_t t_start = MODE == MODE_TOTAL ? globaltimer_ns() : 0ull;
 
     while (true) {
         unsigned long long rr = 0;
         if (lane == 0) {
-            // a count pass over budget stops handing out items
+            // a count pass over budget stops handing out items, and so does a
+            // count-only pass past its deadline
             if (MODE == MODE_COUNT && *(volatile int *)po.stop) rr = ~0ull;
+            else if (MODE == MODE_TOTAL && globaltimer_ns() - t_start > po.budget_ns) rr = ~0ull;
             else rr = atomicAdd(next_item, 1ull);
         }
         rr = __shfl_sync(FULL, rr, 0);
         if (rr >= (unsigned long long)NI) break;
         const int64_t item = (int64_t)rr;
         const uint32_t *rec = items.rec ? items.rec + (size_t)item * items.stride : nullptr;
-        const int64_t root = rec ? (int64_t)rec[0] : item;
+        const int64_t root = rec ? (int64_t)rec[0]
+                                 : (MODE == MODE_TOTAL ? (int64_t)(((unsigned long long)item * po.perm_mul) %
+                                                                   (unsigned long long)n)
+                                                       : items.root_base + item);
         const int64_t o0 = out_off[root];
         const int d = (int)(out_off[root + 1] - o0);
-        if (!rec && d + 1 < klo) continue;
+        if (!rec && d + 1 < klo) {   // no pair of this root has k nodes
+            if (MODE == MODE_TOTAL && lane == 0) atomicAdd(&po.tot->roots_done, 1ull);
+            continue;
+        }
         const int W = (d + 31) >> 5;
 
         // local vertex list and its adjacency bitsets
@@ -162,29 +219,38 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
             }
         }
         // per-item outputs (lane 0)
-        int64_t cP[NCLASS], cN[NCLASS];
+        int64_t cP[NCLASS + 1], cN[NCLASS + 1];
 #pragma unroll
-        for (int c = 0; c < NCLASS; ++c) {
-            cP[c] = MODE == MODE_EMIT ? po.baseP[(int64_t)c * NI + item] : 0;
-            cN[c] = MODE == MODE_EMIT ? po.baseN[(int64_t)c * NI + item] : 0;
+        for (int c = 0; c < NCLASS + 1; ++c) {
+            cP[c] = (MODE == MODE_EMIT && c < NCLASS) ? po.baseP[(int64_t)c * NI + item] : 0;
+            cN[c] = (MODE == MODE_EMIT && c < NCLASS) ? po.baseN[(int64_t)c * NI + item] : 0;
         }
+        bool cut = false;            // TOTAL: the deadline stopped this root's walk
+        unsigned steps = 0;
         int64_t nsp = MODE == MODE_SPAWN ? po.spawn_off[item] : 0;
         unsigned long long ck_lo = 0, ck_hi = 0;
         unsigned long long pend = 0;  // node entries not yet added to nodes_seen
         int mlen = 0;
+        int cbits = 0;                // bit length of the largest n_C counted
 
         // initial frame: the root, or the spawned recursion node
         if (!rec) {
-            if (lane < W) {
-                int rem = d - lane * 32;
-                cand[lane] = rem >= 32 ? FULL : ((1u << rem) - 1u);
+#pragma unroll
+            for (int u = 0; u < WPL; ++u) {
+                const int wi = lane + 32 * u;
+                if (wi < W) {
+                    const int rem = d - wi * 32;
+                    cand[wi] = rem >= 32 ? FULL : ((1u << rem) - 1u);
+                }
             }
             if (lane == 0) { fnh[0] = 1; fnp[0] = 0; fph[0] = 0; hold[0] = -1; }
         } else {
             const int nh0 = (int)rec[1];
             const uint32_t *rc = rec + 2 + k;
             const uint32_t *rp = rc + S;
-            if (lane < W) cand[lane] = rc[lane];
+#pragma unroll
+            for (int u = 0; u < WPL; ++u)
+                if (lane + 32 * u < W) cand[lane + 32 * u] = rc[lane + 32 * u];
             if (lane == 0) {
                 for (int t = 0; t < nh0; ++t) hold[t] = (int32_t)rec[2 + t];
                 int np0 = 0;
@@ -198,12 +264,23 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
         __syncwarp();
         int depth = 0;
         while (depth >= 0) {
+            if (MODE == MODE_TOTAL && ((++steps) & 4095u) == 0u) {
+                int late = 0;
+                if (lane == 0) late = globaltimer_ns() - t_start > po.budget_ns ? 1 : 0;
+                if (__shfl_sync(FULL, late, 0)) { cut = true; break; }
+            }
             uint32_t *cd = cand + (size_t)depth * S;
             uint32_t *td = todo + (size_t)depth * S;
             const int h = fnh[depth], p = fnp[depth];
             if (fph[depth] == 0) {
-                const uint32_t cw = lane < W ? cd[lane] : 0u;
-                const int nc = (int)__reduce_add_sync(FULL, (unsigned)__popc(cw));
+                uint32_t cw[WPL];
+                unsigned pc = 0;
+#pragma unroll
+                for (int u = 0; u < WPL; ++u) {
+                    cw[u] = lane + 32 * u < W ? cd[lane + 32 * u] : 0u;
+                    pc += (unsigned)__popc(cw[u]);
+                }
+                const int nc = (int)__reduce_add_sync(FULL, pc);
                 if (h > k || h + p + nc < klo) { --depth; continue; }
                 if (nc == 0) {
                     if (h <= k && klo <= h + p) {
@@ -211,17 +288,40 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                         const int cls = dev_class(len);
                         // c_k of the hold cap k; a k-agnostic build (klo < k) keeps
                         // pairs with fewer than k nodes and ignores the count's range
-                        const uint64_t nC = p >= k - h ? binom[(size_t)p * bcols + (k - h)] : 0ull;
-                        if (cls < 0 || (klo == k && nC == ~0ull)) {
+                        const U128 nC = p >= k - h ? binom128[(size_t)p * bcols + (k - h)] : U128(0);
+                        const bool ovf = nC == U128_OVF;
+                        if (MODE == MODE_TOTAL) {
+                            if (lane == 0) {
+                                const int c6 = cls < 0 ? NCLASS : cls;
+                                cP[c6] += 1;
+                                cN[c6] += len;
+                                mlen = len > mlen ? len : mlen;
+                                if (ovf) {
+                                    cbits = 129;
+                                } else {
+                                    unsigned long long o = ck_lo;
+                                    ck_lo += nC.lo;
+                                    ck_hi += nC.hi + (ck_lo < o ? 1ull : 0ull);
+                                    const int nb = nC.hi ? 128 - __clzll((long long)nC.hi)
+                                                         : 64 - __clzll((long long)nC.lo);
+                                    cbits = nb > cbits ? nb : cbits;
+                                }
+                            }
+                        } else if (cls < 0 || (klo == k && ovf)) {
                             if (lane == 0) atomicOr(err, cls < 0 ? DERR_CAPACITY : DERR_OVERFLOW);
                         } else if (MODE == MODE_COUNT) {
                             int over = 0;
                             if (lane == 0) {
                                 cP[cls] += 1;
                                 cN[cls] += len;
-                                unsigned long long o = ck_lo;
-                                ck_lo += nC;
-                                ck_hi += ck_lo < o ? 1ull : 0ull;
+                                if (!ovf) {
+                                    unsigned long long o = ck_lo;
+                                    ck_lo += nC.lo;
+                                    ck_hi += nC.hi + (ck_lo < o ? 1ull : 0ull);
+                                    const int nb = nC.hi ? 128 - __clzll((long long)nC.hi)
+                                                         : 64 - __clzll((long long)nC.lo);
+                                    cbits = nb > cbits ? nb : cbits;
+                                }
                                 mlen = len > mlen ? len : mlen;
                                 // report progress against the memory budget
                                 // every 2^16 node entries, and stop once over
@@ -295,12 +395,16 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                     break;
                 }
                 const uint32_t *ax = A + (size_t)bx * S;
-                if (lane < W) {
-                    uint32_t tw = cw & ~ax[lane];
-                    if (lane == (bx >> 5)) tw &= ~(1u << (bx & 31));
-                    if (h >= k) tw = 0u;  // hold branches would exceed k
-                    td[lane] = tw;
-                    cand[(size_t)(depth + 1) * S + lane] = cw & ax[lane];
+#pragma unroll
+                for (int u = 0; u < WPL; ++u) {
+                    const int wi = lane + 32 * u;
+                    if (wi < W) {
+                        uint32_t tw = cw[u] & ~ax[wi];
+                        if (wi == (bx >> 5)) tw &= ~(1u << (bx & 31));
+                        if (h >= k) tw = 0u;  // hold branches would exceed k
+                        td[wi] = tw;
+                        cand[(size_t)(depth + 1) * S + wi] = cw[u] & ax[wi];
+                    }
                 }
                 if (lane == 0) {
                     fph[depth] = 1;
@@ -312,29 +416,47 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 __syncwarp();
                 ++depth;
             } else {
-                const uint32_t tw = lane < W ? td[lane] : 0u;
-                const unsigned any = __ballot_sync(FULL, tw != 0u);
-                if (!any) { --depth; continue; }
-                const int src = __ffs(any) - 1;
-                const uint32_t word = __shfl_sync(FULL, tw, src);
-                const int w = src * 32 + __ffs(word) - 1;
+                // the first non-empty to-do word (lowest index)
+                uint32_t tw[WPL];
+                unsigned first = 0xffffffffu;
+#pragma unroll
+                for (int u = WPL - 1; u >= 0; --u) {
+                    const int wi = lane + 32 * u;
+                    tw[u] = wi < W ? td[wi] : 0u;
+                    if (tw[u]) first = (unsigned)wi;
+                }
+                const unsigned src = __reduce_min_sync(FULL, first);
+                if (src == 0xffffffffu) { --depth; continue; }
+                uint32_t mine = tw[0];
+#pragma unroll
+                for (int u = 1; u < WPL; ++u)
+                    if ((int)(src >> 5) == u) mine = tw[u];
+                const uint32_t word = __shfl_sync(FULL, mine, src & 31);
+                const int w = (int)src * 32 + __ffs(word) - 1;
                 if (depth + 1 >= F) {
                     if (lane == 0) atomicOr(err, DERR_LOGIC);
                     break;
                 }
                 const uint32_t *aw = A + (size_t)w * S;
-                uint32_t child = 0u;
-                if (lane < W) {
-                    const uint32_t cw = cd[lane];
-                    child = cw & aw[lane];
-                    if (lane == src) {
-                        td[lane] = tw & ~(1u << (w & 31));
-                        cd[lane] = cw & ~(1u << (w & 31));
+                uint32_t child[WPL];
+                unsigned pcc = 0;
+#pragma unroll
+                for (int u = 0; u < WPL; ++u) {
+                    const int wi = lane + 32 * u;
+                    child[u] = 0u;
+                    if (wi < W) {
+                        const uint32_t c0 = cd[wi];
+                        child[u] = c0 & aw[wi];
+                        if (wi == (int)src) {
+                            td[wi] = tw[u] & ~(1u << (w & 31));
+                            cd[wi] = c0 & ~(1u << (w & 31));
+                        }
                     }
+                    pcc += (unsigned)__popc(child[u]);
                 }
-                const int ncc = (int)__reduce_add_sync(FULL, (unsigned)__popc(child));
+                const int ncc = (int)__reduce_add_sync(FULL, pcc);
                 // big hold branch: becomes an item of the next level
-                if (h + 1 < k && ncc >= SPLIT_MIN && h + 1 + p + ncc >= klo) {
+                if (MODE != MODE_TOTAL && h + 1 < k && ncc >= SPLIT_MIN && h + 1 + p + ncc >= klo) {
                     // the count pass also writes the record, at a slot taken
                     // from a cursor, while the slots last; if they run out,
                     // a spawn pass writes every record in item order
@@ -357,18 +479,24 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                             r2[2 + h] = (uint32_t)w;
                             for (int t = h + 1; t < k; ++t) r2[2 + t] = 0u;
                         }
-                        if (lane < S) {
-                            r2[2 + k + lane] = lane < W ? child : 0u;
-                            uint32_t pw = 0u;
-                            for (int t = 0; t < p; ++t)
-                                if ((piv[t] >> 5) == lane) pw |= 1u << (piv[t] & 31);
-                            r2[2 + k + S + lane] = pw;
+#pragma unroll
+                        for (int u = 0; u < WPL; ++u) {
+                            const int wi = lane + 32 * u;
+                            if (wi < S) {
+                                r2[2 + k + wi] = wi < W ? child[u] : 0u;
+                                uint32_t pw = 0u;
+                                for (int t = 0; t < p; ++t)
+                                    if ((piv[t] >> 5) == wi) pw |= 1u << (piv[t] & 31);
+                                r2[2 + k + S + wi] = pw;
+                            }
                         }
                     }
                     __syncwarp();
                     continue;  // stay at this depth: next hold branch
                 }
-                if (lane < W) cand[(size_t)(depth + 1) * S + lane] = child;
+#pragma unroll
+                for (int u = 0; u < WPL; ++u)
+                    if (lane + 32 * u < W) cand[(size_t)(depth + 1) * S + lane + 32 * u] = child[u];
                 if (lane == 0) {
                     hold[h] = w;
                     fnh[depth + 1] = h + 1;
@@ -377,6 +505,31 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 }
                 __syncwarp();
                 ++depth;
+            }
+        }
+        if (MODE == MODE_TOTAL && lane == 0) {
+            CountTotals *T = po.tot;
+            if (!cut) {
+#pragma unroll
+                for (int c = 0; c < NCLASS + 1; ++c) {
+                    if (cP[c]) atomicAdd(&T->pairs[c], (unsigned long long)cP[c]);
+                    if (cN[c]) atomicAdd(&T->nodes[c], (unsigned long long)cN[c]);
+                }
+                if (ck_lo || ck_hi) {
+                    unsigned long long old = atomicAdd(&T->ck[0], ck_lo);
+                    unsigned long long carry = (old + ck_lo < old) ? 1ull : 0ull;
+                    if (ck_hi + carry) atomicAdd(&T->ck[1], ck_hi + carry);
+                }
+                atomicAdd(&T->roots_done, 1ull);
+                atomicMax(&T->maxlen, mlen);
+                atomicMax(&T->cbits, cbits);
+            } else {
+                unsigned long long pp = 0, nn = 0;
+#pragma unroll
+                for (int c = 0; c < NCLASS + 1; ++c) { pp += cP[c]; nn += cN[c]; }
+                atomicAdd(&T->cut_pairs, pp);
+                atomicAdd(&T->cut_nodes, nn);
+                atomicAdd(&T->roots_cut, 1ull);
             }
         }
         if (MODE == MODE_COUNT && lane == 0) {
@@ -397,6 +550,7 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                 if (ck_hi + carry) atomicAdd(&po.ck[1], ck_hi + carry);
             }
             atomicMax(po.maxlen, mlen);
+            atomicMax(po.cbits, cbits);
         }
         __syncwarp();
     }
@@ -451,40 +605,60 @@ __global__ void k_pair_copy(int64_t np, const uint64_t *keys, const int64_t *off
     }
 }
 
-__global__ void k_pair_ck(int64_t np, const int64_t *off, const uint8_t *h, const uint64_t *binom,
-                          int bcols, int k, unsigned long long *ck, int *maxlen, int *err) {
+__global__ void k_pair_ck(int64_t np, const int64_t *off, const uint8_t *h, const U128 *binom128,
+                          int bcols, int k, unsigned long long *ck, int *maxlen, int *cbits,
+                          int *err) {
     unsigned long long lo = 0, hi = 0;
-    int ml = 0;
+    int ml = 0, mb = 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
          q += (int64_t)gridDim.x * blockDim.x) {
         int len = (int)(off[q + 1] - off[q]);
         int hq = h[q], p = len - hq;
-        uint64_t nC = binom[(size_t)p * bcols + (k - hq)];
-        if (nC == ~0ull) atomicOr(err, DERR_OVERFLOW);
+        if (hq > k || len < k) continue;   // not in P_k (a k-agnostic SCT counted at k)
+        const U128 nC = binom128[(size_t)p * bcols + (k - hq)];
+        if (nC == U128_OVF) { atomicOr(err, DERR_OVERFLOW); continue; }
         unsigned long long o = lo;
-        lo += nC;
-        hi += lo < o ? 1ull : 0ull;
+        lo += nC.lo;
+        hi += nC.hi + (lo < o ? 1ull : 0ull);
+        const int nb = nC.hi ? 128 - __clzll((long long)nC.hi) : 64 - __clzll((long long)nC.lo);
+        mb = nb > mb ? nb : mb;
         ml = len > ml ? len : ml;
     }
     unsigned long long old = atomicAdd(&ck[0], lo);
     unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
     if (hi + carry) atomicAdd(&ck[1], hi + carry);
     atomicMax(maxlen, ml);
+    atomicMax(cbits, mb);
 }
 
 void upload_binom(const Ctx &c, int rows, int k, SctDev &out) {
-    std::vector<uint64_t> t = host_binom_table(rows, k);
-    out.binom = DBuf<uint64_t>(c, t.size());
-    to_device(c, out.binom.p, t.data(), t.size());
+    BinomTables t = host_binom_tables(rows, k);
+    out.binom = DBuf<uint64_t>(c, t.t64.size());
+    out.binom128 = DBuf<U128>(c, t.t128.size());
+    out.binomf = DBuf<float>(c, t.tf.size());
+    to_device(c, out.binom.p, t.t64.data(), t.t64.size());
+    to_device(c, out.binom128.p, t.t128.data(), t.t128.size());
+    to_device(c, out.binomf.p, t.tf.data(), t.tf.size());
     out.binom_rows = rows;
-    sync(c);  // the host table goes out of scope
+    sync(c);  // the host tables go out of scope
+}
+
+// c_k is a sum of eta counts below 2^cbits each: it fits 128 bits when
+// cbits + bit_length(eta) <= 128.
+void check_ck_range(int cbits, int64_t npairs) {
+    if (cbits + bit_length((uint64_t)std::max<int64_t>(npairs, 1)) > 128)
+        fail(KDSS_ERR_OVERFLOW, "c_k could need more than 128 bits");
 }
 
 }  // namespace
 
-void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
+void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo, int64_t root_lo,
+               int64_t root_hi) {
     if (klo < 0) klo = k;
     const int64_t n = g.n;
+    if (root_hi < 0) root_hi = n;
+    root_lo = std::max<int64_t>(0, std::min<int64_t>(root_lo, n));
+    root_hi = std::max<int64_t>(root_lo, std::min<int64_t>(root_hi, n));
     out.k = k;
     out.n = n;
     const int dmax = std::max(1, g.max_out);
@@ -506,11 +680,11 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
     int grid;
     DBuf<uint32_t> gws;
     if (use_shared) {
-        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_SPAWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_COUNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_SPAWN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_EMIT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sct<MODE_COUNT>, SCT_THREADS, smem));
+        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sct<MODE_COUNT, 1>, SCT_THREADS, smem));
         grid = c.num_sms * std::max(1, per_sm);
     } else {
         // global workspace: bound its size to about 1 GiB
@@ -522,9 +696,9 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
     const size_t dyn = use_shared ? smem : 0;
 
     DBuf<unsigned long long> ctr(c, 4);  // [0] next item, [1..2] c_k, [3] node entries seen
-    DBuf<int> ints(c, 3);                // [0] max len, [1] error, [2] over budget
+    DBuf<int> ints(c, 4);                // [0] max len, [1] error, [2] over budget, [3] n_C bits
     zero(c, ctr.p, 4 * sizeof(unsigned long long));
-    zero(c, ints.p, 3 * sizeof(int));
+    zero(c, ints.p, 4 * sizeof(int));
     // The SCT must fit the device: about 4.5 bytes per node entry (4 for the
     // id, the offset and h of pairs of ~20 nodes), within 85% of the free
     // memory at the start of the build.  The count pass stops once it has
@@ -542,17 +716,17 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
     auto launch = [&](auto kern, const Level &L, const PassOut &po) {
         zero(c, ctr.p, sizeof(unsigned long long));
         int gsz = (int)std::min<int64_t>(grid, std::max<int64_t>(1, ceil_div(L.nitems, SCT_WARPS)));
-        ItemsIn in{L.nitems, L.rec.p, stride};
+        ItemsIn in{L.nitems, L.rec.p, stride, L.rec.p ? 0 : root_lo};
         kern<<<gsz, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k, klo, dmax,
-                                                 S, out.binom.p, bcols, gws.p, use_shared,
-                                                 ctr.p, in, po, ints.p + 1);
+                                                 S, out.binom.p, out.binom128.p, bcols, gws.p,
+                                                 use_shared, ctr.p, in, po, ints.p + 1);
         KDSS_LAUNCH_CHECK();
     };
     // count and spawn, level by level; a spawned item has a larger hold set,
     // so there are at most k levels
     levels.reserve((size_t)k + 2);
     levels.emplace_back();
-    levels[0].nitems = n;
+    levels[0].nitems = root_hi - root_lo;
     for (size_t lv = 0; lv < levels.size(); ++lv) {
         if (lv > (size_t)k) fail(KDSS_ERR_CUDA, "SCT build: more item levels than k");
         Level &L = levels[lv];
@@ -572,10 +746,10 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
         zero(c, dcur.p, sizeof(unsigned long long));
         PassOut po{};
         po.cntP = L.cntP.p; po.cntN = L.cntN.p; po.nspawn = nspawn.p;
-        po.ck = ctr.p + 1; po.maxlen = ints.p;
+        po.ck = ctr.p + 1; po.maxlen = ints.p; po.cbits = ints.p + 3;
         po.nodes_seen = ctr.p + 3; po.node_budget = node_budget; po.stop = ints.p + 2;
         po.direct_rec = direct.p; po.direct_cursor = dcur.p; po.direct_cap = dcap;
-        launch(k_sct<MODE_COUNT>, L, po);
+        launch(k_sct<MODE_COUNT, 1>, L, po);
         {
             int over = 0;
             to_host(c, &over, ints.p + 2, 1);
@@ -603,7 +777,7 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
             PassOut ps{};
             ps.spawn_off = spoff.p;
             ps.spawn_rec = rec.p;
-            launch(k_sct<MODE_SPAWN>, L, ps);
+            launch(k_sct<MODE_SPAWN, 1>, L, ps);
         }
         levels.emplace_back();  // no reference into `levels` is used after this
         levels.back().nitems = ns;
@@ -635,12 +809,13 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
     const int64_t npairs = exclusive_scan_i64(c, allP.p, baseP.p, NCLASS * total);
     const int64_t nnodes = exclusive_scan_i64(c, allN.p, baseN.p, NCLASS * total);
     unsigned long long hc[4];
-    int hi[2];
+    int hi[4];
     to_host(c, hc, ctr.p, 4);
-    to_host(c, hi, ints.p, 2);
-    if (hi[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs 63 bits or more");
+    to_host(c, hi, ints.p, 4);
+    if (hi[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs more than 128 bits");
     if (hi[1] & DERR_CAPACITY) fail(KDSS_ERR_UNSUPPORTED, "a pair longer than 1024 nodes");
     if (hi[1]) fail(KDSS_ERR_CUDA, "SCT build: inconsistent device state");
+    if (klo == k) check_ck_range(hi[3], npairs);
     out.ck_lo = hc[1];
     out.ck_hi = hc[2];
     out.max_len = hi[0];
@@ -655,7 +830,7 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
     allP.reset();
     allN.reset();
     out.pair_off = DBuf<int64_t>(c, (size_t)(npairs + 1));
-    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1));
+    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1) + NODES_PAD);
     out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(npairs, 1));
     if (npairs > 0) {
         // per-level slices of the class-major offsets
@@ -672,13 +847,128 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo) {
             PassOut pe{};
             pe.baseP = lp.p; pe.baseN = ln.p;
             pe.pair_off = out.pair_off.p; pe.nodes = out.nodes.p; pe.h = out.h.p;
-            launch(k_sct<MODE_EMIT>, L, pe);
+            launch(k_sct<MODE_EMIT, 1>, L, pe);
             b += L.nitems;
         }
     }
     to_device(c, out.pair_off.p + npairs, &nnodes, 1);
     to_host(c, hi, ints.p, 2);
     if (hi[1]) fail(KDSS_ERR_CUDA, "SCT emit: inconsistent device state");
+}
+
+// Count-only pass: every root's recursion walked by one warp, nothing
+// stored, so the sizes of an SCT far beyond the device can be measured.
+// Roots are taken in the order i -> (i * P) mod n for a prime P that does
+// not divide n (a permutation), so the roots finished before the deadline
+// are a pseudo-random sample of all roots.
+void sct_ck_at(const Ctx &c, const SctDev &s, int k, uint64_t &lo, uint64_t &hi) {
+    if (k < 2 || k > s.k) fail(KDSS_ERR_INVALID_ARG, "k outside the range the SCT holds");
+    const int B = 256;
+    DBuf<unsigned long long> ck(c, 2);
+    DBuf<int> ml(c, 3);
+    zero(c, ck.p, 2 * sizeof(unsigned long long));
+    zero(c, ml.p, 3 * sizeof(int));
+    if (s.npairs > 0) {
+        k_pair_ck<<<grid_for(c, s.npairs, B), B, 0, c.stream>>>(s.npairs, s.pair_off.p, s.h.p,
+                                                               s.binom128.p, s.bcols(), k, ck.p,
+                                                               ml.p, ml.p + 2, ml.p + 1);
+        KDSS_LAUNCH_CHECK();
+    }
+    unsigned long long hc[2];
+    int hm[3];
+    to_host(c, hc, ck.p, 2);
+    to_host(c, hm, ml.p, 3);
+    if (hm[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs more than 128 bits");
+    check_ck_range(hm[2], s.npairs);
+    lo = hc[0];
+    hi = hc[1];
+}
+
+void count_sct(const Ctx &c, const GraphDev &g, int k, double budget_s, SctCount &out) {
+    const int64_t n = g.n;
+    out = SctCount{};
+    out.roots_total = n;
+    const int dmax = std::max(1, g.max_out);
+    if (dmax > COUNT_MAX_OUT) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "count-only pass: out-degree %d above %d", g.max_out, COUNT_MAX_OUT);
+        fail(KDSS_ERR_UNSUPPORTED, buf);
+    }
+    if (n == 0) { out.complete = 1; return; }
+    const int S = (dmax + 31) / 32;
+    SctDev tab;
+    upload_binom(c, dmax + 2, k, tab);
+    const size_t ww = ws_words(dmax, S);
+    const size_t smem = ww * sizeof(uint32_t) * SCT_WARPS;
+    const int use_shared = smem <= 96 * 1024 ? 1 : 0;
+    int grid;
+    DBuf<uint32_t> gws;
+    if (use_shared) {
+        KDSS_CUDA(cudaFuncSetAttribute(k_sct<MODE_TOTAL, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sct<MODE_TOTAL, 4>, SCT_THREADS, smem));
+        grid = c.num_sms * std::max(1, per_sm);
+    } else {
+        // global workspace: a quarter of the free memory, at most 4 GiB
+        size_t free_b = 0, total_b = 0;
+        KDSS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const size_t cap = std::min<size_t>(free_b / 4, size_t(1) << 32);
+        int64_t warps = (int64_t)(cap / (ww * sizeof(uint32_t)));
+        warps = std::min<int64_t>(warps, (int64_t)c.num_sms * 32);
+        if (warps < SCT_WARPS) fail(KDSS_ERR_OOM, "count-only pass: no room for one block's workspace");
+        grid = (int)(warps / SCT_WARPS);
+        gws = DBuf<uint32_t>(c, (size_t)grid * SCT_WARPS * ww);
+    }
+    grid = (int)std::min<int64_t>(grid, std::max<int64_t>(1, ceil_div(n, SCT_WARPS)));
+    const size_t dyn = use_shared ? smem : 0;
+    DBuf<CountTotals> tot(c, 1);
+    DBuf<unsigned long long> next(c, 1);
+    DBuf<int> err(c, 1);
+    zero(c, tot.p, sizeof(CountTotals));
+    zero(c, next.p, sizeof(unsigned long long));
+    zero(c, err.p, sizeof(int));
+    unsigned long long mul = 0;
+    for (unsigned long long cand : {2654435761ull, 2246822519ull, 3266489917ull})
+        if ((unsigned long long)n % cand != 0) { mul = cand % (unsigned long long)n; break; }
+    if (mul == 0) mul = 1;
+    PassOut po{};
+    po.tot = tot.p;
+    po.perm_mul = mul;
+    po.budget_ns = budget_s <= 0 ? ~0ull : (unsigned long long)(budget_s * 1e9);
+    ItemsIn in{n, nullptr, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    KDSS_CUDA(cudaEventCreate(&e0));
+    KDSS_CUDA(cudaEventCreate(&e1));
+    KDSS_CUDA(cudaEventRecord(e0, c.stream));
+    k_sct<MODE_TOTAL, 4><<<grid, SCT_THREADS, dyn, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p, k, k,
+                                                           dmax, S, tab.binom.p, tab.binom128.p, k + 1,
+                                                           gws.p, use_shared, next.p, in, po, err.p);
+    KDSS_LAUNCH_CHECK();
+    KDSS_CUDA(cudaEventRecord(e1, c.stream));
+    CountTotals h;
+    int he = 0;
+    to_host(c, &h, tot.p, 1);
+    to_host(c, &he, err.p, 1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (he) fail(KDSS_ERR_CUDA, "count-only pass: inconsistent device state");
+    for (int cl = 0; cl <= NCLASS; ++cl) {
+        out.pairs_per_class[cl] = (int64_t)h.pairs[cl];
+        out.eta += (int64_t)h.pairs[cl];
+        out.L += (int64_t)h.nodes[cl];
+    }
+    out.ck_lo = h.ck[0];
+    out.ck_hi = h.ck[1];
+    out.roots_done = (int64_t)h.roots_done;
+    out.roots_cut = (int64_t)h.roots_cut;
+    out.cut_pairs = (int64_t)h.cut_pairs;
+    out.cut_nodes = (int64_t)h.cut_nodes;
+    out.max_len = h.maxlen;
+    out.count_bits = h.cbits;
+    out.seconds = ms / 1e3;
+    out.complete = (out.roots_done == n) ? 1 : 0;
 }
 
 void sct_from_pairs(const Ctx &c, int64_t n, int k, int64_t np, const int64_t *pair_off,
@@ -708,7 +998,7 @@ void sct_from_pairs(const Ctx &c, int64_t n, int k, int64_t np, const int64_t *p
     }
     to_device(c, out.pair_off.p + np, &nnodes, 1);
     out.nnodes = nnodes;
-    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1));
+    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1) + NODES_PAD);
     out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(np, 1));
     if (np > 0) {
         k_pair_copy<<<grid_for(c, np * 32, B), B, 0, c.stream>>>(np, keys.p, pair_off, h, nodes,
@@ -737,19 +1027,23 @@ void sct_from_pairs(const Ctx &c, int64_t n, int k, int64_t np, const int64_t *p
     }
     upload_binom(c, maxlen + 2, k, out);
     DBuf<unsigned long long> ck(c, 2);
-    DBuf<int> ml(c, 1);
+    DBuf<int> ml(c, 2);
     zero(c, ck.p, 2 * sizeof(unsigned long long));
-    zero(c, ml.p, sizeof(int));
+    zero(c, ml.p, 2 * sizeof(int));
     if (np > 0) {
-        k_pair_ck<<<grid_for(c, np, B), B, 0, c.stream>>>(np, out.pair_off.p, out.h.p, out.binom.p,
-                                                         k + 1, k, ck.p, ml.p, err.p);
+        k_pair_ck<<<grid_for(c, np, B), B, 0, c.stream>>>(np, out.pair_off.p, out.h.p,
+                                                         out.binom128.p, k + 1, k, ck.p, ml.p,
+                                                         ml.p + 1, err.p);
         KDSS_LAUNCH_CHECK();
     }
     unsigned long long hc[2];
+    int hm[2];
     to_host(c, hc, ck.p, 2);
+    to_host(c, hm, ml.p, 2);
     to_host(c, &he, err.p, 1);
     if (he & DERR_BAD_ID) fail(KDSS_ERR_INVALID_ARG, "a pair node id is outside [0, n)");
-    if (he & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs 63 bits or more");
+    if (he & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs more than 128 bits");
+    check_ck_range(hm[1], np);
     out.ck_lo = hc[0];
     out.ck_hi = hc[1];
     out.max_len = maxlen;
@@ -803,7 +1097,7 @@ void sct_restrict(const Ctx &c, const SctDev &all, int k, SctDev &out) {
     out.npairs = kept;
     out.nnodes = nn;
     out.pair_off = DBuf<int64_t>(c, (size_t)kept + 1);
-    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nn, 1));
+    out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nn, 1) + NODES_PAD);
     out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(kept, 1));
     if (kept > 0) {
         k_keep_copy<<<grid_for(c, np * 32, B), B, 0, c.stream>>>(np, all.pair_off.p, all.nodes.p, all.h.p,
@@ -823,19 +1117,21 @@ void sct_restrict(const Ctx &c, const SctDev &all, int k, SctDev &out) {
     // binomials for k, then c_k and the longest pair
     upload_binom(c, std::max(all.max_len, 1) + 2, k, out);
     DBuf<unsigned long long> ck(c, 2);
-    DBuf<int> ml(c, 2);
+    DBuf<int> ml(c, 3);
     zero(c, ck.p, 2 * sizeof(unsigned long long));
-    zero(c, ml.p, 2 * sizeof(int));
+    zero(c, ml.p, 3 * sizeof(int));
     if (kept > 0) {
-        k_pair_ck<<<grid_for(c, kept, B), B, 0, c.stream>>>(kept, out.pair_off.p, out.h.p, out.binom.p,
-                                                           k + 1, k, ck.p, ml.p, ml.p + 1);
+        k_pair_ck<<<grid_for(c, kept, B), B, 0, c.stream>>>(kept, out.pair_off.p, out.h.p,
+                                                           out.binom128.p, k + 1, k, ck.p, ml.p,
+                                                           ml.p + 2, ml.p + 1);
         KDSS_LAUNCH_CHECK();
     }
     unsigned long long hc[2];
-    int hm[2];
+    int hm[3];
     to_host(c, hc, ck.p, 2);
-    to_host(c, hm, ml.p, 2);
-    if (hm[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs 63 bits or more");
+    to_host(c, hm, ml.p, 3);
+    if (hm[1] & DERR_OVERFLOW) fail(KDSS_ERR_OVERFLOW, "a pair's clique count needs more than 128 bits");
+    check_ck_range(hm[2], kept);
     out.ck_lo = hc[0];
     out.ck_hi = hc[1];
     out.max_len = hm[0];

@@ -62,7 +62,7 @@ struct Query {
 };
 
 int64_t sct_footprint(const SctDev &s) {
-    return (int64_t)(s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + s.binom.bytes());
+    return (int64_t)(s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + binom_bytes(s));
 }
 
 int64_t state_footprint(const SctDev &s, int precision) {
@@ -377,7 +377,7 @@ kdss_status kdss_server_submit(kdss_server *s, const kdss_query *q, int64_t *tic
     try {
         if (!s || !q || !ticket) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
         const kdss_graph_desc &g = q->graph;
-        if (q->k < 2 || q->k > 64) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, 64]");
+        if (q->k < 2 || q->k > 255) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, 255]");
         if (q->T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
         if (g.n < 0 || g.n >= (int64_t)INT32_MAX) fail(KDSS_ERR_INVALID_ARG, "n must be in [0, 2^31 - 1)");
         if (g.m < 0 || g.m > ((int64_t)1 << 30)) fail(KDSS_ERR_INVALID_ARG, "m must be in [0, 2^30]");

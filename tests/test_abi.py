@@ -45,12 +45,13 @@ def test_binding_loads_and_reports_version():
 def test_struct_layouts_match_the_header(tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kdss_server.h"\n'
-                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
                    "sizeof(kdss_opts), sizeof(kdss_graph_desc), sizeof(kdss_sct_stats),"
                    "sizeof(kdss_result), sizeof(kdss_timing), sizeof(kdss_query),"
                    "offsetof(kdss_result, status), offsetof(kdss_opts, stream),"
                    "sizeof(kdss_server_opts), sizeof(kdss_query_timing),"
-                   "sizeof(kdss_server_stats));return 0;}\n")
+                   "sizeof(kdss_server_stats), sizeof(kdss_sct_count_stats),"
+                   "offsetof(kdss_sct_count_stats, seconds));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", build_ext.INCLUDE, "-o", str(exe), str(src)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
@@ -59,7 +60,8 @@ def test_struct_layouts_match_the_header(tmp_path):
             ctypes.sizeof(K.kdss_timing), ctypes.sizeof(K.kdss_query),
             K.kdss_result.status.offset, K.kdss_opts.stream.offset,
             ctypes.sizeof(K.kdss_server_opts), ctypes.sizeof(K.kdss_query_timing),
-            ctypes.sizeof(K.kdss_server_stats)]
+            ctypes.sizeof(K.kdss_server_stats), ctypes.sizeof(K.kdss_sct_count_stats),
+            K.kdss_sct_count_stats.seconds.offset]
     assert got == want
 
 

@@ -64,3 +64,50 @@ def test_k_agnostic_handles_are_restricted_before_use():
         with pytest.raises(K.KdssError) as e:
             call()
         assert e.value.code == K.KDSS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_iterating_at_k_filters_p_k_in_place(name):
+    """kdss_fw_iterate_at runs the iterations over P_k of the k-agnostic SCT
+    where it stands (pairs outside P_k skipped by the kernels): r_T, c_k and
+    the extracted prefix equal the k-pruned build's, bit for bit, in the
+    integer rule, and the FP32 rule reaches the same density."""
+    n, s, d = GRAPHS[name]()
+    kmax, T = 7, 20
+    multi = K.kdss_build_sct_multi(n, s, d, kmax)
+    for k in range(2, kmax + 1):
+        b = K.kdss_build_sct(n, s, d, k)
+        if not K.kdss_sct_info(b)["eta_k"]:
+            continue
+        for prec in (K.KDSS_INT64, K.KDSS_FP64):
+            o = K.make_opts(precision=prec)
+            sa = K.kdss_fw_iterate_at(multi, k, None, T, o)
+            sb = K.kdss_fw_iterate(b, None, T, o)
+            ra, ta = K.kdss_state_copy_r(sa, n, prec)
+            rb, tb = K.kdss_state_copy_r(sb, n, prec)
+            assert ta == tb == T and np.array_equal(ra, rb), (k, prec)
+            ea, eb = K.kdss_extract(multi, sa, o), K.kdss_extract(b, sb, o)
+            assert (ea["istar"], ea["count"], ea["ids"].tolist()) == \
+                (eb["istar"], eb["count"], eb["ids"].tolist())
+            assert ea["upper_bound"] == eb["upper_bound"] and ea["rho_prime"] == eb["rho_prime"]
+        o32 = K.make_opts(precision=K.KDSS_FP32K)
+        ea = K.kdss_extract(multi, K.kdss_fw_iterate_at(multi, k, None, T, o32), o32)
+        eb = K.kdss_extract(b, K.kdss_fw_iterate(b, None, T, o32), o32)
+        assert abs(ea["density"] - eb["density"]) <= 0.01 * max(eb["density"], 1e-30)
+
+
+def test_iterating_at_k_checks_its_arguments():
+    n, s, d = synth.g1()
+    multi = K.kdss_build_sct_multi(n, s, d, 4)
+    pruned = K.kdss_build_sct(n, s, d, 3)
+    st = K.kdss_fw_iterate_at(multi, 3, None, 2)
+    for call in (lambda: K.kdss_fw_iterate_at(multi, 5, None, 1),       # above k_max
+                 lambda: K.kdss_fw_iterate_at(multi, 1, None, 1),
+                 lambda: K.kdss_fw_iterate_at(pruned, 4, None, 1),      # not its k
+                 lambda: K.kdss_fw_iterate_at(multi, 4, st, 1)):        # a state of k = 3
+        with pytest.raises(K.KdssError) as e:
+            call()
+        assert e.value.code == K.KDSS_ERR_INVALID_ARG
+    st = K.kdss_fw_iterate_at(multi, 3, st, 48)
+    res = K.kdss_extract(multi, st)
+    assert res["istar"] == 6 and res["count"] == 8                      # Example 1.1

@@ -43,10 +43,10 @@ MUTANTS = {
         "for (int64_t j = i + 1; j < nc; ++j)\n            if (is_adj(c->off, c->adj, v, cand[j]))",
         "for (int64_t j = i + 2; j < nc; ++j)\n            if (is_adj(c->off, c->adj, v, cand[j]))"),
     "binomial_off_by_one": (
-        "v = v * (u128)(a - b + i) / (u128)i;",
-        "v = v * (u128)(a - b + i + 1) / (u128)i;"),
+        "u128 f = (u128)(a - b + i), x = v, y = (u128)i;",
+        "u128 f = (u128)(a - b + i + 1), x = v, y = (u128)i;"),
     "cont_delta_not_cleared_between_iterations": (
-        "memset(dr, 0, sizeof(double) * (size_t)n);", ""),
+        "++t) {\n        memset(dr, 0, sizeof(double) * (size_t)n);", "++t) {\n"),
     "cont_pairs_update_r_in_place": (
         "rc = orc_pbupdate_cont(len, ids, rv, hcnt[q], k, dv);\n            if (rc) break;\n"
         "            for (int i = 0; i < len; ++i) dr[ids[i]] += dv[i];",

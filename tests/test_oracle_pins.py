@@ -282,6 +282,43 @@ def test_pbupdate_is_an_optimal_integer_allocation():
                     assert fin[i] - 1 <= fin[j]
 
 
+def test_binomials_beyond_64_bits():
+    """The 128-bit binomials equal exact integer arithmetic (math.comb) where
+    64 bits overflow, and a value beyond 128 bits is refused."""
+    import math
+    for a, b in [(70, 35), (100, 39), (120, 39), (127, 63), (200, 30), (64, 32)]:
+        assert O.binom128(a, b) == math.comb(a, b)
+    with pytest.raises(OverflowError):
+        O.binom128(300, 150)
+    with pytest.raises(OverflowError):
+        O.binom(100, 39)
+
+
+def test_pbupdate_continuous_with_counts_beyond_64_bits():
+    """The continuous water level of a pair whose n_C = C(p, k - h) needs
+    more than 64 bits: all n_C units are placed (to double rounding), no node
+    exceeds its Lemma 2.6 cap, and the receiving nodes share one level."""
+    import math
+    rng = random.Random(17)
+    for _ in range(200):
+        p = rng.randint(90, 130)
+        h = rng.randint(1, 3)
+        k = h + rng.randint(30, 45)
+        ids = np.array(rng.sample(range(5000), h + p), np.int32)
+        nC = math.comb(p, k - h)
+        assert nC >= 2 ** 64
+        r = np.array([rng.random() * nC * 3 for _ in ids])
+        dl = O.pbupdate_cont(ids, r, h, k)
+        cap = [float(nC)] * h + [float(math.comb(p - 1, k - h - 1))] * p
+        assert abs(dl.sum() - nC) <= 1e-9 * nC
+        assert all(-1e-9 * nC <= dl[i] <= cap[i] * (1 + 1e-12) for i in range(len(ids)))
+        fin = r + dl
+        recv = [i for i in range(len(ids)) if dl[i] > 1e-9 * nC and dl[i] < cap[i] * (1 - 1e-9)]
+        if recv:
+            L = fin[recv[0]]
+            assert all(abs(fin[i] - L) <= 1e-9 * L for i in recv)
+
+
 def test_pbupdate_continuous_is_the_exact_water_level():
     """Continuous rule: all units placed, caps hold, and every node that
     receives weight ends at one common level L that no node with spare
@@ -495,6 +532,21 @@ def test_threaded_synchronous_iterations_equal_the_serial_ones():
         want = O.fw_sync(n, sc, k, T)
         for th in (1, 3, 8):
             assert np.array_equal(O.fw_sync_par(n, sc, k, T, th), want)
+
+
+def test_threaded_continuous_iterations_equal_the_serial_ones():
+    """The host-threaded continuous-rule iterations (used to state the FP32
+    path's error against FP64 on large graphs) add the same numbers in the
+    same order as the serial form: r_T is bit for bit equal."""
+    for n, s, d, k, T in [(*synth.g1(), 3, 40),
+                          (*synth.chung_lu(3000, 10.0, 2.4, 12, plant_size=20, plant_prob=0.9)[:3], 4, 15)]:
+        off, adj = O.csr(n, s, d)
+        core, rnd, _ = O.peel(n, off, adj)
+        rank, vert = O.order(n, core, rnd)
+        sc = O.sct(n, off, adj, rank, vert, k)
+        want = O.fw_cont(n, sc, k, T)
+        for th in (1, 3, 8):
+            assert np.array_equal(O.fw_cont_par(n, sc, k, T, th), want)
 
 
 def test_alg1_synchronous_over_explicit_cliques():
