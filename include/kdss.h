@@ -71,6 +71,11 @@ typedef int32_t kdss_status;
  * 1 ms limit, so every block gives up at its first barrier, the kernel returns
  * and the build fails with KDSS_ERR_TIMEOUT.  Nothing else is affected. */
 #define KDSS_FLAG_TEST_BARRIER_TIMEOUT 8u
+/* Integer-rule first step on the root-shared form of the SCT (each pair as
+ * 16-bit indices into its root's out-neighbourhood, the neighbourhood's r
+ * gathered once per tile) whatever the SCT's size; by default it is used only
+ * when the SCT's node stream exceeds 96 MiB (beyond L2). */
+#define KDSS_FLAG_ROOTED 16u
 
 typedef void *(*kdss_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*kdss_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);

@@ -339,6 +339,7 @@ kdss_status fw_iterate_impl(kdss_sct *s, int32_t k, kdss_state **state, int32_t 
             st->st.qchunk = opts->chunk;
             st->st.qtpp = opts->threads_per_path == 8 ? 8 : 32;
         }
+        st->st.force_rooted = opts && (opts->flags & KDSS_FLAG_ROOTED);
         try {
             fw_init(c, s->s, prec, st->st, k);
         } catch (...) {

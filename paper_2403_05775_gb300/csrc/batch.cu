@@ -415,10 +415,10 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
     for (Group *g : gl) Ts.push_back(g->T);
     std::sort(Ts.begin(), Ts.end());
     Ts.erase(std::unique(Ts.begin(), Ts.end()), Ts.end());
-    // The integer rule runs one work-queue pass per iteration over every
-    // active group (k_pb_queue + k_pb_queue_long), the FP32 rule one set of
-    // per-group launches; either way an iteration is one replayed CUDA graph.
-    const bool queue = prec != KDSS_FP32K;
+    // Every iteration is one work-queue pass over every active group
+    // (k_pb_queue / k_pb_queue_f32 and the long-pair queue kernels) and the
+    // groups' steps, as one replayed CUDA graph.
+    const bool queue = true;
     int chunk = opts ? opts->chunk : 0, tpp = opts ? opts->threads_per_path : 0;
     BatchTuning tune;
     int done = 0;
@@ -473,7 +473,8 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
         };
         // autotuner: after two warm-up iterations, one iteration per candidate
         // (each is a real iteration of the run; the integer results do not
-        // depend on the configuration), then the fastest for the rest
+        // depend on the configuration, the FP32 ones only through the order
+        // of their atomic sums), then the fastest for the rest
         if ((chunk <= 0 || tpp <= 0) && !tune.done) {
             std::vector<std::pair<int, int>> cand;
             bool has_long = false;

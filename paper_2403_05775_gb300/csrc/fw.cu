@@ -398,21 +398,23 @@ __device__ __forceinline__ void warp_seg_add(int32_t id, V x, V *gacc) {
 // unsettled pairs of a tile take their slots with one atomic on the list's
 // counter (lane ranks from a ballot), not one atomic each.
 // Every lane of the warp calls this; lanes with `want` append `value`.
-__device__ __forceinline__ void slow_append(bool want, int32_t value, int32_t *slow, int *slow_count,
-                                            int64_t cap, int *err) {
+// Returns the lane's slot (-1 when it appends nothing).
+__device__ __forceinline__ int64_t slow_append(bool want, int32_t value, int32_t *slow,
+                                               int *slow_count, int64_t cap, int *err) {
     const unsigned FULL_ = 0xffffffffu;
     const unsigned m = __ballot_sync(FULL_, want);
-    if (!m) return;
+    if (!m) return -1;
     const int leader = __ffs(m) - 1;
     int base = 0;
     if ((threadIdx.x & 31) == leader) base = atomicAdd(slow_count, __popc(m));
     base = __shfl_sync(FULL_, base, leader);
-    if (want) {
-        const int64_t slot = (int64_t)base + __popc(m & lanemask_lt());
-        if (slot < cap) slow[slot] = value;
-        else atomicOr(err, DERR_CAPACITY);
-    }
+    if (!want) return -1;
+    const int64_t slot = (int64_t)base + __popc(m & lanemask_lt());
+    if (slot < cap) slow[slot] = value;
+    else atomicOr(err, DERR_CAPACITY);
+    return slot;
 }
+
 
 // First step of Alg. 3 for pairs of at most 32 nodes.  A warp takes 32
 // consecutive pairs: their node ids are copied to shared memory (coalesced)
@@ -533,6 +535,154 @@ k_pb_fast(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
             warp_seg_add<AV>(rid, amount, (AV *)acc);
         }
         __syncwarp();  // sv and sid are rewritten by the next tile
+    }
+}
+
+// First step on the root-shared form of the SCT (SctDev::rooted()): the
+// pairs of a tile come from few roots, and all nodes of a pair lie in its
+// root's out-neighbourhood, so the warp gathers the r words of each distinct
+// root's neighbourhood once (ids and words staged by asynchronous copies),
+// and lane i reads pair i as 16-bit indices into that staged list: the tile
+// costs one gather per neighbourhood entry instead of one per pair node, and
+// the pair stream is 2 bytes per node instead of 4.  A tile whose
+// neighbourhoods do not fit RA_NB entries hands all its pairs to the slow
+// kernel, which takes any pair.  The first-step test is k_pb_fast's.
+constexpr int RA_WARPS = 4;
+constexpr int RA_NB = 768;
+constexpr int64_t ROOTED_MIN_BYTES = int64_t(96) << 20;
+
+struct RootedWarpSmem {
+    uint64_t nbv[RA_NB];       // r words of the tile's neighbourhoods
+    int32_t nbid[RA_NB];       // their original ids
+    uint16_t lid[FA_CAP];      // the tile's local indices (V_h mark in bit 15)
+};
+constexpr size_t RA_SMEM = sizeof(RootedWarpSmem) * RA_WARPS;
+
+template <class RT>
+__global__ void __launch_bounds__(RA_WARPS * 32)
+k_pb_fast_rooted(const int64_t *__restrict__ pair_off, const uint16_t *__restrict__ lidx,
+                 const int32_t *__restrict__ proot, const int64_t *__restrict__ rnb_off,
+                 const int32_t *__restrict__ rnb_ids, const uint8_t *__restrict__ hcnt,
+                 int64_t p_begin, int64_t p_end, const RT *__restrict__ r, RT *acc,
+                 const uint64_t *__restrict__ binom, int bcols, int k, int32_t *slow,
+                 int *slow_count, int64_t slow_cap, int *err) {
+    extern __shared__ __align__(16) unsigned char ra_smem[];
+    using AV = typename AccV<RT>::T;
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    RootedWarpSmem &W = reinterpret_cast<RootedWarpSmem *>(ra_smem)[wib];
+    const int64_t np = p_end - p_begin;
+    const int64_t ntile = (np + 31) >> 5;
+    for (int64_t tile = blockIdx.x * (int64_t)RA_WARPS + wib; tile < ntile;
+         tile += (int64_t)gridDim.x * RA_WARPS) {
+        const int64_t qi = tile * 32 + lane;
+        const bool valid = qi < np;
+        const int64_t q = p_begin + (valid ? qi : np - 1);
+        const int64_t myb = pair_off[q], mye = pair_off[q + 1];
+        const int hq = valid ? (int)hcnt[q] : 0;
+        const int32_t root = proot[q];
+        const int64_t B = __shfl_sync(FULL_, myb, 0);
+        const int64_t E = __shfl_sync(FULL_, mye, 31);
+        const int cnt = (int)(E - B);
+        if (cnt > FA_CAP) {
+            if (lane == 0) atomicOr(err, DERR_CAPACITY);
+            continue;
+        }
+        // distinct roots of the tile: the lowest lane of each root's group
+        // leads it; leaders' list sizes, scanned in lane order, place them
+        const unsigned grp = __match_any_sync(FULL_, root);
+        const int leader = __ffs(grp) - 1;
+        const bool lead = lane == leader;
+        const int64_t roff = rnb_off[root];
+        const int rsz = lead ? (int)(rnb_off[root + 1] - roff) : 0;
+        int incl = rsz;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(FULL_, incl, 31);
+        const int mybase = __shfl_sync(FULL_, incl - rsz, leader);
+        if (total > RA_NB) {   // uniform: the slow kernel takes the whole tile
+            const bool inpk = valid && hq <= k && k <= (int)(mye - myb);
+            slow_append(inpk, (int32_t)qi, slow, slow_count, slow_cap, err);
+            continue;
+        }
+        // stage the neighbourhoods' ids, and the tile's local indices
+        unsigned leaders = __ballot_sync(FULL_, lead);
+        while (leaders) {
+            const int L = __ffs(leaders) - 1;
+            leaders &= leaders - 1;
+            const int64_t off = __shfl_sync(FULL_, roff, L);
+            const int sz = __shfl_sync(FULL_, rsz, L);
+            const int base = __shfl_sync(FULL_, incl - rsz, L);
+            for (int i = lane; i < sz; i += 32) cp_async4(W.nbid + base + i, rnb_ids + off + i);
+        }
+        for (int i = lane; i < cnt; i += 32) W.lid[i] = __ldg(lidx + B + i);
+        cp_async_wait_all();
+        __syncwarp();
+        for (int i = lane; i < total; i += 32) cp_async8(W.nbv + i, r + W.nbid[i]);
+        cp_async_wait_all();
+        __syncwarp();
+        uint32_t rmask = 0;
+        bool want_slow = false;
+        uint64_t w = 0, R = 0;
+        int o = 0;
+        if (valid && hq <= k && k <= (int)(mye - myb)) {
+            o = (int)(myb - B);
+            const int len = (int)(mye - myb);
+            const int h = hq;
+            const int p = len - h;
+            const uint64_t nC = __ldg(binom + (size_t)p * bcols + (k - h));
+            const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                                       ? __ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+            const uint64_t pm = cap_p > 0 ? 0ull : ~0ull;
+            uint64_t m1 = ~0ull, m2 = ~0ull;
+            uint32_t mask1 = 0;
+            bool piv1 = false;
+            for (int s2 = 0; s2 < len; ++s2) {
+                const uint32_t li = W.lid[o + s2];
+                const bool hold = (li & 0x8000u) != 0;
+                const uint64_t e = W.nbv[mybase + (li & 0x7fffu)];
+                const uint64_t v = e | (hold ? 0ull : pm);
+                const bool lt = v < m1;
+                const bool eq = v == m1 && v != ~0ull;
+                const uint64_t mn = v < m2 ? v : m2;
+                m2 = lt ? m1 : (eq ? m2 : mn);
+                m1 = lt ? v : m1;
+                const uint32_t bit = 1u << s2;
+                mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                piv1 = lt ? !hold : (piv1 || (eq && !hold));
+            }
+            if (mask1) {
+                const uint64_t na = (uint64_t)__popc(mask1);
+                const uint64_t mu = piv1 ? cap_p : nC;
+                const uint64_t gap = m2 == ~0ull ? ~0ull : level_of<RT>(m2) - level_of<RT>(m1);
+                w = nC / na;
+                R = nC - w * na;
+                const uint64_t lim = mu < gap ? mu : gap;
+                if (!(R == 0 ? w > lim : w >= lim)) rmask = mask1;
+                else want_slow = true;
+            }
+        }
+        slow_append(want_slow, (int32_t)qi, slow, slow_count, slow_cap, err);
+        uint64_t rank = 0;
+        while (__any_sync(FULL_, rmask != 0)) {
+            int32_t rid = -1;
+            AV amount = AV(0);
+            if (rmask) {
+                const int sl = __ffs(rmask) - 1;
+                rmask &= rmask - 1;
+                const uint64_t dl = w + (rank < R ? 1ull : 0ull);
+                ++rank;
+                if (dl) {
+                    rid = W.nbid[mybase + (W.lid[o + sl] & 0x7fffu)];
+                    amount = (AV)dl;
+                }
+            }
+            warp_seg_add<AV>(rid, amount, (AV *)acc);
+        }
+        __syncwarp();
     }
 }
 
@@ -748,6 +898,7 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int64_t np = *list_count;
     np = np < list_cap ? np : list_cap;
+    using AVs = typename AccV<RT>::T;
     // PIPE: software pipeline over the warp's pairs li, li + st, li + 2 st,
     // ...  A pair's data is a chain of dependent loads (list entry ->
     // offsets -> node ids -> r words), so each iteration issues the next link
@@ -758,7 +909,7 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
     // per warp, where the prologue would not pay).
     const int64_t st = (int64_t)gridDim.x * SB_WARPS;
     const int64_t li0 = blockIdx.x * (int64_t)SB_WARPS + wib;
-    // slots marked -1 (claimed by a first-step warp, not used) are skipped
+    // a negative entry names no pair and is skipped
     auto pair_of = [&](int64_t x) -> int64_t {
         if (x >= np) return -1;
         const int32_t l = list[x];
@@ -819,7 +970,6 @@ k_pb_slow(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ node
             continue;
         }
         if (len == 0) continue;  // an unused slot
-        using AVs = typename AccV<RT>::T;
         slow_pair_walk<AVs>(len, h, rawc, rjc, k, binom, bcols, acc, sr[wib], sc[wib], err);
     }
 }
@@ -1117,6 +1267,109 @@ k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
 // active level: L is the water level with g(L) = n_C/s, found from the
 // largest breakpoint b with g(b) <= n_C/s as b + (n_C/s - g(b)) / slope(b);
 // node j takes min(cap_j, max(0, L - x_j)).
+// The continuous water level of one pair of at most 32 nodes by one warp
+// (k_pb_slow_f32's walk and closed form): lane j holds node j (raw id with the
+// V_h mark in rawc, its r/t value xc); lanes >= len hold nothing.  nC_raw
+// and the caps come from the float table, scaled by inv_sigma.  sp_w: 32
+// float2 of this warp's shared memory.
+__device__ __forceinline__ void slow_pair_walk_f32(int len, int h, int32_t rawc, float xc, int k,
+                                                   const float *__restrict__ binomf, int bcols,
+                                                   float inv_sigma, float *acc, float *accc,
+                                                   float2 *sp_w, int *err) {
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float INF = __int_as_float(0x7f800000);
+    const int p = len - h;
+    const float nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
+    const float cap_p = (p >= 1 && k - h - 1 >= 0)
+                            ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                            : 0.f;
+    int32_t id = -1;
+    float xj = 0.f, cj = 0.f;
+    if (lane < len) {
+        id = rawc & 0x7fffffff;
+        xj = xc;
+        cj = rawc < 0 ? nC : cap_p;
+    }
+    // lowest level among the nodes that can receive (non-negative floats
+    // order like their bit patterns: one 32-bit warp reduction)
+    const float base = __uint_as_float(
+        __reduce_min_sync(FULL_, __float_as_uint(cj > 0.f ? xj : INF)));
+    const float xl = cj > 0.f ? xj - base : 0.f;
+    // the walk of Alg. 3 in real arithmetic, as in k_pb_slow: the level
+    // rises from event to event while the units last and stops at
+    // L* = L + rem / na; pairs that cross more than SB_ROUNDS events take
+    // the closed form below
+    {
+        const float top = xl + cj;
+        float L = 0.f, rem = nC, Ls = 0.f;
+        bool done = false;
+        for (int round = 0; round < SB_ROUNDS; ++round) {
+            const bool act = cj > 0.f && xl <= L && L < top;
+            const int na = __popc(__ballot_sync(FULL_, act));
+            const float e1 = (cj > 0.f && xl > L) ? xl : INF;
+            const float e2 = act ? top : INF;
+            const float ev = __uint_as_float(__reduce_min_sync(FULL_, __float_as_uint(fminf(e1, e2))));
+            if (na == 0) {
+                if (ev == INF) break;
+                L = ev;
+                continue;
+            }
+            const float qd = rem / (float)na;
+            if (ev == INF || L + qd <= ev) {
+                Ls = L + qd;
+                done = true;
+                break;
+            }
+            rem -= (ev - L) * (float)na;
+            L = ev;
+            if (!(rem > 0.f)) {
+                Ls = L;
+                done = true;
+                break;
+            }
+        }
+        if (done) {
+            const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, Ls - xl)) : 0.f;
+            if (dj > 0.f) gadd_f32(acc, accc, id, dj);
+            __syncwarp();
+            return;
+        }
+    }
+    sp_w[lane] = make_float2(xl, cj);
+    __syncwarp();
+    const float b1 = xl, b2 = xl + cj;
+    float g1 = 0.f, g2 = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < len; ++i) {
+        const float2 e = sp_w[i];
+        g1 += fminf(e.y, fmaxf(0.f, b1 - e.x));
+        g2 += fminf(e.y, fmaxf(0.f, b2 - e.x));
+    }
+    float key = -1.f, bg = 0.f;
+    if (cj > 0.f) {
+        if (g1 <= nC) { key = b1; bg = g1; }
+        if (g2 <= nC) { key = b2; bg = g2; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ok = __shfl_xor_sync(FULL_, key, o);
+        const float og = __shfl_xor_sync(FULL_, bg, o);
+        if (ok > key) { key = ok; bg = og; }
+    }
+    if (key < 0.f) {
+        if (lane == 0) atomicOr(err, DERR_LOGIC);
+        return;
+    }
+    // right slope at key: nodes with x_j <= key < x_j + c_j, the upper end
+    // rounded exactly as the breakpoint b2 was
+    const int sl = __popc(__ballot_sync(FULL_, cj > 0.f && key >= xl && key < b2));
+    const float L = sl > 0 ? key + (nC - bg) / (float)sl : key;
+    const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, L - xl)) : 0.f;
+    if (dj > 0.f) gadd_f32(acc, accc, id, dj);
+    __syncwarp();
+}
+
 template <bool PIPE>
 __global__ void __launch_bounds__(SB_WARPS * 32, 5)
 k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
@@ -1125,16 +1378,14 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
               const int *t_done, const int32_t *__restrict__ list, const int *list_count,
               int64_t list_cap, int *err) {
     __shared__ float2 sp[SB_WARPS][32];
-    const unsigned FULL_ = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const float inv_sigma = inv_sigma_of(t_done);
-    const float INF = __int_as_float(0x7f800000);
     int64_t np = *list_count;
     np = np < list_cap ? np : list_cap;
     // the load pipeline of k_pb_slow (PIPE) or one chain per pair
     const int64_t st = (int64_t)gridDim.x * SB_WARPS;
     const int64_t li0 = blockIdx.x * (int64_t)SB_WARPS + wib;
-    // slots marked -1 (claimed by a first-step warp, not used) are skipped
+    // a negative entry names no pair and is skipped
     auto pair_of = [&](int64_t x) -> int64_t {
         if (x >= np) return -1;
         const int32_t l = list[x];
@@ -1192,95 +1443,112 @@ k_pb_slow_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ 
             continue;
         }
         if (len == 0) continue;  // an unused slot
-        const int p = len - h;
-        const float nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
-        const float cap_p = (p >= 1 && k - h - 1 >= 0)
-                                ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
-                                : 0.f;
-        int32_t id = -1;
-        float xj = 0.f, cj = 0.f;
-        if (lane < len) {
-            id = rawc & 0x7fffffff;
-            xj = xc;
-            cj = rawc < 0 ? nC : cap_p;
-        }
-        // lowest level among the nodes that can receive (non-negative floats
-        // order like their bit patterns: one 32-bit warp reduction)
-        const float base = __uint_as_float(
-            __reduce_min_sync(FULL_, __float_as_uint(cj > 0.f ? xj : INF)));
-        const float xl = cj > 0.f ? xj - base : 0.f;
-        // the walk of Alg. 3 in real arithmetic, as in k_pb_slow: the level
-        // rises from event to event while the units last and stops at
-        // L* = L + rem / na; pairs that cross more than SB_ROUNDS events take
-        // the closed form below
-        {
-            const float top = xl + cj;
-            float L = 0.f, rem = nC, Ls = 0.f;
-            bool done = false;
-            for (int round = 0; round < SB_ROUNDS; ++round) {
-                const bool act = cj > 0.f && xl <= L && L < top;
-                const int na = __popc(__ballot_sync(FULL_, act));
-                const float e1 = (cj > 0.f && xl > L) ? xl : INF;
-                const float e2 = act ? top : INF;
-                const float ev = __uint_as_float(__reduce_min_sync(FULL_, __float_as_uint(fminf(e1, e2))));
-                if (na == 0) {
-                    if (ev == INF) break;
-                    L = ev;
-                    continue;
-                }
-                const float qd = rem / (float)na;
-                if (ev == INF || L + qd <= ev) {
-                    Ls = L + qd;
-                    done = true;
-                    break;
-                }
-                rem -= (ev - L) * (float)na;
-                L = ev;
-                if (!(rem > 0.f)) {
-                    Ls = L;
-                    done = true;
-                    break;
-                }
-            }
-            if (done) {
-                const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, Ls - xl)) : 0.f;
-                if (dj > 0.f) gadd_f32(acc, accc, id, dj);
-                __syncwarp();
-                continue;
-            }
-        }
-        sp[wib][lane] = make_float2(xl, cj);
-        __syncwarp();
-        const float b1 = xl, b2 = xl + cj;
-        float g1 = 0.f, g2 = 0.f;
-#pragma unroll 4
-        for (int i = 0; i < len; ++i) {
-            const float2 e = sp[wib][i];
-            g1 += fminf(e.y, fmaxf(0.f, b1 - e.x));
-            g2 += fminf(e.y, fmaxf(0.f, b2 - e.x));
-        }
-        float key = -1.f, bg = 0.f;
-        if (cj > 0.f) {
-            if (g1 <= nC) { key = b1; bg = g1; }
-            if (g2 <= nC) { key = b2; bg = g2; }
-        }
+        slow_pair_walk_f32(len, h, rawc, xc, k, binomf, bcols, inv_sigma, acc, accc, sp[wib], err);
+    }
+}
+
+// Rule C PBUpdate of one pair by a group of G lanes (as group_pair_walk):
+// the continuous walk relative to the pair's lowest active level; every lane
+// of the warp calls it; scatter(id, amount) receives each node's allocation.
+template <int G, int NPL, class Scatter>
+__device__ __forceinline__ void group_pair_walk_f32(bool active, int64_t q,
+                                                    const int64_t *__restrict__ pair_off,
+                                                    const int32_t *__restrict__ nodes,
+                                                    const uint8_t *__restrict__ hcnt,
+                                                    const float *__restrict__ r,
+                                                    const float *__restrict__ binomf, int bcols,
+                                                    int k, float inv_sigma, int *err,
+                                                    Scatter scatter) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const float INF = __int_as_float(0x7f800000);
+    int64_t off0 = 0;
+    int len = 0, h = 0;
+    if (active) {
+        off0 = pair_off[q];
+        len = (int)(pair_off[q + 1] - off0);
+        h = hcnt[q];
+    }
+    const bool inpk = active && h <= k && k <= len;   // P_k filter, as k_pbupdate_int
+    const int p = len - h;
+    float nC = 0.f, cap_h = 0.f, cap_p = 0.f;
+    if (inpk) {
+        nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
+        cap_h = nC;
+        cap_p = (p >= 1 && k - h - 1 >= 0)
+                    ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                    : 0.f;
+    }
+    float r0[NPL], cur[NPL], up[NPL];
+    int32_t id[NPL];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ok = __shfl_xor_sync(FULL_, key, o);
-            const float og = __shfl_xor_sync(FULL_, bg, o);
-            if (ok > key) { key = ok; bg = og; }
+    for (int s = 0; s < NPL; ++s) {
+        const int j = s * G + gl;
+        const bool valid = inpk && j < len;
+        const int32_t raw = valid ? __ldg(nodes + off0 + j) : 0;
+        id[s] = raw & 0x7fffffff;
+        r0[s] = valid ? __ldg(r + id[s]) : INF;
+        up[s] = valid ? (raw < 0 ? cap_h : cap_p) : 0.f;
+        cur[s] = r0[s];
+    }
+    float rem = inpk ? nC : 0.f;
+    // Work relative to the pair's lowest active level, so that the
+    // allocation (final level - start) is not a difference of two large
+    // values of r.
+    float lev = 0.f;
+    {
+        float m = INF;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s)
+            if (up[s] > 0.f) m = fminf(m, cur[s]);
+        const float base = gmin_f32<G>(m);
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            r0[s] = (r0[s] == INF || base == INF) ? INF : r0[s] - base;
+            cur[s] = r0[s];
         }
-        if (key < 0.f) {
-            if (lane == 0) atomicOr(err, DERR_LOGIC);
-            continue;
+    }
+    int guard = 0;
+    const int guard_max = 4 * G * NPL + 8;
+    while (__any_sync(FULL, rem > 0.f)) {
+        float nx = INF, mu = INF;
+        int na = 0;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            if (up[s] > 0.f) {
+                if (cur[s] == lev) { ++na; mu = fminf(mu, up[s]); }
+                else if (cur[s] > lev) nx = fminf(nx, cur[s]);
+            }
         }
-        // right slope at key: nodes with x_j <= key < x_j + c_j, the upper end
-        // rounded exactly as the breakpoint b2 was
-        const int sl = __popc(__ballot_sync(FULL_, cj > 0.f && key >= xl && key < b2));
-        const float L = sl > 0 ? key + (nC - bg) / (float)sl : key;
-        const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, L - xl)) : 0.f;
-        if (dj > 0.f) gadd_f32(acc, accc, id, dj);
-        __syncwarp();
+        na = gsum_i32<G>(na);
+        mu = gmin_f32<G>(mu);
+        nx = gmin_f32<G>(nx);
+        if (rem > 0.f) {
+            if (na == 0) {
+                if (nx == INF) { atomicOr(err, DERR_LOGIC); rem = 0.f; }
+                else lev = nx;
+            } else {
+                const float gap = nx - lev;
+                const float share = rem / (float)na;
+                float w = fminf(mu, gap);
+                const bool last = share <= w;
+                if (last) w = share;
+                const float nl = (!last && w == gap) ? nx : lev + w;
+#pragma unroll
+                for (int s = 0; s < NPL; ++s)
+                    if (up[s] > 0.f && cur[s] == lev) { cur[s] = nl; up[s] -= w; }
+                rem = last ? 0.f : rem - w * (float)na;
+                if (rem < 0.f) rem = 0.f;
+                lev = nl;
+            }
+        }
+        if (++guard > guard_max) break;
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const int j = s * G + gl;
+        if (inpk && j < len && cur[s] > r0[s])
+            scatter(id[s], cur[s] - r0[s]);
     }
 }
 
@@ -1295,7 +1563,6 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
     constexpr int GPW = 32 / G;
     const float inv_sigma = inv_sigma_of(t_done);
     const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // pairs [p_begin, p_end), or p_begin + list[i] for i < *list_count
@@ -1304,7 +1571,6 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
         const int lc = *list_count;
         np = lc < np ? lc : np;
     }
-    const float INF = __int_as_float(0x7f800000);
     __shared__ AggTable<float> tbl;
     agg_init(tbl);
     const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
@@ -1315,96 +1581,156 @@ k_pbupdate_f32(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
         const int64_t qi = wb + lane / G;
         const bool active = qi < ce;
         const int64_t q = p_begin + (list ? (active ? (int64_t)list[qi] : 0) : qi);
-        int64_t off0 = 0;
-        int len = 0, h = 0;
-        if (active) {
-            off0 = pair_off[q];
-            len = (int)(pair_off[q + 1] - off0);
-            h = hcnt[q];
-        }
-        const bool inpk = active && h <= k && k <= len;   // P_k filter, as k_pbupdate_int
-        const int p = len - h;
-        float nC = 0.f, cap_h = 0.f, cap_p = 0.f;
-        if (inpk) {
-            nC = __ldg(binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
-            cap_h = nC;
-            cap_p = (p >= 1 && k - h - 1 >= 0)
-                        ? __ldg(binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
-                        : 0.f;
-        }
-        float r0[NPL], cur[NPL], up[NPL];
-        int32_t id[NPL];
-#pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int j = s * G + gl;
-            const bool valid = inpk && j < len;
-            const int32_t raw = valid ? __ldg(nodes + off0 + j) : 0;
-            id[s] = raw & 0x7fffffff;
-            r0[s] = valid ? __ldg(r + id[s]) : INF;
-            up[s] = valid ? (raw < 0 ? cap_h : cap_p) : 0.f;
-            cur[s] = r0[s];
-        }
-        float rem = inpk ? nC : 0.f;
-        // Work relative to the pair's lowest active level, so that the
-        // allocation (final level - start) is not a difference of two large
-        // values of r.
-        float lev = 0.f;
-        {
-            float m = INF;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s)
-                if (up[s] > 0.f) m = fminf(m, cur[s]);
-            const float base = gmin_f32<G>(m);
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                r0[s] = (r0[s] == INF || base == INF) ? INF : r0[s] - base;
-                cur[s] = r0[s];
-            }
-        }
-        int guard = 0;
-        const int guard_max = 4 * G * NPL + 8;
-        while (__any_sync(FULL, rem > 0.f)) {
-            float nx = INF, mu = INF;
-            int na = 0;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                if (up[s] > 0.f) {
-                    if (cur[s] == lev) { ++na; mu = fminf(mu, up[s]); }
-                    else if (cur[s] > lev) nx = fminf(nx, cur[s]);
-                }
-            }
-            na = gsum_i32<G>(na);
-            mu = gmin_f32<G>(mu);
-            nx = gmin_f32<G>(nx);
-            if (rem > 0.f) {
-                if (na == 0) {
-                    if (nx == INF) { atomicOr(err, DERR_LOGIC); rem = 0.f; }
-                    else lev = nx;
-                } else {
-                    const float gap = nx - lev;
-                    const float share = rem / (float)na;
-                    float w = fminf(mu, gap);
-                    const bool last = share <= w;
-                    if (last) w = share;
-                    const float nl = (!last && w == gap) ? nx : lev + w;
-#pragma unroll
-                    for (int s = 0; s < NPL; ++s)
-                        if (up[s] > 0.f && cur[s] == lev) { cur[s] = nl; up[s] -= w; }
-                    rem = last ? 0.f : rem - w * (float)na;
-                    if (rem < 0.f) rem = 0.f;
-                    lev = nl;
-                }
-            }
-            if (++guard > guard_max) break;
-        }
-#pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int j = s * G + gl;
-            if (inpk && j < len && cur[s] > r0[s])
-                agg_add_f32(tbl, id[s], cur[s] - r0[s], acc, accc);
-        }
+        group_pair_walk_f32<G, NPL>(active, q, pair_off, nodes, hcnt, r, binomf, bcols, k, inv_sigma,
+                                    err, [&](int32_t id, float x) { agg_add_f32(tbl, id, x, acc, accc); });
     }
     agg_flush_f32(tbl, acc, accc);
+}
+
+// The continuous rule (KDSS_FP32K) on the work queue: the first step of
+// k_pb_fast_f32s on each tile (r/t words gathered through registers, the V_h
+// mark in the sign bit), the pairs it leaves walked by the same warp from the
+// staged tile (slow_pair_walk_f32), compensated scatter-adds.
+struct QSmemF32 {
+    float sval[QW][FA_CAP];
+    float2 sp[QW][32];   // walk scratch
+};
+
+__global__ void __launch_bounds__(QW * 32)
+k_pb_queue_f32(const QGroup *__restrict__ groups, const QItem *__restrict__ items, int nitems,
+               unsigned *cursor, const float *__restrict__ r_all, float *acc_all, float *accc_all,
+               const int *t_done, int *err) {
+    __shared__ QSmemF32 S;
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const float INF = __int_as_float(0x7f800000);
+    const float inv_sigma = inv_sigma_of(t_done);
+    float *sv = S.sval[wib];
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(cursor, 1u);
+        it = __shfl_sync(FULL_, it, 0);
+        if (it >= nitems) break;
+        const QItem I = items[it];
+        const QGroup G = groups[I.g];
+        const float *r = r_all + G.node_off;
+        float *acc = acc_all + G.node_off;
+        float *accc = accc_all + G.node_off;
+        const int k = G.k, bcols = G.bcols;
+        const int64_t np = G.short_end;
+        for (int64_t tile = I.first; tile < I.first + I.count; ++tile) {
+            const int64_t qi = tile * 32 + lane;
+            const bool valid = qi < np;
+            const int64_t q = valid ? qi : np - 1;
+            const int64_t myb = G.pair_off[q], mye = G.pair_off[q + 1];
+            const int64_t B = __shfl_sync(FULL_, myb, 0);
+            const int64_t E = __shfl_sync(FULL_, mye, 31);
+            const int cnt = (int)(E - B);
+            if (cnt > FA_CAP) {
+                if (lane == 0) atomicOr(err, DERR_CAPACITY);
+                continue;
+            }
+#pragma unroll 4
+            for (int i = lane; i < cnt; i += 32) {
+                const int32_t raw = __ldg(G.nodes + B + i);
+                const float v = __ldg(r + (raw & 0x7fffffff));
+                sv[i] = raw < 0 ? -v : v;  // -0.0 keeps the mark for v = 0
+            }
+            __syncwarp();
+            const int o = (int)(myb - B);
+            const int len = (int)(mye - myb);
+            const int h = valid ? (int)G.h[q] : 0;
+            uint32_t rmask = 0;
+            float share = 0.f;
+            bool want_slow = false;
+            if (valid && h <= k && k <= len) {
+                const int p = len - h;
+                const float nC = __ldg(G.binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
+                const float cap_p = (p >= 1 && k - h - 1 >= 0)
+                                        ? __ldg(G.binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                                        : 0.f;
+                const bool prx = cap_p > 0.f;
+                float m1 = INF, m2 = INF;
+                uint32_t mask1 = 0;
+                bool piv1 = false;
+                for (int s2 = 0; s2 < len; ++s2) {
+                    const float e = sv[o + s2];
+                    const bool hold = signbit(e);
+                    const float v = (hold || prx) ? fabsf(e) : INF;
+                    const bool lt = v < m1;
+                    const bool eq = v == m1 && v < INF;
+                    const float mn = fminf(m2, v);
+                    m2 = lt ? m1 : (eq ? m2 : mn);
+                    m1 = lt ? v : m1;
+                    const uint32_t bit = 1u << s2;
+                    mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                    piv1 = lt ? !hold : (piv1 || (eq && !hold));
+                }
+                if (mask1) {
+                    const float na = (float)__popc(mask1);
+                    const float mu = piv1 ? cap_p : nC;
+                    share = nC / na;
+                    if (share <= mu && share <= m2 - m1) rmask = mask1;
+                    else want_slow = true;
+                }
+            }
+            unsigned um = __ballot_sync(FULL_, want_slow);
+            while (um) {
+                const int src = __ffs(um) - 1;
+                um &= um - 1;
+                const int so = __shfl_sync(FULL_, o, src);
+                const int sl = __shfl_sync(FULL_, len, src);
+                const int shh = __shfl_sync(FULL_, h, src);
+                int32_t rawc = 0;
+                float xc = 0.f;
+                if (lane < sl) {
+                    rawc = __ldg(G.nodes + B + so + lane);
+                    xc = fabsf(sv[so + lane]);
+                }
+                slow_pair_walk_f32(sl, shh, rawc, xc, k, G.binomf, bcols, inv_sigma, acc, accc,
+                                   S.sp[wib], err);
+            }
+            while (__any_sync(FULL_, rmask != 0)) {
+                int32_t rid = -1;
+                float amount = 0.f;
+                if (rmask) {
+                    const int sl = __ffs(rmask) - 1;
+                    rmask &= rmask - 1;
+                    rid = __ldg(G.nodes + B + o + sl) & 0x7fffffff;
+                    amount = share;
+                }
+                warp_seg_add_f32(rid, amount, acc, accc);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int G, int NPL>
+__global__ void __launch_bounds__(FW_THREADS)
+k_pb_queue_long_f32(const QGroup *__restrict__ groups, const QItem *__restrict__ items, int nitems,
+                    unsigned *cursor, const float *__restrict__ r_all, float *acc_all,
+                    float *accc_all, const int *t_done, int *err) {
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const float inv_sigma = inv_sigma_of(t_done);
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(cursor, 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= nitems) break;
+        const QItem I = items[it];
+        const QGroup Gd = groups[I.g];
+        const float *r = r_all + Gd.node_off;
+        float *acc = acc_all + Gd.node_off;
+        float *accc = accc_all + Gd.node_off;
+        for (int64_t q0 = I.first; q0 < I.first + I.count; q0 += GPW) {
+            const int64_t q = q0 + lane / G;
+            group_pair_walk_f32<G, NPL>(q < I.first + I.count, q, Gd.pair_off, Gd.nodes, Gd.h, r,
+                                        Gd.binomf, Gd.bcols, Gd.k, inv_sigma, err,
+                                        [&](int32_t id, float x) { gadd_f32(acc, accc, id, x); });
+        }
+    }
 }
 
 // r_t = r_{t-1} + delta (rule I); running max of r for the bound.
@@ -1478,7 +1804,7 @@ inline bool slow_pipelined(int64_t short_pairs, int grid) {
 // 32-lane group walk directly.
 template <class RT>
 void launch_pbupdate_int(const Ctx &c, const SctDev &s, int k, RT *r, RT *acc, int32_t *slow,
-                         int *slow_count, int *err) {
+                         int *slow_count, int *err, bool force_rooted = false) {
     const int bc = s.bcols();
     const int64_t b = s.class_begin[0], e = s.class_begin[3];
     auto go = [&](auto kern, int G, int64_t pb, int64_t pe, const int32_t *list, const int *lc) {
@@ -1491,10 +1817,28 @@ void launch_pbupdate_int(const Ctx &c, const SctDev &s, int k, RT *r, RT *acc, i
     if (e > b) {
         const int64_t tiles = ceil_div(e - b, 32);
         const int64_t cap = slow_list_capacity(e - b, c.num_sms);
-        int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
-        k_pb_fast<RT><<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e, r,
-                                                            acc, s.binom.p, bc, k, slow, slow_count,
-                                                            cap, err);
+        // the root-shared first step where the pair stream exceeds L2 (where
+        // each gathered r word costs a DRAM-side sector); the flat one where
+        // the SCT stays in L2 and the extra indirection does not pay
+        if (s.rooted() && (force_rooted || s.nnodes * (int64_t)sizeof(int32_t) > ROOTED_MIN_BYTES)) {
+            static thread_local int attr_dev = -1;
+            if (attr_dev != c.device) {
+                KDSS_CUDA(cudaFuncSetAttribute(k_pb_fast_rooted<uint64_t>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RA_SMEM));
+                KDSS_CUDA(cudaFuncSetAttribute(k_pb_fast_rooted<double>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RA_SMEM));
+                attr_dev = c.device;
+            }
+            int grid = (int)std::min<int64_t>(ceil_div(tiles, RA_WARPS), (int64_t)c.num_sms * 5);
+            k_pb_fast_rooted<RT><<<grid, RA_WARPS * 32, RA_SMEM, c.stream>>>(
+                s.pair_off.p, s.lidx.p, s.proot.p, s.rnb_off.p, s.rnb_ids.p, s.h.p, b, e, r, acc,
+                s.binom.p, bc, k, slow, slow_count, cap, err);
+        } else {
+            int grid = (int)std::min<int64_t>(ceil_div(tiles, FA_WARPS), (int64_t)c.num_sms * 7);
+            k_pb_fast<RT><<<grid, FA_WARPS * 32, 0, c.stream>>>(s.pair_off.p, s.nodes.p, s.h.p, b, e,
+                                                                r, acc, s.binom.p, bc, k, slow,
+                                                                slow_count, cap, err);
+        }
         KDSS_LAUNCH_CHECK();
         int sgrid = (int)std::min<int64_t>(ceil_div(e - b, SB_WARPS), (int64_t)c.num_sms * 8);
         auto slow_kern = slow_pipelined(e - b, sgrid) ? k_pb_slow<RT, true> : k_pb_slow<RT, false>;
@@ -1599,16 +1943,16 @@ void fw_init(const Ctx &c, const SctDev &s, int precision, StateDev &st, int k) 
 namespace {
 
 void enqueue_pbupdate(const Ctx &c, const SctDev &s, StateDev &st) {
-    if (st.qchunk > 0 && st.precision != KDSS_FP32K) {
+    if (st.qchunk > 0) {
         queue_enqueue(c, st.qplan, st);
     } else if (st.precision == KDSS_FP32K) {
         launch_pbupdate_f32(c, s, st);
     } else if (st.precision == KDSS_FP64) {
         launch_pbupdate_int<double>(c, s, st.k, (double *)st.r.p, (double *)st.acc.p, st.ovf_list.p,
-                                    st.ovf_count.p, st.err.p);
+                                    st.ovf_count.p, st.err.p, st.force_rooted);
     } else {
         launch_pbupdate_int<uint64_t>(c, s, st.k, st.r.p, st.acc.p, st.ovf_list.p, st.ovf_count.p,
-                                      st.err.p);
+                                      st.err.p, st.force_rooted);
     }
 }
 
@@ -1690,8 +2034,7 @@ void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
     // per (state, SCT) and replayed T times on the caller's stream.
     if (st.graph_sct != &s) {
         st.release_graphs();
-        if (st.qchunk > 0 && st.precision != KDSS_FP32K)
-            queue_plan(c, {{&s, 0}}, st.qchunk, st.qtpp, st.qplan, st.k);
+        if (st.qchunk > 0) queue_plan(c, {{&s, 0}}, st.qchunk, st.qtpp, st.qplan, st.k);
         st.nk_pb = capture(c, &st.g_pb, [&](const Ctx &cc) { enqueue_pbupdate(cc, s, st); });
         st.nk_step = capture(c, &st.g_step, [&](const Ctx &cc) { enqueue_step(cc, s, st); });
         capture(c, &st.g_iter, [&](const Ctx &cc) {
@@ -1876,6 +2219,7 @@ void queue_plan(const Ctx &c, const std::vector<std::pair<const SctDev *, int64_
         d.nodes = s.nodes.p;
         d.h = s.h.p;
         d.binom = s.binom.p;
+        d.binomf = s.binomf.p;
         d.bcols = s.bcols();
         d.k = k >= 0 ? k : s.k;
         d.node_off = sets[g].second;
@@ -1924,11 +2268,33 @@ void queue_launch_long(const Ctx &c, QueuePlan &qp, StateDev &st, RT *r, RT *acc
     go(k_pb_queue_long<RT, 32, 32>, qp.nlong[1], base2, qp.cursor.p + 2);
 }
 
+void queue_enqueue_f32(const Ctx &c, QueuePlan &qp, StateDev &st) {
+    const int64_t base1 = qp.nitems, base2 = qp.nitems + qp.nlong[0];
+    auto go = [&](auto kern, int n, int64_t base, unsigned *cur) {
+        if (n == 0) return;
+        const int grid = (int)std::min<int64_t>(ceil_div(n, FW_THREADS / 32), (int64_t)c.num_sms * 4);
+        kern<<<grid, FW_THREADS, 0, c.stream>>>(qp.groups.p, qp.items.p + base, n, cur, st.r32.p,
+                                                st.a32.p, st.a32c.p, st.dev_t.p, st.err.p);
+        KDSS_LAUNCH_CHECK();
+    };
+    if (qp.tpp == 8) go(k_pb_queue_long_f32<8, 32>, qp.nlong[0], base1, qp.cursor.p + 1);
+    else go(k_pb_queue_long_f32<32, 8>, qp.nlong[0], base1, qp.cursor.p + 1);
+    go(k_pb_queue_long_f32<32, 32>, qp.nlong[1], base2, qp.cursor.p + 2);
+    if (qp.nitems == 0) return;
+    const int grid = (int)std::min<int64_t>(ceil_div(qp.nitems, QW), (int64_t)c.num_sms * 6);
+    k_pb_queue_f32<<<grid, QW * 32, 0, c.stream>>>(qp.groups.p, qp.items.p, qp.nitems, qp.cursor.p,
+                                                    st.r32.p, st.a32.p, st.a32c.p, st.dev_t.p,
+                                                    st.err.p);
+    KDSS_LAUNCH_CHECK();
+}
+
 void queue_enqueue(const Ctx &c, QueuePlan &qp, StateDev &st) {
     if (qp.nitems + qp.nlong[0] + qp.nlong[1] == 0) return;
-    if (st.precision != KDSS_FP64 && st.precision != KDSS_INT64)
-        fail(KDSS_ERR_UNSUPPORTED, "work-queue iterations: integer rule only");
     KDSS_CUDA(cudaMemsetAsync(qp.cursor.p, 0, 3 * sizeof(unsigned), c.stream));
+    if (st.precision == KDSS_FP32K) {
+        queue_enqueue_f32(c, qp, st);
+        return;
+    }
     if (st.precision == KDSS_FP64)
         queue_launch_long<double>(c, qp, st, (double *)st.r.p, (double *)st.acc.p);
     else

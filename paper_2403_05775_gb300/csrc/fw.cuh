@@ -13,6 +13,7 @@ struct QGroup {
     const int32_t *nodes;
     const uint8_t *h;
     const uint64_t *binom;
+    const float *binomf;
     int bcols, k;
     int64_t node_off;     // its slice of the shared state
     int64_t short_end;    // pairs [0, short_end) have at most 32 nodes
@@ -58,6 +59,7 @@ struct StateDev {
     kdss_timing timing{};
     Ctx ctx;
     int qchunk = 0, qtpp = 32;       // > 0: integer-rule passes on the work-queue kernels
+    bool force_rooted = false;       // the root-shared first step whatever the SCT's size
     QueuePlan qplan;                 // their plan, bound like the graphs to one SCT
     // one FW iteration as CUDA graphs, bound to the SCT they were captured for
     const SctDev *graph_sct = nullptr;

@@ -135,6 +135,8 @@ struct PassOut {
     int64_t *pair_off;
     int32_t *nodes;
     uint8_t *h;
+    uint16_t *lidx;                  // root-shared form (EMIT)
+    int32_t *proot;
     CountTotals *tot;                // (TOTAL)
     unsigned long long perm_mul;     // root of item i: (i * perm_mul) mod n (TOTAL)
     unsigned long long budget_ns;    // each warp stops this long after it started (TOTAL)
@@ -363,10 +365,15 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
                                 int pos = 0;
                                 for (int u = 0; u < len; ++u) pos += ((ids[u] & 0x7fffffff) < my) ? 1 : 0;
                                 po.nodes[noff + pos] = raw;
+                                // the same node as an index into the root's
+                                // neighbourhood (0 = the root), V_h mark in bit 15
+                                const int li = t < h ? hold[t] : piv[t - h];
+                                po.lidx[noff + pos] = (uint16_t)((li < 0 ? 0 : li + 1) | (t < h ? 0x8000 : 0));
                             }
                             if (lane == 0) {
                                 po.pair_off[pidx] = noff;
                                 po.h[pidx] = (uint8_t)h;
+                                po.proot[pidx] = (int32_t)root;
                             }
                             __syncwarp();
                         }
@@ -652,6 +659,42 @@ void check_ck_range(int cbits, int64_t npairs) {
 
 }  // namespace
 
+namespace {
+// rnb_off[v] = out_off[v] + v; entry 0 of v's list is v's id, entry j + 1 the
+// id of its j-th out-neighbour (rank space -> original ids).
+__global__ void k_rnb(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_adj,
+                      const int32_t *__restrict__ vert, int64_t *rnb_off, int32_t *rnb_ids) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nw) {
+        const int64_t b = out_off[v], e = out_off[v + 1], o = b + v;
+        if (lane == 0) {
+            rnb_off[v] = o;
+            rnb_ids[o] = vert[v];
+            if (v == n - 1) rnb_off[n] = e + n;
+        }
+        for (int64_t j = b + lane; j < e; j += 32) rnb_ids[o + 1 + (j - b)] = vert[out_adj[j]];
+    }
+}
+}  // namespace
+
+void build_root_neighbourhoods(const Ctx &c, const GraphDev &g, SctDev &out) {
+    const int64_t n = g.n;
+    int64_t m1 = 0;
+    if (n > 0) to_host(c, &m1, g.out_off.p + n, 1);
+    out.rnb_off = DBuf<int64_t>(c, (size_t)n + 1);
+    out.rnb_ids = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n + m1, 1));
+    if (n > 0) {
+        const int B = 256;
+        k_rnb<<<grid_for(c, n * 32, B), B, 0, c.stream>>>(n, g.out_off.p, g.out_adj.p, g.vert.p,
+                                                          out.rnb_off.p, out.rnb_ids.p);
+        KDSS_LAUNCH_CHECK();
+    } else {
+        zero(c, out.rnb_off.p, sizeof(int64_t));
+    }
+}
+
 void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo, int64_t root_lo,
                int64_t root_hi) {
     if (klo < 0) klo = k;
@@ -832,6 +875,9 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo, int
     out.pair_off = DBuf<int64_t>(c, (size_t)(npairs + 1));
     out.nodes = DBuf<int32_t>(c, (size_t)std::max<int64_t>(nnodes, 1) + NODES_PAD);
     out.h = DBuf<uint8_t>(c, (size_t)std::max<int64_t>(npairs, 1));
+    out.proot = DBuf<int32_t>(c, (size_t)std::max<int64_t>(npairs, 1));
+    out.lidx = DBuf<uint16_t>(c, (size_t)std::max<int64_t>(nnodes, 1) + NODES_PAD);
+    build_root_neighbourhoods(c, g, out);
     if (npairs > 0) {
         // per-level slices of the class-major offsets
         int64_t b = 0;
@@ -847,6 +893,7 @@ void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo, int
             PassOut pe{};
             pe.baseP = lp.p; pe.baseN = ln.p;
             pe.pair_off = out.pair_off.p; pe.nodes = out.nodes.p; pe.h = out.h.p;
+            pe.lidx = out.lidx.p; pe.proot = out.proot.p;
             launch(k_sct<MODE_EMIT, 1>, L, pe);
             b += L.nitems;
         }

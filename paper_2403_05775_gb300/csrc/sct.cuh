@@ -39,6 +39,17 @@ struct SctDev {
     uint64_t ck_lo = 0, ck_hi = 0;
     int max_len = 0;
     int bcols() const { return k + 1; }   // columns of the binomial tables
+    // Root-shared form of the same pairs (SCTs built here): every pair comes
+    // from the recursion of one root, whose out-neighbourhood holds all its
+    // nodes.  proot[q] is that root (rank); lidx[i] is node i of the pair as
+    // an index into the root's neighbourhood list rnb_ids[rnb_off[root] ..]
+    // (0 = the root itself, j + 1 = its j-th out-neighbour), bit 15 the V_h
+    // mark, in the same slots as `nodes`.
+    DBuf<int32_t> proot;          // [npairs]
+    DBuf<uint16_t> lidx;          // [nnodes + NODES_PAD]
+    DBuf<int64_t> rnb_off;        // [n + 1]
+    DBuf<int32_t> rnb_ids;        // [n + out-edges] original ids
+    bool rooted() const { return proot.p != nullptr; }
 };
 
 // Host tables of C(a, b) for a < rows, b <= k: in 64 bits (entries that need
@@ -51,13 +62,16 @@ struct BinomTables {
 };
 BinomTables host_binom_tables(int rows, int k);
 std::vector<uint64_t> host_binom_table(int rows, int k);
-// Bytes of the three device tables of an SCT.
+// Bytes of an SCT's device tables and of its root-shared form.
 inline int64_t binom_bytes(const SctDev &s) {
-    return (int64_t)(s.binom.bytes() + s.binom128.bytes() + s.binomf.bytes());
+    return (int64_t)(s.binom.bytes() + s.binom128.bytes() + s.binomf.bytes() + s.proot.bytes() +
+                     s.lidx.bytes() + s.rnb_off.bytes() + s.rnb_ids.bytes());
 }
 
 // klo < k: the k-agnostic form -- every pair with |V_h| <= k and at least
 // klo nodes (the pruning of Lemma 2.5 for the sizes klo..k at once).
+// The root-shared neighbourhood lists of every root (SctDev::rnb_*).
+void build_root_neighbourhoods(const Ctx &c, const GraphDev &g, SctDev &out);
 // root_lo / root_hi: only the pairs of the roots [root_lo, root_hi) in the
 // build order (rank space); the default is every root.
 void build_sct(const Ctx &c, const GraphDev &g, int k, SctDev &out, int klo = -1,

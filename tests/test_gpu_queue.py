@@ -96,3 +96,35 @@ def test_batch_through_the_queue_equals_solve_and_reports_tuning():
     assert (t2["chunk"], t2["threads_per_path"], t2["autotuned"]) == (2, 8, False)
     for a, b in zip(out, fixed):
         assert (a["istar"], a["count"]) == (b["istar"], b["count"])
+
+
+@pytest.mark.parametrize("name", ["chunglu3k", "long80", "long300"])
+def test_fp32_queue_iterations_match_the_fp64_oracle(name):
+    """The continuous rule on the work queue: one iteration from zero and four
+    iterations agree with the FP64 oracle within 1e-5 (relative, inf-norm),
+    for every item size and lanes-per-pair choice."""
+    n, s, d = GRAPHS[name]()
+    k = 4
+    off, adj = O.csr(n, s, d)
+    core, rnd, _ = O.peel(n, off, adj)
+    rank, vert = O.order(n, core, rnd)
+    sc = O.sct(n, off, adj, rank, vert, k)
+    sct = K.kdss_build_sct(n, s, d, k)
+    for T in (1, 4):
+        want = O.fw_cont(n, sc, k, T) / T
+        for chunk, tpp in ((1, 32), (4, 8), (16, 32)):
+            o = K.make_opts(precision=K.KDSS_FP32K, chunk=chunk, threads_per_path=tpp)
+            got, t = K.kdss_state_copy_r(K.kdss_fw_iterate(sct, None, T, o), n, K.KDSS_FP32K)
+            assert t == T
+            err = np.max(np.abs(got.astype(np.float64) - want)) / np.max(np.abs(want))
+            assert err <= 1e-5, (T, chunk, tpp, err)
+
+
+def test_fp32_batch_through_the_queue_matches_the_oracle_density():
+    qs = [(*synth.batch_rmat_graph(i, nn), 3 + i, 40) for i, nn in enumerate([900, 1700, 2600])]
+    out = K.kdss_solve_batch(qs, K.make_opts(precision=K.KDSS_FP32K))
+    assert K.kdss_batch_last_tuning()["autotuned"]
+    for q, res in zip(qs, out):
+        want = O.solve(*q)
+        assert res["status"] == 0
+        assert abs(res["density"] - want["density"]) <= 0.01 * want["density"]
