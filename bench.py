@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0,
                     help="integer-rule iterations on the work-queue kernels with this many tiles "
                          "per item (0: the per-class kernels)")
+    ap.add_argument("--per-iteration", action="store_true",
+                    help="integer-rule iterations as launches per iteration, not one resident "
+                         "launch")
     return ap.parse_args()
 
 
@@ -775,9 +778,11 @@ def main():
     dst = torch.from_numpy(d_np).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    base_flags = K.KDSS_FLAG_PER_ITERATION if args.per_iteration else 0
+
     def step(flags):
-        o = K.make_opts(precision=prec, flags=flags, stream=stream, allocator=args.allocator,
-                        chunk=args.chunk)
+        o = K.make_opts(precision=prec, flags=flags | base_flags, stream=stream,
+                        allocator=args.allocator, chunk=args.chunk)
         sct = K.kdss_build_sct(n, src, dst, k, o)
         st = K.kdss_fw_iterate(sct, None, T, o)
         res = K.kdss_extract(sct, st, o)
@@ -826,7 +831,7 @@ def main():
         t0 = time.perf_counter()
         r2 = K.kdss_solve(n, s_np, d_np, k, T, K.make_opts(precision=prec, stream=stream,
                                                            allocator=args.allocator,
-                                                           chunk=args.chunk))
+                                                           chunk=args.chunk, flags=base_flags))
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_value = T * ck * world / (statistics.mean(e2e_ms) / 1e3)
@@ -838,6 +843,9 @@ def main():
     l2_gbs = l2_copy_gbs(torch, dev)
     alg_bytes = 4 * info["L_k"] + 9 * info["eta_k"]
     avg_s = (fw_ms / max(fw_launches, 1)) / 1e3
+    # the resident launch counts every iteration it runs; the per-iteration
+    # path times every 8th PBUpdate pass
+    resident = fw_launches == T * args.steps and not args.chunk
     achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
     traffic = ncu_traffic(os.path.join(ROOT, "paper_2403_05775_gb300", "csrc", "fw.cu"))
 
@@ -853,6 +861,7 @@ def main():
                    "l2": "flushed by a 256 MiB write before every step",
                    "allocator": args.allocator,
                    "pbupdate_kernels": (f"work queue, {args.chunk} tiles per item" if args.chunk
+                                        else "resident launch, T iterations" if resident
                                         else "per length class"),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -864,6 +873,9 @@ def main():
                             "peak_gbs": l2_gbs, "frac": achieved / l2_gbs if l2_gbs else None},
                      "kernel": ("PBUpdate pass of one FW iteration (k_pb_queue + k_pb_queue_long)"
                                 if args.chunk else
+                                "one FW iteration of the resident launch k_fw_resident (gather of "
+                                "r, PBUpdate of every pair, fold of the delta, grid barrier); "
+                                "launch time / T" if resident else
                                 "PBUpdate pass of one FW iteration (k_pb_fast + k_pb_slow + "
                                 "length-class group kernels)"),
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,

@@ -76,6 +76,16 @@ typedef int32_t kdss_status;
  * gathered once per tile) whatever the SCT's size; by default it is used only
  * when the SCT's node stream exceeds 96 MiB (beyond L2). */
 #define KDSS_FLAG_ROOTED 16u
+/* Integer-rule iterations as launches per iteration (CUDA graphs of the
+ * PBUpdate kernels and the step) even where the resident launch applies.  By
+ * default, when every pair of the SCT has at most 32 nodes and the pairs fit
+ * the blocks' shared memory (one block per SM, 12 bytes per pair node: about
+ * 18,000 pair nodes per SM), kdss_fw_iterate runs all T iterations in one
+ * cooperative launch that keeps the pair stream in shared memory and ends
+ * each iteration on a bounded grid barrier.  Both forms give the same r bit
+ * for bit; with KDSS_FLAG_PROFILE the resident launch is timed as a whole and
+ * kdss_timing counts it as T PBUpdate passes with the step inside. */
+#define KDSS_FLAG_PER_ITERATION 32u
 
 typedef void *(*kdss_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*kdss_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
@@ -146,7 +156,8 @@ typedef struct kdss_result {
 typedef struct kdss_timing {
     double fw_kernel_ms;    /* summed event time of the timed PBUpdate passes */
     double step_kernel_ms;  /* summed event time of the timed step kernels */
-    int64_t fw_launches;    /* PBUpdate passes timed (every 8th iteration) */
+    int64_t fw_launches;    /* PBUpdate passes timed (every 8th iteration; every iteration of
+                               a resident launch, whose time includes its steps) */
     int64_t step_launches;
 } kdss_timing;
 

@@ -40,6 +40,7 @@ KDSS_FLAG_KEEP_GRAPH = 2
 KDSS_FLAG_ASYNC = 4
 KDSS_FLAG_TEST_BARRIER_TIMEOUT = 8
 KDSS_FLAG_ROOTED = 16
+KDSS_FLAG_PER_ITERATION = 32
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

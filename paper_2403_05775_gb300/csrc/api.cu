@@ -350,6 +350,7 @@ kdss_status fw_iterate_impl(kdss_sct *s, int32_t k, kdss_state **state, int32_t 
         created = true;
     }
     if ((*state)->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
+    (*state)->st.per_iteration = opts && (opts->flags & KDSS_FLAG_PER_ITERATION);
     try {
         if (opts && (opts->flags & KDSS_FLAG_ASYNC))
             fw_run_async(c, s->s, (*state)->st, T);

@@ -1892,9 +1892,539 @@ void launch_pbupdate_f32(const Ctx &c, const SctDev &s, StateDev &st) {
     launch_pbupdate_f32_on(c, s, st.k, st, st.r32.p, st.a32.p, st.a32c.p);
 }
 
+// ---------------------------------------------------------------------------
+// Resident iterations (rule I): all T iterations of Alg. 2 in one cooperative
+// launch, one block per SM.  The pairs (all of at most 32 nodes) are dealt
+// round-robin: pair q goes to block q mod G.  The pairs that need the full
+// walk cluster (the roots of a dense region sit next to each other in the
+// pair order), and dealing single pairs gives every block an even sample of
+// them; contiguous ranges or dealt tiles leave some blocks with far more
+// walks than others, and every iteration waits for the slowest block.
+//
+// A planning kernel gives every block's share its distinct nodes: a hash
+// table in shared memory maps each node id to a local index, every pair node
+// is rewritten as a 16-bit local index (V_h mark in bit 15), and every pair
+// gets its offset in the block's local node list.  The resident kernel copies
+// the local indices, offsets and h of its pairs into shared memory once.  An
+// iteration then gathers r once per distinct node of the block (the SCT's
+// pairs crowd on few nodes: on a 1e5-node power-law graph with a planted
+// near-clique the ~16,000 pair nodes of a block name ~200 distinct nodes),
+// runs the first step of Alg. 3 over the block's pairs 32 at a time, appends
+// the pairs it leaves to a block list, walks that list one pair per warp, and
+// adds every allocation into a shared-memory accumulator per distinct node,
+// which is flushed with one global atomic per node.
+//
+// One grid barrier per iteration.  r lives in two copies R[0], R[1] and the
+// per-iteration delta in three vectors A[0..2].  Iteration j (0-based) reads
+// r_j = R[j%2] + A[(j+2)%3] (the previous delta, not yet folded), adds its
+// allocation into A[j%3], and meanwhile every block writes its own node slice
+// of R[(j+1)%2] = R[j%2] + A[(j+2)%3] and clears its slice of A[(j+1)%3].
+// In iteration j nobody reads R[(j+1)%2] or A[(j+1)%3] (last read in
+// iteration j-1) and nobody reads A[j%3] (cleared in iteration j-1, read in
+// iteration j+1), so the barrier that ends iteration j is the only ordering
+// the buffers need.  After the last iteration each block folds its slice
+// into R[0] and clears the deltas, which leaves the state as the per-iteration
+// launches do: r_T in R[0], the deltas zero.
+// ---------------------------------------------------------------------------
+constexpr int RS_WARPS = 32;
+constexpr int RS_UCAP = 6144;    // distinct nodes per block share at most
+constexpr int RS_HS = 8192;      // hash slots of the planning kernel
+
+struct ResidentArgs {
+    const int64_t *pair_off;
+    const uint16_t *lidx;    // [nnodes] local index of every pair node in its block
+    const uint16_t *loff;    // [npairs] offset of every pair in its block's node list
+    const int32_t *uid;      // [G * RS_UCAP] distinct nodes of each block
+    const int *plan;         // [2G] distinct nodes, then pair nodes, of each block
+    const uint8_t *h;
+    int64_t npairs;
+    const uint64_t *binom;
+    int bcols, k;
+    int64_t n;
+    uint64_t *R[2];
+    uint64_t *A[3];
+    unsigned long long *maxr;
+    int *err;
+    GridBarrier *bar;
+    uint64_t timeout_ns;
+    int T;
+    int ncap, pcap, ucap;    // pair nodes, pairs and distinct nodes of the largest share
+};
+
+// Sum of two r words (uint64, or the bits of doubles holding integers).
+template <class RT>
+__device__ __forceinline__ uint64_t rword_add(uint64_t a, uint64_t b);
+template <>
+__device__ __forceinline__ uint64_t rword_add<uint64_t>(uint64_t a, uint64_t b) { return a + b; }
+template <>
+__device__ __forceinline__ uint64_t rword_add<double>(uint64_t a, uint64_t b) {
+    return (uint64_t)__double_as_longlong(__longlong_as_double((long long)a) +
+                                          __longlong_as_double((long long)b));
+}
+
+// walk scratch; r words, accumulators and ids of the distinct nodes; local
+// indices; local pair offsets; the walk list; h
+size_t resident_smem_bytes(int ncap, int pcap, int ucap) {
+    size_t b = (size_t)RS_WARPS * 64 * sizeof(uint64_t);
+    b += (size_t)ucap * (2 * sizeof(uint64_t) + sizeof(int32_t));
+    b += (size_t)ncap * sizeof(uint16_t);
+    b += (size_t)(pcap + 1) * sizeof(uint16_t) + (size_t)pcap * sizeof(uint16_t) + (size_t)pcap;
+    return (b + 15) & ~(size_t)15;
+}
+
+// Pairs of block b's share: b, b + G, b + 2G, ... below npairs.
+__host__ __device__ __forceinline__ int64_t resident_share_pairs(int64_t npairs, int G, int b) {
+    return (int64_t)b < npairs ? (npairs - 1 - b) / G + 1 : 0;
+}
+
+__device__ __forceinline__ unsigned resident_hash(int32_t id) {
+    return ((uint32_t)id * 2654435761u) >> (32 - 13);   // RS_HS = 2^13 slots
+}
+
+constexpr size_t RS_PLAN_SMEM = 2 * RS_HS * sizeof(int32_t);
+
+// Planning: for every block's share, the offset of each pair in the share's
+// node list (an exclusive scan of the pair lengths, 1024 pairs at a time),
+// the distinct nodes, and the local index of every pair node.  plan[b] =
+// distinct nodes (RS_UCAP + 1 when the share has more than a block can hold),
+// plan[G + b] = pair nodes of the share.
+__global__ void __launch_bounds__(1024)
+k_resident_plan(const int64_t *__restrict__ pair_off, const int32_t *__restrict__ nodes,
+                int64_t npairs, uint16_t *lidx, uint16_t *loff, int32_t *uid, int *plan) {
+    extern __shared__ int32_t rp_smem[];   // RS_HS keys, then RS_HS local indices
+    __shared__ int s_nu, s_full, s_run;
+    __shared__ int s_wsum[32];
+    int32_t *hk = rp_smem, *hv = rp_smem + RS_HS;
+    volatile int32_t *vk = hk;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < RS_HS; i += blockDim.x) hk[i] = -1;
+    if (threadIdx.x == 0) {
+        s_nu = 0;
+        s_full = 0;
+        s_run = 0;
+    }
+    __syncthreads();
+    const int G = gridDim.x;
+    const int64_t np = resident_share_pairs(npairs, G, blockIdx.x);
+    int32_t *myuid = uid + (size_t)blockIdx.x * RS_UCAP;
+    for (int64_t c0 = 0; c0 < np; c0 += blockDim.x) {   // uniform trip count
+        const int64_t j = c0 + threadIdx.x;
+        int len = 0;
+        int64_t e0 = 0;
+        if (j < np) {
+            const int64_t q = blockIdx.x + j * G;
+            e0 = pair_off[q];
+            len = (int)(pair_off[q + 1] - e0);
+        }
+        // exclusive scan of len over the block
+        int x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[wib] = x;
+        __syncthreads();
+        if (wib == 0) {
+            int t = lane < nwarp ? s_wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            s_wsum[lane] = t;   // inclusive warp totals
+        }
+        __syncthreads();
+        const int excl = s_run + (wib ? s_wsum[wib - 1] : 0) + x - len;
+        if (j < np) loff[blockIdx.x + j * G] = (uint16_t)excl;   // shares above 65535 nodes are refused
+        __syncthreads();
+        if (threadIdx.x == 0) s_run += s_wsum[nwarp - 1];
+        // this pair's nodes into the hash table (linear probing, at most every slot)
+        for (int y = 0; y < len; ++y) {
+            const int32_t id = nodes[e0 + y] & 0x7fffffff;
+            unsigned slot = resident_hash(id);
+            bool placed = false;
+            for (int p = 0; p < RS_HS; ++p) {
+                int32_t cur = vk[slot];
+                if (cur == -1) {
+                    cur = atomicCAS(&hk[slot], -1, id);
+                    if (cur == -1) {   // this thread placed id: give it the next index
+                        const int li = atomicAdd(&s_nu, 1);
+                        if (li < RS_UCAP) {
+                            hv[slot] = li;
+                            myuid[li] = id;
+                        }
+                        placed = true;
+                        break;
+                    }
+                }
+                if (cur == id) {
+                    placed = true;
+                    break;
+                }
+                slot = (slot + 1) & (RS_HS - 1);
+            }
+            if (!placed) s_full = 1;
+        }
+        __syncthreads();
+    }
+    // every pair node as its local index
+    for (int64_t j = threadIdx.x; j < np; j += blockDim.x) {
+        const int64_t q = blockIdx.x + j * G;
+        const int64_t e0 = pair_off[q], e1 = pair_off[q + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const int32_t raw = nodes[e];
+            const int32_t id = raw & 0x7fffffff;
+            unsigned slot = resident_hash(id);
+            int li = RS_UCAP;
+            for (int p = 0; p < RS_HS; ++p) {
+                const int32_t cur = hk[slot];
+                if (cur == id) {
+                    li = hv[slot];
+                    break;
+                }
+                if (cur == -1) break;
+                slot = (slot + 1) & (RS_HS - 1);
+            }
+            if (li >= RS_UCAP) s_full = 1;
+            lidx[e] = (uint16_t)((li & 0x7fff) | (raw < 0 ? 0x8000 : 0));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        plan[blockIdx.x] = (s_full || s_nu > RS_UCAP) ? RS_UCAP + 1 : s_nu;
+        plan[G + blockIdx.x] = s_run;
+    }
+}
+
+template <class RT>
+__global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    __shared__ int s_cursor, s_nslow, s_wcur;
+    // the block accumulates in integers (every allocation is an integer
+    // below 2^53, and 64-bit integer adds are native shared-memory atomics)
+    // and converts once per node when it flushes
+    using AV = unsigned long long;
+    using GV = typename AccV<RT>::T;
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint64_t *wsr = reinterpret_cast<uint64_t *>(rs_smem) + wib * 64;
+    uint64_t *wsc = wsr + 32;
+    uint64_t *sval = reinterpret_cast<uint64_t *>(rs_smem) + RS_WARPS * 64;
+    AV *sacc = reinterpret_cast<AV *>(sval + a.ucap);
+    int32_t *suid = reinterpret_cast<int32_t *>(sacc + a.ucap);
+    uint16_t *slid = reinterpret_cast<uint16_t *>(suid + a.ucap);
+    uint16_t *poff = slid + a.ncap;
+    uint16_t *slist = poff + a.pcap + 1;
+    uint8_t *hh = reinterpret_cast<uint8_t *>(slist + a.pcap);
+    const int G = gridDim.x;
+    // this block's distinct nodes, then its pairs b, b + G, ... with their
+    // nodes as local indices
+    int np = (int)resident_share_pairs(a.npairs, G, blockIdx.x);
+    int nu = a.plan[blockIdx.x], nn = a.plan[G + blockIdx.x];
+    if (np > a.pcap || nn > a.ncap || nu > a.ucap) {
+        // the host sized the shares; a mismatch skips the work but keeps the
+        // barriers, so that no other block waits for this one
+        if (threadIdx.x == 0) atomicOr(a.err, DERR_CAPACITY);
+        nu = 0;
+        nn = 0;
+        np = 0;
+    }
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) suid[i] = a.uid[(size_t)blockIdx.x * RS_UCAP + i];
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int64_t q = blockIdx.x + (int64_t)j * G;
+        const int64_t e0 = a.pair_off[q];
+        const int len = (int)(a.pair_off[q + 1] - e0);
+        const int o = a.loff[q];
+        poff[j] = (uint16_t)o;
+        hh[j] = a.h[q];
+        if (o + len <= nn)
+            for (int x = 0; x < len; ++x) slid[o + x] = a.lidx[e0 + x];
+    }
+    if (threadIdx.x == 0) poff[np] = (uint16_t)nn;
+    __syncthreads();
+    const int64_t v0 = a.n * blockIdx.x / G, v1 = a.n * (blockIdx.x + 1) / G;
+    const int ntile = (np + 31) >> 5;
+    const int k = a.k, bcols = a.bcols;
+    for (int j = 0; j < a.T; ++j) {
+        const uint64_t *Rc = a.R[j & 1];
+        uint64_t *Rn = a.R[(j + 1) & 1];
+        const uint64_t *Ap = a.A[(j + 2) % 3];
+        uint64_t *Az = a.A[(j + 1) % 3];
+        GV *gacc = reinterpret_cast<GV *>(a.A[j % 3]);
+        if (threadIdx.x == 0) {
+            s_cursor = 0;
+            s_nslow = 0;
+            s_wcur = 0;
+        }
+        // r_j of the block's distinct nodes (L2 reads: other blocks wrote them)
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+            const int32_t u = suid[i];
+            sval[i] = rword_add<RT>(__ldcg(Rc + u), __ldcg(Ap + u));
+            sacc[i] = AV(0);
+        }
+        // fold the previous delta into the other copy of r, clear the
+        // delta that iteration j + 1 adds into
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            __stcg(Rn + v, rword_add<RT>(__ldcg(Rc + v), __ldcg(Ap + v)));
+            __stcg(Az + v, 0ull);
+        }
+        __syncthreads();
+        // first step of every pair; the pairs it leaves go to the block list
+        while (true) {
+            int ti = 0;
+            if (lane == 0) ti = atomicAdd(&s_cursor, 1);
+            ti = __shfl_sync(FULL_, ti, 0);
+            if (ti >= ntile) break;
+            const int qi = ti * 32 + lane;
+            const bool valid = qi < np;
+            const int o = valid ? poff[qi] : 0;
+            const int len = valid ? (int)poff[qi + 1] - o : 0;
+            const int h = valid ? (int)hh[qi] : 0;
+            uint32_t rmask = 0;
+            bool want_slow = false;
+            uint64_t w = 0, R = 0;
+            if (valid && h <= k && k <= len && len <= 32) {
+                const int p = len - h;
+                const uint64_t nC = __ldg(a.binom + (size_t)p * bcols + (k - h));
+                const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                                           ? __ldg(a.binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
+                const uint64_t pm = cap_p > 0 ? 0ull : ~0ull;
+                uint64_t m1 = ~0ull, m2 = ~0ull;
+                uint32_t mask1 = 0;
+                bool piv1 = false;
+                for (int s2 = 0; s2 < len; ++s2) {
+                    const unsigned l = slid[o + s2];
+                    const bool hold = (l & 0x8000u) != 0;
+                    const uint64_t v = sval[l & 0x7fffu] | (hold ? 0ull : pm);
+                    const bool lt = v < m1;
+                    const bool eq = v == m1 && v != ~0ull;
+                    const uint64_t mn = v < m2 ? v : m2;
+                    m2 = lt ? m1 : (eq ? m2 : mn);
+                    m1 = lt ? v : m1;
+                    const uint32_t bit = 1u << s2;
+                    mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                    piv1 = lt ? !hold : (piv1 || (eq && !hold));
+                }
+                if (mask1) {
+                    const uint64_t na = (uint64_t)__popc(mask1);
+                    const uint64_t mu = piv1 ? cap_p : nC;
+                    const uint64_t gap = m2 == ~0ull ? ~0ull : level_of<RT>(m2) - level_of<RT>(m1);
+                    w = nC / na;
+                    R = nC - w * na;
+                    const uint64_t lim = mu < gap ? mu : gap;
+                    if (!(R == 0 ? w > lim : w >= lim)) rmask = mask1;
+                    else want_slow = true;
+                }
+            } else if (valid && len > 32) {
+                atomicOr(a.err, DERR_CAPACITY);
+            }
+            const unsigned um = __ballot_sync(FULL_, want_slow);
+            if (um) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_nslow, __popc(um));
+                base = __shfl_sync(FULL_, base, 0);
+                if (want_slow) slist[base + __popc(um & lanemask_lt())] = (uint16_t)qi;
+            }
+            uint64_t rank = 0;
+            while (__any_sync(FULL_, rmask != 0)) {
+                int32_t rid = -1;
+                AV amount = AV(0);
+                if (rmask) {
+                    const int sl = __ffs(rmask) - 1;
+                    rmask &= rmask - 1;
+                    const uint64_t dl = w + (rank < R ? 1ull : 0ull);
+                    ++rank;
+                    if (dl) {
+                        rid = (int32_t)(slid[o + sl] & 0x7fffu);
+                        amount = (AV)dl;
+                    }
+                }
+                warp_seg_add<AV>(rid, amount, sacc);
+            }
+        }
+        __syncthreads();
+        // the walks of the block list, one pair per warp at a time
+        const int nslow = s_nslow;
+        while (true) {
+            int wi = 0;
+            if (lane == 0) wi = atomicAdd(&s_wcur, 1);
+            wi = __shfl_sync(FULL_, wi, 0);
+            if (wi >= nslow) break;
+            const int q = slist[wi];
+            const int so = poff[q];
+            const int sl = (int)poff[q + 1] - so;
+            int32_t rawc = 0;
+            uint64_t rjc = 0;
+            if (lane < sl) {
+                const unsigned l = slid[so + lane];
+                rawc = (int32_t)(l & 0x7fffu) | ((l & 0x8000u) ? (int32_t)0x80000000 : 0);
+                rjc = level_of<RT>(sval[l & 0x7fffu]);
+            }
+            slow_pair_walk<AV>(sl, (int)hh[q], rawc, rjc, k, a.binom, bcols, sacc, wsr, wsc, a.err);
+        }
+        __syncthreads();
+        // one global add per distinct node that received units
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+            const AV x = sacc[i];
+            if (x != AV(0)) atomicAdd(gacc + suid[i], (GV)x);
+        }
+        if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
+    }
+    // r_T = R[T%2] + A[(T+2)%3] into R[0]; clear the two deltas still set
+    const uint64_t *Rc = a.R[a.T & 1];
+    uint64_t *Al = a.A[(a.T + 2) % 3], *Ao = a.A[(a.T + 1) % 3];
+    unsigned long long m = 0;
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const uint64_t x = rword_add<RT>(__ldcg(Rc + v), __ldcg(Al + v));
+        a.R[0][v] = x;
+        Al[v] = 0;
+        Ao[v] = 0;
+        m = x > m ? x : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(FULL_, m, o);
+        m = t > m ? t : m;
+    }
+    if (lane == 0 && m) atomicMax(a.maxr, m);
+}
+
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
 };
+
+// Whether the resident launch can run the iterations of this state on s:
+// the integer rule, pairs of at most 32 nodes only, and the largest block
+// range within one block's shared memory.  Plans once per (state, SCT).
+bool resident_ready(const Ctx &c, const SctDev &s, StateDev &st) {
+    if (st.per_iteration || st.precision == KDSS_FP32K || st.qchunk > 0 || st.force_rooted)
+        return false;
+    if (s.npairs <= 0 || s.class_begin[0] != 0 || s.class_begin[3] != s.npairs) return false;
+    if (st.res_sct == &s) return st.res_state > 0;
+    st.res_sct = &s;
+    st.res_state = -1;
+    int coop = 0, optin = 0;
+    KDSS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.device));
+    KDSS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
+    if (!coop) return false;
+    const int G = c.num_sms;
+    // cheap rejects: the local indices of the average share, or the largest
+    // share's pairs, exceed what a block holds
+    if (s.nnodes * (int64_t)sizeof(uint16_t) > (int64_t)G * optin) return false;
+    const int64_t pcap = resident_share_pairs(s.npairs, G, 0);
+    if (pcap > 65535 || resident_smem_bytes(0, (int)pcap, 0) + 1024 > (size_t)optin) return false;
+    // distinct nodes of every share, local indices and offsets
+    DBuf<uint16_t> lidx(c, (size_t)std::max<int64_t>(s.nnodes, 1));
+    DBuf<uint16_t> loff(c, (size_t)s.npairs);
+    DBuf<int32_t> uid(c, (size_t)G * RS_UCAP);
+    DBuf<int> plan(c, (size_t)2 * G);
+    static thread_local int plan_attr_dev = -1;
+    if (plan_attr_dev != c.device) {
+        KDSS_CUDA(cudaFuncSetAttribute(k_resident_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)RS_PLAN_SMEM));
+        plan_attr_dev = c.device;
+    }
+    k_resident_plan<<<G, 1024, RS_PLAN_SMEM, c.stream>>>(s.pair_off.p, s.nodes.p, s.npairs, lidx.p,
+                                                         loff.p, uid.p, plan.p);
+    KDSS_LAUNCH_CHECK();
+    std::vector<int> hplan((size_t)2 * G);
+    to_host(c, hplan.data(), plan.p, (size_t)2 * G);
+    int ucap = 0, ncap = 0;
+    for (int b = 0; b < G; ++b) {
+        ucap = std::max(ucap, hplan[b]);
+        ncap = std::max(ncap, hplan[G + b]);
+    }
+    if (ucap > RS_UCAP || ncap > 65535) return false;
+    const size_t smem = resident_smem_bytes(ncap, (int)pcap, ucap);
+    if (smem + 1024 > (size_t)optin) return false;   // static shared memory and slack
+    auto kern = st.precision == KDSS_FP64 ? k_fw_resident<double> : k_fw_resident<uint64_t>;
+    KDSS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RS_WARPS * 32, smem));
+    if (per_sm < 1) return false;
+    st.res_lidx = std::move(lidx);
+    st.res_loff = std::move(loff);
+    st.res_uid = std::move(uid);
+    st.res_plan = std::move(plan);
+    st.res_ucap = ucap;
+    const size_t n = (size_t)std::max<int64_t>(s.n, 1);
+    st.res_r1 = DBuf<uint64_t>(c, n);
+    st.res_a1 = DBuf<uint64_t>(c, n);
+    st.res_a2 = DBuf<uint64_t>(c, n);
+    st.res_bar = DBuf<GridBarrier>(c, 1);
+    zero(c, st.res_a1.p, n * 8);
+    zero(c, st.res_a2.p, n * 8);
+    zero(c, st.res_bar.p, sizeof(GridBarrier));
+    st.res_ncap = ncap;
+    st.res_pcap = (int)pcap;
+    st.res_smem = smem;
+    st.res_state = 1;
+    return true;
+}
+
+// T iterations in one resident launch.  With `profile` the launch is timed
+// with events; the state's timing then counts it as T iterations (PBUpdate
+// and step together).
+void fw_run_resident(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
+    ResidentArgs a{};
+    a.pair_off = s.pair_off.p;
+    a.lidx = st.res_lidx.p;
+    a.loff = st.res_loff.p;
+    a.uid = st.res_uid.p;
+    a.plan = st.res_plan.p;
+    a.h = s.h.p;
+    a.npairs = s.npairs;
+    a.binom = s.binom.p;
+    a.bcols = s.bcols();
+    a.k = st.k;
+    a.n = s.n;
+    a.R[0] = st.r.p;
+    a.R[1] = st.res_r1.p;
+    a.A[0] = st.acc.p;
+    a.A[1] = st.res_a1.p;
+    a.A[2] = st.res_a2.p;
+    a.maxr = st.maxr.p;
+    a.err = st.err.p;
+    a.bar = st.res_bar.p;
+    a.timeout_ns = 20ull * 1000 * 1000 * 1000;   // 20 s per barrier wait
+    a.T = T;
+    a.ncap = st.res_ncap;
+    a.pcap = st.res_pcap;
+    a.ucap = st.res_ucap;
+    auto kern = st.precision == KDSS_FP64 ? k_fw_resident<double> : k_fw_resident<uint64_t>;
+    void *args[] = {&a};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profile) {
+        while (st.events.size() < 2) {
+            cudaEvent_t e;
+            KDSS_CUDA(cudaEventCreate(&e));
+            st.events.push_back(e);
+        }
+        e0 = st.events[0];
+        e1 = st.events[1];
+        KDSS_CUDA(cudaEventRecord(e0, c.stream));
+    }
+    KDSS_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(c.num_sms), dim3(RS_WARPS * 32),
+                                          args, st.res_smem, c.stream));
+    KDSS_LAUNCH_CHECK();
+    if (profile) KDSS_CUDA(cudaEventRecord(e1, c.stream));
+    st.t += T;
+    int herr = 0;
+    to_host(c, &herr, st.err.p, 1);
+    if (profile) {
+        float ms = 0.f;
+        KDSS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        st.timing.fw_kernel_ms += ms;
+        st.timing.fw_launches += T;
+    }
+    if (herr) {   // the barrier may be left mid-count: plan afresh next time
+        zero(c, st.res_bar.p, sizeof(GridBarrier));
+        st.res_sct = nullptr;
+        if (herr & DERR_TIMEOUT) fail(KDSS_ERR_TIMEOUT, "FW iteration: a grid barrier wait expired");
+        fail(KDSS_ERR_CUDA, "FW iteration: water-filling invariant failed on the device");
+    }
+}
 
 }  // namespace
 
@@ -2029,6 +2559,10 @@ void fw_run(const Ctx &c, const SctDev &s, StateDev &st, int T, bool profile) {
         const long double ck = (long double)st.ck_lo + (long double)st.ck_hi * 18446744073709551616.0L;
         if ((long double)(st.t + T) * ck >= lim)
             fail(KDSS_ERR_OVERFLOW, "T * c_k leaves the exact range of r");
+    }
+    if (resident_ready(c, s, st)) {
+        fw_run_resident(c, s, st, T, profile);
+        return;
     }
     // One iteration as CUDA graphs (PBUpdate, step, and both), captured once
     // per (state, SCT) and replayed T times on the caller's stream.

@@ -61,6 +61,20 @@ struct StateDev {
     int qchunk = 0, qtpp = 32;       // > 0: integer-rule passes on the work-queue kernels
     bool force_rooted = false;       // the root-shared first step whatever the SCT's size
     QueuePlan qplan;                 // their plan, bound like the graphs to one SCT
+    bool per_iteration = false;      // no resident launch: per-iteration kernels only
+    // resident iterations (all T in one cooperative launch): the second
+    // copy of r, the two extra delta vectors, the shares' local indices and
+    // distinct nodes, and the largest share, bound like the graphs to one SCT
+    const SctDev *res_sct = nullptr;
+    int res_state = 0;               // 1: usable for res_sct, -1: not usable
+    DBuf<uint64_t> res_r1, res_a1, res_a2;
+    DBuf<GridBarrier> res_bar;
+    DBuf<uint16_t> res_lidx;         // [nnodes] local index of every pair node in its share
+    DBuf<uint16_t> res_loff;         // [npairs] offset of every pair in its share's node list
+    DBuf<int32_t> res_uid;           // distinct nodes of every share
+    DBuf<int> res_plan;              // [2G] distinct nodes and pair nodes of every share
+    int res_ncap = 0, res_pcap = 0, res_ucap = 0;
+    size_t res_smem = 0;
     // one FW iteration as CUDA graphs, bound to the SCT they were captured for
     const SctDev *graph_sct = nullptr;
     cudaGraphExec_t g_iter = nullptr, g_pb = nullptr, g_step = nullptr;

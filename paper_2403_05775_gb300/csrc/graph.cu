@@ -68,38 +68,98 @@ __global__ void k_degrees(const int64_t *off, int64_t n, int32_t *deg, int32_t *
 struct PeelCtl {
     GridBarrier bar;
     int err;
-    int count[3];   // frontier sizes, rotating by round mod 3
+    int acnt[2];              // appends of the rounds of each parity (never reset)
+    int ltail;                // end of the peel order during a run of rounds in block 0
     unsigned int minval;
     int rounds;
     int degeneracy;
+    int pub_round, pub_start, pub_end;   // state after such a run
 };
 
 constexpr int PEEL_THREADS = 1024;
+// Frontiers of at most this many vertices are removed by block 0 alone, one
+// round after another with block barriers, while the other blocks wait at
+// the next grid barrier: most rounds of a power-law graph are a few vertices
+// at the end of a level, and there a round costs its chain of dependent
+// loads and atomics, not its work.
+constexpr int PEEL_SMALL = 128;
 
+// Remove the frontier cur[0, cnt): warps [warp0, warp0 + nwarps) take its
+// vertices; every neighbour loses one degree, and one that falls from
+// level + 1 to level joins the next round: it is written to the peel order
+// at position atomicAdd(counter, 1) + pos_off.  Neighbours already removed or
+// queued are decremented too: their degree is at most the level they were
+// taken at, which is at most `level`, so it never again equals level + 1, and
+// nothing reads it afterwards; skipping the check saves a dependent load of
+// rnd per neighbour.
+__device__ __forceinline__ void peel_remove(int cnt, int64_t warp0, int64_t nwarps,
+                                            const int32_t *cur, int32_t *order,
+                                            const int64_t *__restrict__ off,
+                                            const int32_t *__restrict__ adj, int32_t *deg,
+                                            int32_t *rnd, int32_t *core, int *counter,
+                                            int64_t pos_off, int64_t n, int level, int round) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = warp0; i < cnt; i += nwarps) {
+        const int32_t v = __ldcg(cur + i);
+        const int64_t e0 = off[v], e1 = off[v + 1];
+        // four neighbours per lane at a time: their loads and atomics are
+        // independent and overlap (hubs have thousands of neighbours)
+        for (int64_t e = e0 + lane; e < e1; e += 128) {
+            int32_t w[4];
+            int old[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t ee = e + 32 * u;
+                w[u] = ee < e1 ? adj[ee] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) old[u] = w[u] >= 0 ? atomicSub(deg + w[u], 1) : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (w[u] >= 0 && old[u] == level + 1) {
+                    rnd[w[u]] = round + 1;
+                    core[w[u]] = level;
+                    const int64_t idx = (int64_t)atomicAdd(counter, 1) + pos_off;
+                    if (idx >= 0 && idx < n) order[idx] = w[u];
+                }
+            }
+        }
+    }
+}
+
+// The frontiers are consecutive ranges of one array, the peel order: round r
+// removes order[S_r, S_{r+1}).  Round r appends through acnt[(r + 1) & 1] and
+// round r + 1 reads that counter to find its end, so no round's appends touch
+// the counter the same round reads (a late block may still be reading it
+// while others append), and no counter is ever reset.  Each block keeps the
+// value of each counter it last read; a counter changes only between two of
+// its reads, so the differences give the rounds' sizes.  A run of rounds in
+// block 0 appends through its own counter and leaves acnt untouched.
 __global__ void __launch_bounds__(PEEL_THREADS, 1)
 k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-       int32_t *deg, int32_t *rnd, int32_t *core, int32_t *fa, int32_t *fb, PeelCtl *ctl,
+       int32_t *deg, int32_t *rnd, int32_t *core, int32_t *order, PeelCtl *ctl,
        uint64_t timeout_ns, unsigned int phantom) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     // phantom > 0 (failure-injection test only): the barriers wait for blocks
     // that do not exist, so the first wait expires in every block
     const unsigned int nb = gridDim.x + phantom;
-    int32_t *cur = fa, *nxt = fb;
     int level = 0, round = 0;
-    int64_t removed = 0;
-    volatile int *vcount = ctl->count;
+    int64_t S = 0, E = 0;        // this round's frontier: order[S, E)
+    int last0 = 0, last1 = 0;    // acnt[0], acnt[1] as this block last read them
+    bool have_end = false;       // E already known (after a run in block 0)
+    volatile int *vacnt = ctl->acnt;
     while (true) {
-        // count[round % 3] is this round's frontier, count[(round + 1) % 3] the
-        // next one; count[(round + 2) % 3] was read by everyone before the
-        // barrier that ended the previous round and is next written after the
-        // barrier that ends this one, so it is reset here.
-        const int ci = round % 3, cn = (round + 1) % 3, cz = (round + 2) % 3;
-        if (tid == 0) ctl->count[cz] = 0;
-        int cnt = vcount[ci];
-        if (cnt > n) { if (tid == 0) atomicOr(&ctl->err, DERR_CAPACITY); return; }  // uniform
-        if (cnt == 0) {
-            if (removed >= n) break;
+        const int pr = round & 1;
+        if (!have_end) {
+            const int a = vacnt[pr];
+            E = S + (a - (pr ? last1 : last0));
+            if (pr) last1 = a; else last0 = a;
+        }
+        have_end = false;
+        if (E > n || E < S) { if (tid == 0) atomicOr(&ctl->err, DERR_CAPACITY); return; }  // uniform
+        if (E == S) {
+            if (S >= n) break;
             // smallest remaining degree
             unsigned int mn = 0xffffffffu;
             for (int64_t v = tid; v < n; v += nth)
@@ -120,59 +180,68 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
                 return;
             }
             if ((int)mv > level) level = (int)mv;
+            // the new level's first frontier, through acnt[pr] (everyone read
+            // it before the barrier above)
+            const int64_t base = S - (pr ? last1 : last0);
             for (int64_t v = tid; v < n; v += nth)
                 if (__ldcg(rnd + v) < 0 && __ldcg(deg + v) <= level) {
-                    int idx = atomicAdd(&ctl->count[ci], 1);
-                    if (idx < n) cur[idx] = (int32_t)v;
+                    const int64_t idx = (int64_t)atomicAdd(&ctl->acnt[pr], 1) + base;
+                    if (idx >= 0 && idx < n) order[idx] = (int32_t)v;
                     rnd[v] = round;
                     core[v] = level;
                 }
             if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
             // minval is next read after at least one more barrier
             if (tid == 0) ctl->minval = 0xffffffffu;
-            cnt = vcount[ci];
-            if (cnt > n) { if (tid == 0) atomicOr(&ctl->err, DERR_CAPACITY); return; }
+            const int a = vacnt[pr];
+            E = S + (a - (pr ? last1 : last0));
+            if (pr) last1 = a; else last0 = a;
+            if (E > n || E <= S) { if (tid == 0) atomicOr(&ctl->err, DERR_LOGIC); return; }
         }
-        // Remove the frontier: decrement remaining neighbours; a neighbour
-        // whose degree falls from level + 1 to level joins the next round.
-        const int lane = threadIdx.x & 31;
-        const int64_t warp = tid >> 5, nwarps = nth >> 5;
-        for (int64_t i = warp; i < cnt; i += nwarps) {
-            int32_t v = __ldcg(cur + i);
-            int64_t e0 = off[v], e1 = off[v + 1];
-            // four neighbours per lane at a time: their loads and atomics are
-            // independent and overlap (hubs have thousands of neighbours)
-            for (int64_t e = e0 + lane; e < e1; e += 128) {
-                int32_t w[4];
-                bool live[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int64_t ee = e + 32 * u;
-                    w[u] = ee < e1 ? adj[ee] : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) live[u] = w[u] >= 0 && __ldcg(rnd + w[u]) < 0;
-                int old[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) old[u] = live[u] ? atomicSub(deg + w[u], 1) : 0;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (live[u] && old[u] == level + 1) {
-                        rnd[w[u]] = round + 1;
-                        core[w[u]] = level;
-                        int idx = atomicAdd(&ctl->count[cn], 1);
-                        if (idx < n) nxt[idx] = w[u];
+        if (E - S <= PEEL_SMALL) {
+            if (blockIdx.x == 0) {
+                // consecutive small rounds in this block alone
+                int64_t s = S, e = E;
+                if (threadIdx.x == 0) ctl->ltail = (int)e;
+                __syncthreads();
+                while (true) {
+                    peel_remove((int)(e - s), threadIdx.x >> 5, blockDim.x >> 5, order + s, order, off,
+                                adj, deg, rnd, core, &ctl->ltail, 0, n, level, round);
+                    if (threadIdx.x == 0) {
+                        if (level > ctl->degeneracy) ctl->degeneracy = level;
+                        ctl->rounds = round + 1;
                     }
+                    __syncthreads();
+                    const int64_t e2 = *(volatile int *)&ctl->ltail;
+                    __syncthreads();   // every thread has read ltail before the next appends
+                    ++round;
+                    s = e;
+                    e = e2 < n ? e2 : n;   // (appends beyond n are dropped; caught below)
+                    if (e == s || e - s > PEEL_SMALL) break;   // uniform in the block
+                }
+                if (threadIdx.x == 0) {
+                    ctl->pub_round = round;
+                    ctl->pub_start = (int)s;
+                    ctl->pub_end = (int)e;
                 }
             }
+            if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+            round = *(volatile int *)&ctl->pub_round;
+            S = *(volatile int *)&ctl->pub_start;
+            E = *(volatile int *)&ctl->pub_end;
+            have_end = true;
+            continue;
         }
-        removed += cnt;
+        // a large frontier: every block; appends through acnt[round + 1 & 1]
+        const int64_t pos_off = E - (pr ? last0 : last1);
+        peel_remove((int)(E - S), tid >> 5, nth >> 5, order + S, order, off, adj, deg, rnd, core,
+                    &ctl->acnt[pr ^ 1], pos_off, n, level, round);
         if (tid == 0) {
             if (level > ctl->degeneracy) ctl->degeneracy = level;
             ctl->rounds = round + 1;
         }
         if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
-        int32_t *t = cur; cur = nxt; nxt = t;
+        S = E;
         ++round;
     }
 }
@@ -296,7 +365,7 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
     out.core = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
     out.rnd = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
     if (n > 0) {
-        DBuf<int32_t> deg(c, (size_t)n), fa(c, (size_t)n), fb(c, (size_t)n);
+        DBuf<int32_t> deg(c, (size_t)n), order(c, (size_t)n);
         DBuf<PeelCtl> ctl(c, 1);
         zero(c, ctl.p, sizeof(PeelCtl));
         unsigned int ff = 0xffffffffu;
@@ -319,9 +388,9 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
         int64_t nn = n;
         const int64_t *offp = out.off.p;
         const int32_t *adjp = out.adj.p;
-        int32_t *degp = deg.p, *rndp = out.rnd.p, *corep = out.core.p, *fap = fa.p, *fbp = fb.p;
+        int32_t *degp = deg.p, *rndp = out.rnd.p, *corep = out.core.p, *orderp = order.p;
         PeelCtl *ctlp = ctl.p;
-        void *args[] = {&nn, &offp, &adjp, &degp, &rndp, &corep, &fap, &fbp, &ctlp, &timeout_ns,
+        void *args[] = {&nn, &offp, &adjp, &degp, &rndp, &corep, &orderp, &ctlp, &timeout_ns,
                         &phantom};
         KDSS_CUDA(cudaLaunchCooperativeKernel((const void *)k_peel, dim3(grid), dim3(PEEL_THREADS),
                                               args, 0, c.stream));

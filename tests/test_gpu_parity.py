@@ -221,13 +221,15 @@ def test_fw_large_counts_are_bit_exact():
 
 
 def test_profiled_and_graph_runs_agree():
-    """The profiled path (every 8th iteration as separate graphs between
-    events, the others fused) and the plain path (one graph per iteration)
-    give the same r, for every precision."""
+    """The profiled per-iteration path (every 8th iteration as separate graphs
+    between events, the others fused) and the default path (the resident
+    launch for the integer rule, one graph per iteration for FP32K) give the
+    same r, for every precision."""
     n, s, d = GRAPHS["rmat2k"]()
     sct = K.kdss_build_sct(n, s, d, 4)
     for prec in (K.KDSS_INT64, K.KDSS_FP64, K.KDSS_FP32K):
-        a = K.kdss_fw_iterate(sct, None, 30, K.make_opts(precision=prec, flags=K.KDSS_FLAG_PROFILE))
+        a = K.kdss_fw_iterate(sct, None, 30, K.make_opts(
+            precision=prec, flags=K.KDSS_FLAG_PROFILE | K.KDSS_FLAG_PER_ITERATION))
         b = K.kdss_fw_iterate(sct, None, 30, K.make_opts(precision=prec))
         ra, _ = K.kdss_state_copy_r(a, n, prec)
         rb, _ = K.kdss_state_copy_r(b, n, prec)
