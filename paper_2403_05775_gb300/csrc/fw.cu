@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <functional>
+#include <type_traits>
 
 #include "fw.cuh"
 
@@ -700,6 +701,115 @@ k_pb_fast_rooted(const int64_t *__restrict__ pair_off, const uint16_t *__restric
 constexpr int SB_WARPS = 8;
 constexpr int SB_ROUNDS = 24;
 
+// The walk of one pair on levels relative to its lowest receiving node, all
+// in 32 bits: lane j holds node j's relative level rl, its cap cl (0: never
+// receives) and its id (-1 past the pair); n_C = nC32 < 2^31 and every
+// rl < 2^31.  Adds each node's allocation to acc[id].
+template <class AV>
+__device__ __forceinline__ void walk_rel32(uint32_t rl, uint32_t cl, int32_t id, int len,
+                                           uint32_t nC32, void *acc, uint64_t *sr_w, int *err) {
+    const unsigned FULL_ = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    // The walk of Alg. 3 with warp-uniform state: at water level L the
+    // receiving nodes are those with rl <= L < rl + cl; the level rises
+    // to the next event (a node's level, or a receiving node's level
+    // plus cap) while the units last, and stops at
+    // L* = L + floor(rem / na) with R = rem mod na units left for the
+    // lowest ids receiving at L*.  A level where every node is capped
+    // jumps to the next node.  Pairs that cross more than SB_ROUNDS
+    // events take the closed form below.
+    {
+        const uint32_t INF32 = 0xffffffffu;
+        uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
+        bool done = false;
+        for (int round = 0; round < SB_ROUNDS; ++round) {
+            const bool act = cl > 0 && rl <= L && L - rl < cl;
+            const uint32_t na = (uint32_t)__popc(__ballot_sync(FULL_, act));
+            const uint32_t e1 = (cl > 0 && rl > L) ? rl : INF32;
+            const uint32_t e2 = act ? rl + cl : INF32;
+            const uint32_t ev = __reduce_min_sync(FULL_, e1 < e2 ? e1 : e2);
+            if (na == 0) {
+                if (ev == INF32) break;
+                L = ev;
+                continue;
+            }
+            // the units end before the next event, or exactly at it
+            // (then nothing is left over and L* = ev allocates the
+            // same): floor(rem / na) < ev - L, or rem = (ev - L) na,
+            // which is rem <= (ev - L) na; one division at the end
+            const uint64_t span = (uint64_t)(ev - L) * na;
+            if (ev == INF32 || rem <= span) {
+                const uint32_t qd = rem / na;
+                Ls = L + qd;
+                R = rem - qd * na;
+                done = true;
+                break;
+            }
+            rem -= (uint32_t)span;
+            L = ev;
+        }
+        if (done) {
+            uint32_t dj = 0;
+            bool elig = false;
+            if (cl > 0) {
+                if (Ls > rl) dj = min(Ls - rl, cl);
+                elig = rl <= Ls && Ls - rl < cl;
+            }
+            const unsigned eb = __ballot_sync(FULL_, elig);
+            if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+            if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+            __syncwarp();
+            return;
+        }
+    }
+    // (level, cap) of every node as one 64-bit word; a zero cap adds
+    // nothing below (min(d, 0) = 0), so no special case
+    uint2 *sp = (uint2 *)sr_w;
+    sp[lane] = make_uint2(rl, cl);
+    __syncwarp();
+    const uint32_t b1 = rl, b2 = rl + cl, lim = nC32 + 1u;
+    uint32_t g1 = 0, g2 = 0;
+#pragma unroll 4
+    for (int i = 0; i < len; ++i) {
+        const uint2 e = sp[i];
+        if (b1 > e.x) g1 = min(g1 + min(b1 - e.x, e.y), lim);
+        if (b2 > e.x) g2 = min(g2 + min(b2 - e.x, e.y), lim);
+    }
+    uint32_t key = 0, bg = 0;
+    int hv = 0;
+    if (cl > 0) {
+        if (g1 <= nC32) { key = b1; bg = g1; hv = 1; }
+        if (g2 <= nC32) { key = b2; bg = g2; hv = 1; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t ok = __shfl_xor_sync(FULL_, key, o);
+        const int oh = __shfl_xor_sync(FULL_, hv, o);
+        const uint32_t og = __shfl_xor_sync(FULL_, bg, o);
+        if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; }
+    }
+    // right slope of g at the winning breakpoint
+    const int bs = __popc(__ballot_sync(FULL_, cl > 0 && key >= rl && key - rl < cl));
+    if (!hv || bs <= 0) {
+        if (lane == 0) atomicOr(err, DERR_LOGIC);
+        return;
+    }
+    const uint32_t L = key + (nC32 - bg) / (uint32_t)bs;
+    uint32_t dj = 0;
+    bool elig = false;
+    if (cl > 0) {
+        if (L > rl) dj = min(L - rl, cl);
+        elig = rl <= L && L - rl < cl;
+    }
+    uint32_t tot = __reduce_add_sync(FULL_, dj);
+    const uint32_t R = nC32 - tot;
+    const unsigned eb = __ballot_sync(FULL_, elig);
+    if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+    if (dj) atomicAdd((AV *)acc + id, (AV)dj);
+    __syncwarp();
+    return;
+}
+
 // The water level of one pair of at most 32 nodes by one warp (the closed
 // form of Alg. 3's walk): lane j holds node j (raw id with the V_h mark in
 // rawc, its integer level rjc); lanes >= len hold nothing.  Used by the slow
@@ -732,103 +842,7 @@ __device__ __forceinline__ void slow_pair_walk(int len, int h, int32_t rawc, uin
     const uint64_t base = ((uint64_t)bh << 32) | bl;
     if (__all_sync(FULL_, cj == 0 || rj - base < (1ull << 31)) && nC < (1ull << 31)) {
         const uint32_t rl = cj > 0 ? (uint32_t)(rj - base) : 0u, cl = (uint32_t)cj;
-        // The walk of Alg. 3 with warp-uniform state: at water level L the
-        // receiving nodes are those with rl <= L < rl + cl; the level rises
-        // to the next event (a node's level, or a receiving node's level
-        // plus cap) while the units last, and stops at
-        // L* = L + floor(rem / na) with R = rem mod na units left for the
-        // lowest ids receiving at L*.  A level where every node is capped
-        // jumps to the next node.  Pairs that cross more than SB_ROUNDS
-        // events take the closed form below.
-        {
-            const uint32_t nC32 = (uint32_t)nC, INF32 = 0xffffffffu;
-            uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
-            bool done = false;
-            for (int round = 0; round < SB_ROUNDS; ++round) {
-                const bool act = cl > 0 && rl <= L && L - rl < cl;
-                const uint32_t na = (uint32_t)__popc(__ballot_sync(FULL_, act));
-                const uint32_t e1 = (cl > 0 && rl > L) ? rl : INF32;
-                const uint32_t e2 = act ? rl + cl : INF32;
-                const uint32_t ev = __reduce_min_sync(FULL_, e1 < e2 ? e1 : e2);
-                if (na == 0) {
-                    if (ev == INF32) break;
-                    L = ev;
-                    continue;
-                }
-                // the units end before the next event, or exactly at it
-                // (then nothing is left over and L* = ev allocates the
-                // same): floor(rem / na) < ev - L, or rem = (ev - L) na,
-                // which is rem <= (ev - L) na; one division at the end
-                const uint64_t span = (uint64_t)(ev - L) * na;
-                if (ev == INF32 || rem <= span) {
-                    const uint32_t qd = rem / na;
-                    Ls = L + qd;
-                    R = rem - qd * na;
-                    done = true;
-                    break;
-                }
-                rem -= (uint32_t)span;
-                L = ev;
-            }
-            if (done) {
-                uint32_t dj = 0;
-                bool elig = false;
-                if (cl > 0) {
-                    if (Ls > rl) dj = min(Ls - rl, cl);
-                    elig = rl <= Ls && Ls - rl < cl;
-                }
-                const unsigned eb = __ballot_sync(FULL_, elig);
-                if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
-                if (dj) atomicAdd((AV *)acc + id, (AV)dj);
-                __syncwarp();
-                return;
-            }
-        }
-        // (level, cap) of every node as one 64-bit word; a zero cap adds
-        // nothing below (min(d, 0) = 0), so no special case
-        uint2 *sp = (uint2 *)sr_w;
-        sp[lane] = make_uint2(rl, cl);
-        __syncwarp();
-        const uint32_t b1 = rl, b2 = rl + cl, lim = (uint32_t)nC + 1u, nC32 = (uint32_t)nC;
-        uint32_t g1 = 0, g2 = 0;
-#pragma unroll 4
-        for (int i = 0; i < len; ++i) {
-            const uint2 e = sp[i];
-            if (b1 > e.x) g1 = min(g1 + min(b1 - e.x, e.y), lim);
-            if (b2 > e.x) g2 = min(g2 + min(b2 - e.x, e.y), lim);
-        }
-        uint32_t key = 0, bg = 0;
-        int hv = 0;
-        if (cl > 0) {
-            if (g1 <= nC32) { key = b1; bg = g1; hv = 1; }
-            if (g2 <= nC32) { key = b2; bg = g2; hv = 1; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint32_t ok = __shfl_xor_sync(FULL_, key, o);
-            const int oh = __shfl_xor_sync(FULL_, hv, o);
-            const uint32_t og = __shfl_xor_sync(FULL_, bg, o);
-            if (oh && (!hv || ok > key)) { key = ok; hv = 1; bg = og; }
-        }
-        // right slope of g at the winning breakpoint
-        const int bs = __popc(__ballot_sync(FULL_, cl > 0 && key >= rl && key - rl < cl));
-        if (!hv || bs <= 0) {
-            if (lane == 0) atomicOr(err, DERR_LOGIC);
-            return;
-        }
-        const uint32_t L = key + (nC32 - bg) / (uint32_t)bs;
-        uint32_t dj = 0;
-        bool elig = false;
-        if (cl > 0) {
-            if (L > rl) dj = min(L - rl, cl);
-            elig = rl <= L && L - rl < cl;
-        }
-        uint32_t tot = __reduce_add_sync(FULL_, dj);
-        const uint32_t R = nC32 - tot;
-        const unsigned eb = __ballot_sync(FULL_, elig);
-        if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
-        if (dj) atomicAdd((AV *)acc + id, (AV)dj);
-        __syncwarp();
+        walk_rel32<AV>(rl, cl, id, len, (uint32_t)nC, acc, sr_w, err);
         return;
     }
     sr_w[lane] = rj;
@@ -885,6 +899,27 @@ __device__ __forceinline__ void slow_pair_walk(int len, int h, int32_t rawc, uin
     if (elig && (uint64_t)__popc(eb & lanemask_lt()) < R) dj += 1;
     if (dj) atomicAdd((AV *)acc + id, (AV)dj);
     __syncwarp();
+}
+
+// slow_pair_walk for levels and n_C below 2^31 (the resident kernel's 32-bit
+// mode): one 32-bit warp reduction gives the base, no spread test.
+template <class AV>
+__device__ __forceinline__ void slow_pair_walk32(int len, int h, int32_t rawc, uint32_t lev, int k,
+                                                 const uint64_t *__restrict__ binom, int bcols,
+                                                 void *acc, uint64_t *sr_w, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int p = len - h;
+    const uint32_t nC = (uint32_t)__ldg(binom + (size_t)p * bcols + (k - h));
+    const uint32_t cap_p = (p >= 1 && k - h - 1 >= 0)
+                               ? (uint32_t)__ldg(binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0u;
+    int32_t id = -1;
+    uint32_t cj = 0;
+    if (lane < len) {
+        id = rawc & 0x7fffffff;
+        cj = rawc < 0 ? nC : cap_p;
+    }
+    const uint32_t base = __reduce_min_sync(0xffffffffu, cj > 0 ? lev : 0xffffffffu);
+    walk_rel32<AV>(cj > 0 ? lev - base : 0u, cj, id, len, nC, acc, sr_w, err);
 }
 
 template <class RT, bool PIPE>
@@ -2097,22 +2132,28 @@ k_resident_plan(const int64_t *__restrict__ pair_off, const int32_t *__restrict_
     }
 }
 
-template <class RT>
+// L32: every level stays below 2^31 for the whole launch ((t + T) c_k < 2^31,
+// as r_t(u) <= t c_k), so levels, n_C, caps and the per-iteration sums run
+// in 32 bits.
+template <class RT, bool L32>
 __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const ResidentArgs a) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     __shared__ int s_cursor, s_nslow, s_wcur;
     // the block accumulates in integers (every allocation is an integer
-    // below 2^53, and 64-bit integer adds are native shared-memory atomics)
-    // and converts once per node when it flushes
-    using AV = unsigned long long;
+    // below 2^53, and integer adds are native shared-memory atomics) and
+    // converts once per node when it flushes; a node's allocations in one
+    // iteration sum to at most c_k
+    using AV = typename std::conditional<L32, unsigned int, unsigned long long>::type;
+    using LT = typename std::conditional<L32, uint32_t, uint64_t>::type;   // levels
     using GV = typename AccV<RT>::T;
     const unsigned FULL_ = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint64_t *wsr = reinterpret_cast<uint64_t *>(rs_smem) + wib * 64;
     uint64_t *wsc = wsr + 32;
     uint64_t *sval = reinterpret_cast<uint64_t *>(rs_smem) + RS_WARPS * 64;
+    LT *slev = reinterpret_cast<LT *>(sval);   // integer level of each distinct node
     AV *sacc = reinterpret_cast<AV *>(sval + a.ucap);
-    int32_t *suid = reinterpret_cast<int32_t *>(sacc + a.ucap);
+    int32_t *suid = reinterpret_cast<int32_t *>(sval + 2 * (size_t)a.ucap);
     uint16_t *slid = reinterpret_cast<uint16_t *>(suid + a.ucap);
     uint16_t *poff = slid + a.ncap;
     uint16_t *slist = poff + a.pcap + 1;
@@ -2160,7 +2201,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
         // r_j of the block's distinct nodes (L2 reads: other blocks wrote them)
         for (int i = threadIdx.x; i < nu; i += blockDim.x) {
             const int32_t u = suid[i];
-            sval[i] = rword_add<RT>(__ldcg(Rc + u), __ldcg(Ap + u));
+            slev[i] = (LT)level_of<RT>(rword_add<RT>(__ldcg(Rc + u), __ldcg(Ap + u)));
             sacc[i] = AV(0);
         }
         // fold the previous delta into the other copy of r, clear the
@@ -2183,23 +2224,24 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
             const int h = valid ? (int)hh[qi] : 0;
             uint32_t rmask = 0;
             bool want_slow = false;
-            uint64_t w = 0, R = 0;
+            LT w = 0, R = 0;
             if (valid && h <= k && k <= len && len <= 32) {
                 const int p = len - h;
-                const uint64_t nC = __ldg(a.binom + (size_t)p * bcols + (k - h));
-                const uint64_t cap_p = (p >= 1 && k - h - 1 >= 0)
-                                           ? __ldg(a.binom + (size_t)(p - 1) * bcols + (k - h - 1)) : 0ull;
-                const uint64_t pm = cap_p > 0 ? 0ull : ~0ull;
-                uint64_t m1 = ~0ull, m2 = ~0ull;
+                const LT nC = (LT)__ldg(a.binom + (size_t)p * bcols + (k - h));
+                const LT cap_p = (p >= 1 && k - h - 1 >= 0)
+                                     ? (LT)__ldg(a.binom + (size_t)(p - 1) * bcols + (k - h - 1)) : LT(0);
+                const LT NONE = ~LT(0);
+                const LT pm = cap_p > 0 ? LT(0) : NONE;
+                LT m1 = NONE, m2 = NONE;
                 uint32_t mask1 = 0;
                 bool piv1 = false;
                 for (int s2 = 0; s2 < len; ++s2) {
                     const unsigned l = slid[o + s2];
                     const bool hold = (l & 0x8000u) != 0;
-                    const uint64_t v = sval[l & 0x7fffu] | (hold ? 0ull : pm);
+                    const LT v = slev[l & 0x7fffu] | (hold ? LT(0) : pm);
                     const bool lt = v < m1;
-                    const bool eq = v == m1 && v != ~0ull;
-                    const uint64_t mn = v < m2 ? v : m2;
+                    const bool eq = v == m1 && v != NONE;
+                    const LT mn = v < m2 ? v : m2;
                     m2 = lt ? m1 : (eq ? m2 : mn);
                     m1 = lt ? v : m1;
                     const uint32_t bit = 1u << s2;
@@ -2207,12 +2249,12 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
                     piv1 = lt ? !hold : (piv1 || (eq && !hold));
                 }
                 if (mask1) {
-                    const uint64_t na = (uint64_t)__popc(mask1);
-                    const uint64_t mu = piv1 ? cap_p : nC;
-                    const uint64_t gap = m2 == ~0ull ? ~0ull : level_of<RT>(m2) - level_of<RT>(m1);
+                    const LT na = (LT)__popc(mask1);
+                    const LT mu = piv1 ? cap_p : nC;
+                    const LT gap = m2 == NONE ? NONE : m2 - m1;
                     w = nC / na;
                     R = nC - w * na;
-                    const uint64_t lim = mu < gap ? mu : gap;
+                    const LT lim = mu < gap ? mu : gap;
                     if (!(R == 0 ? w > lim : w >= lim)) rmask = mask1;
                     else want_slow = true;
                 }
@@ -2226,14 +2268,14 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
                 base = __shfl_sync(FULL_, base, 0);
                 if (want_slow) slist[base + __popc(um & lanemask_lt())] = (uint16_t)qi;
             }
-            uint64_t rank = 0;
+            LT rank = 0;
             while (__any_sync(FULL_, rmask != 0)) {
                 int32_t rid = -1;
                 AV amount = AV(0);
                 if (rmask) {
                     const int sl = __ffs(rmask) - 1;
                     rmask &= rmask - 1;
-                    const uint64_t dl = w + (rank < R ? 1ull : 0ull);
+                    const LT dl = w + (rank < R ? LT(1) : LT(0));
                     ++rank;
                     if (dl) {
                         rid = (int32_t)(slid[o + sl] & 0x7fffu);
@@ -2255,13 +2297,16 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
             const int so = poff[q];
             const int sl = (int)poff[q + 1] - so;
             int32_t rawc = 0;
-            uint64_t rjc = 0;
+            LT lev = 0;
             if (lane < sl) {
                 const unsigned l = slid[so + lane];
                 rawc = (int32_t)(l & 0x7fffu) | ((l & 0x8000u) ? (int32_t)0x80000000 : 0);
-                rjc = level_of<RT>(sval[l & 0x7fffu]);
+                lev = slev[l & 0x7fffu];
             }
-            slow_pair_walk<AV>(sl, (int)hh[q], rawc, rjc, k, a.binom, bcols, sacc, wsr, wsc, a.err);
+            if constexpr (L32)
+                slow_pair_walk32<AV>(sl, (int)hh[q], rawc, lev, k, a.binom, bcols, sacc, wsr, a.err);
+            else
+                slow_pair_walk<AV>(sl, (int)hh[q], rawc, lev, k, a.binom, bcols, sacc, wsr, wsc, a.err);
         }
         __syncthreads();
         // one global add per distinct node that received units
@@ -2297,6 +2342,12 @@ struct EventPair {
 // Whether the resident launch can run the iterations of this state on s:
 // the integer rule, pairs of at most 32 nodes only, and the largest block
 // range within one block's shared memory.  Plans once per (state, SCT).
+using ResidentKernel = void (*)(ResidentArgs);
+ResidentKernel resident_kernel(int precision, bool l32) {
+    if (precision == KDSS_FP64) return l32 ? k_fw_resident<double, true> : k_fw_resident<double, false>;
+    return l32 ? k_fw_resident<uint64_t, true> : k_fw_resident<uint64_t, false>;
+}
+
 bool resident_ready(const Ctx &c, const SctDev &s, StateDev &st) {
     if (st.per_iteration || st.precision == KDSS_FP32K || st.qchunk > 0 || st.force_rooted)
         return false;
@@ -2338,10 +2389,14 @@ bool resident_ready(const Ctx &c, const SctDev &s, StateDev &st) {
     if (ucap > RS_UCAP || ncap > 65535) return false;
     const size_t smem = resident_smem_bytes(ncap, (int)pcap, ucap);
     if (smem + 1024 > (size_t)optin) return false;   // static shared memory and slack
-    auto kern = st.precision == KDSS_FP64 ? k_fw_resident<double> : k_fw_resident<uint64_t>;
-    KDSS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RS_WARPS * 32, smem));
+    int per_sm = 1;
+    for (int l32 = 0; l32 < 2; ++l32) {
+        auto kern = resident_kernel(st.precision, l32 != 0);
+        KDSS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, RS_WARPS * 32, smem));
+        per_sm = std::min(per_sm, b);
+    }
     if (per_sm < 1) return false;
     st.res_lidx = std::move(lidx);
     st.res_loff = std::move(loff);
@@ -2392,7 +2447,10 @@ void fw_run_resident(const Ctx &c, const SctDev &s, StateDev &st, int T, bool pr
     a.ncap = st.res_ncap;
     a.pcap = st.res_pcap;
     a.ucap = st.res_ucap;
-    auto kern = st.precision == KDSS_FP64 ? k_fw_resident<double> : k_fw_resident<uint64_t>;
+    // 32-bit levels when every r_t(u) <= t c_k stays below 2^31
+    const long double top = (long double)(st.t + T) *
+                            ((long double)st.ck_lo + (long double)st.ck_hi * 18446744073709551616.0L);
+    auto kern = resident_kernel(st.precision, top < 2147483648.0L);
     void *args[] = {&a};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profile) {

@@ -128,3 +128,26 @@ def test_resident_solve_with_a_stop_rule():
                                                  flags=K.KDSS_FLAG_PER_ITERATION))
     assert (a["istar"], a["count"], a["t_used"]) == (b["istar"], b["count"], b["t_used"])
     assert a["upper_bound"] == b["upper_bound"]
+
+
+@pytest.mark.parametrize("prec", [K.KDSS_INT64, K.KDSS_FP64])
+def test_resident_levels_past_32_bits(prec):
+    """A 30-clique beside a sparse graph at k = 10: c_k = C(30, 10) + ... so
+    40 iterations keep every level below 2^31 (the launch runs on 32-bit
+    levels) and the next 40 cross it (64-bit levels); both runs, and their
+    hand-over inside one state, equal the oracle."""
+    n1, s1, d1 = synth.chung_lu(1500, 8.0, 2.5, 61)[:3]
+    iu = np.triu_indices(30, 1)
+    n, s, d = n1 + 30, np.concatenate([s1, iu[0] + n1]).astype(np.int32), \
+        np.concatenate([d1, iu[1] + n1]).astype(np.int32)
+    k = 10
+    sct = K.kdss_build_sct(n, s, d, k)
+    info = K.kdss_sct_info(sct)
+    ck = info["c_k"]
+    assert 40 * ck < 2 ** 31 <= 80 * ck
+    assert info["pairs_per_class"][3:] == [0, 0]
+    st, r, t, nl = _run(sct, n, 40, prec, 0)
+    assert nl <= 3 and np.array_equal(r, _oracle_r(n, s, d, k, 40))
+    st, r, t, nl = _run(sct, n, 40, prec, 0, st)
+    assert nl == 1 and t == 80
+    assert np.array_equal(r, _oracle_r(n, s, d, k, 80))
