@@ -37,6 +37,16 @@ __global__ void k_keys_u64(int64_t n, const uint64_t *r, uint64_t maxv, uint64_t
         vals[v] = (int32_t)v;
     }
 }
+// FP64 storage: the integer value of each r, so that the key has only as
+// many bits as max r (the raw bit patterns would need all 64).
+__global__ void k_keys_f64(int64_t n, const uint64_t *r, uint64_t maxv, uint64_t *keys,
+                           int32_t *vals) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        keys[v] = maxv - (uint64_t)__longlong_as_double((long long)r[v]);
+        vals[v] = (int32_t)v;
+    }
+}
 __global__ void k_keys_f32(int64_t n, const float *r, uint32_t maxbits, uint64_t *keys,
                            int32_t *vals) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -410,11 +420,14 @@ void prefix_begin(const Ctx &c, int64_t n, const StateDev &st, bool wide, Prefix
             double md;
             memcpy(&md, &mb, 8);
             a.rmax = st.t > 0 ? md / st.t : 0.0;
+            const uint64_t mv = (uint64_t)md;   // an integer below 2^53
+            k_keys_f64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mv, keys.p, a.order.p);
+            bits = bit_length(mv);
         } else {
             a.rmax = st.t > 0 ? (double)mb / st.t : 0.0;
+            k_keys_u64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mb, keys.p, a.order.p);
+            bits = bit_length(mb);
         }
-        k_keys_u64<<<grid_for(c, n, B, 4), B, 0, c.stream>>>(n, st.r.p, mb, keys.p, a.order.p);
-        bits = bit_length(mb);
     }
     KDSS_LAUNCH_CHECK();
     radix_sort_u64(c, keys.p, a.order.p, n, {{0, bits}});

@@ -720,14 +720,17 @@ __device__ __forceinline__ void walk_rel32(uint32_t rl, uint32_t cl, int32_t id,
     // events take the closed form below.
     {
         const uint32_t INF32 = 0xffffffffu;
+        // a node that never receives sits at INF32.  Receiving at level L
+        // is lo <= L < lo + cl, which is L - lo < cl in wrapping 32-bit
+        // arithmetic: rl and cl are below 2^31, so L - lo wraps to at least
+        // 2^31 > cl when lo > L (and cl = 0 never holds).
+        const uint32_t lo = cl > 0 ? rl : INF32, hi = rl + cl;
         uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
         bool done = false;
         for (int round = 0; round < SB_ROUNDS; ++round) {
-            const bool act = cl > 0 && rl <= L && L - rl < cl;
+            const bool act = L - lo < cl;
             const uint32_t na = (uint32_t)__popc(__ballot_sync(FULL_, act));
-            const uint32_t e1 = (cl > 0 && rl > L) ? rl : INF32;
-            const uint32_t e2 = act ? rl + cl : INF32;
-            const uint32_t ev = __reduce_min_sync(FULL_, e1 < e2 ? e1 : e2);
+            const uint32_t ev = __reduce_min_sync(FULL_, act ? hi : (lo > L ? lo : INF32));
             if (na == 0) {
                 if (ev == INF32) break;
                 L = ev;
@@ -749,12 +752,8 @@ __device__ __forceinline__ void walk_rel32(uint32_t rl, uint32_t cl, int32_t id,
             L = ev;
         }
         if (done) {
-            uint32_t dj = 0;
-            bool elig = false;
-            if (cl > 0) {
-                if (Ls > rl) dj = min(Ls - rl, cl);
-                elig = rl <= Ls && Ls - rl < cl;
-            }
+            const bool elig = Ls - lo < cl;
+            uint32_t dj = Ls > lo ? min(Ls - lo, cl) : 0u;
             const unsigned eb = __ballot_sync(FULL_, elig);
             if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
             if (dj) atomicAdd((AV *)acc + id, (AV)dj);

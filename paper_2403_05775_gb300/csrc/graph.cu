@@ -411,8 +411,10 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
         const int32_t *key = order == KDSS_ORDER_CORE ? out.core.p : out.rnd.p;
         k_order_keys<<<grid_for(c, n, B), B, 0, c.stream>>>(n, key, okeys.p);
         KDSS_LAUNCH_CHECK();
-        int kb = bit_length((uint64_t)std::max<int64_t>(n, out.peel_rounds + 1));
-        radix_sort_u64(c, okeys.p, nullptr, n, {{0, b}, {32, 32 + kb}});
+        // the keys are written in id order and the sort is stable, so the
+        // high word alone (round or core) gives the (key, id) order
+        int kb = bit_length((uint64_t)std::max<int64_t>(out.peel_rounds, out.degeneracy) + 1);
+        radix_sort_u64(c, okeys.p, nullptr, n, {{32, 32 + kb}});
         k_order_ranks<<<grid_for(c, n, B), B, 0, c.stream>>>(n, okeys.p, out.vert.p, out.rank.p);
         KDSS_LAUNCH_CHECK();
     }

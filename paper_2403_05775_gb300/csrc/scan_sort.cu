@@ -106,19 +106,23 @@ void scan_impl(const Ctx &c, const T *in, T *out, int64_t n) {
 // ---------------------------------------------------------------------------
 // Radix sort
 // ---------------------------------------------------------------------------
+// A block sorts a tile of `rounds` x 256 keys, 256 per round.  The rounds
+// per tile grow with n so that the grid stays at about two blocks per SM: a
+// small sort (1e5 keys) then takes one or two short rounds per block instead
+// of a few blocks walking 32 rounds each.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 32;
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_MAX_ROUNDS = 32;
 
 __global__ void k_rs_hist(const uint64_t *keys, int64_t n, int shift, uint32_t mask,
-                          int32_t *hist, int64_t nblocks) {
+                          int32_t *hist, int64_t nblocks, int rounds) {
     __shared__ int32_t cnt[RS_WARPS][256];
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int w = threadIdx.x >> 5;
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    int64_t end = base + RS_TILE < n ? base + RS_TILE : n;
+    const int64_t tile = (int64_t)RS_THREADS * rounds;
+    int64_t base = (int64_t)blockIdx.x * tile;
+    int64_t end = base + tile < n ? base + tile : n;
     for (int64_t i = base + threadIdx.x; i < end; i += RS_THREADS) {
         uint32_t d = (uint32_t)(keys[i] >> shift) & mask;
         atomicAdd(&cnt[w][d], 1);
@@ -134,7 +138,7 @@ __global__ void k_rs_hist(const uint64_t *keys, int64_t n, int shift, uint32_t m
 
 __global__ void k_rs_scatter(const uint64_t *kin, const int32_t *vin, uint64_t *kout,
                              int32_t *vout, int64_t n, int shift, uint32_t mask,
-                             const int32_t *hist_scan, int64_t nblocks) {
+                             const int32_t *hist_scan, int64_t nblocks, int rounds) {
     __shared__ int32_t s_base[256];
     __shared__ int32_t s_run[256];
     __shared__ int32_t s_w[RS_WARPS][256];
@@ -143,8 +147,8 @@ __global__ void k_rs_scatter(const uint64_t *kin, const int32_t *vin, uint64_t *
         s_base[d] = hist_scan[(int64_t)d * nblocks + blockIdx.x];
         s_run[d] = 0;
     }
-    int64_t tile = (int64_t)blockIdx.x * RS_TILE;
-    for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t tile = (int64_t)blockIdx.x * RS_THREADS * rounds;
+    for (int r = 0; r < rounds; ++r) {
         int64_t i = tile + (int64_t)r * RS_THREADS + threadIdx.x;
         bool valid = i < n;
         uint64_t key = valid ? kin[i] : 0ull;
@@ -237,18 +241,21 @@ void radix_sort_u64(const Ctx &c, uint64_t *keys, int32_t *vals, int64_t n,
             passes.push_back({s, (1u << bits) - 1u});
         }
     if (passes.empty()) return;
-    int64_t nb = ceil_div(n, RS_TILE);
+    const int rounds = (int)std::min<int64_t>(
+        RS_MAX_ROUNDS, std::max<int64_t>(1, ceil_div(n, (int64_t)RS_THREADS * 2 * c.num_sms)));
+    int64_t nb = ceil_div(n, (int64_t)RS_THREADS * rounds);
     DBuf<uint64_t> kalt(c, (size_t)n);
     DBuf<int32_t> valt(c, vals ? (size_t)n : 0);
     DBuf<int32_t> hist(c, (size_t)(256 * nb)), hscan(c, (size_t)(256 * nb));
     uint64_t *ka = keys, *kb = kalt.p;
     int32_t *va = vals, *vb = valt.p;
     for (const Pass &p : passes) {
-        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, c.stream>>>(ka, n, p.shift, p.mask, hist.p, nb);
+        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, c.stream>>>(ka, n, p.shift, p.mask, hist.p, nb,
+                                                            rounds);
         KDSS_LAUNCH_CHECK();
         scan_impl<int32_t, false>(c, hist.p, hscan.p, 256 * nb);
         k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, c.stream>>>(ka, va, kb, vb, n, p.shift, p.mask,
-                                                                hscan.p, nb);
+                                                                hscan.p, nb, rounds);
         KDSS_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
