@@ -69,7 +69,6 @@ struct PeelCtl {
     GridBarrier bar;
     int err;
     int acnt[2];              // appends of the rounds of each parity (never reset)
-    int ltail;                // end of the peel order during a run of rounds in block 0
     unsigned int minval;
     int rounds;
     int degeneracy;
@@ -93,15 +92,15 @@ constexpr int PEEL_SMALL = 128;
 // nothing reads it afterwards; skipping the check saves a dependent load of
 // rnd per neighbour.
 __device__ __forceinline__ void peel_remove(int cnt, int64_t warp0, int64_t nwarps,
-                                            const int32_t *cur, int32_t *order,
+                                            const longlong2 *cur, longlong2 *order,
                                             const int64_t *__restrict__ off,
                                             const int32_t *__restrict__ adj, int32_t *deg,
                                             int32_t *rnd, int32_t *core, int *counter,
                                             int64_t pos_off, int64_t n, int level, int round) {
     const int lane = threadIdx.x & 31;
     for (int64_t i = warp0; i < cnt; i += nwarps) {
-        const int32_t v = __ldcg(cur + i);
-        const int64_t e0 = off[v], e1 = off[v + 1];
+        const longlong2 er = __ldcg(cur + i);
+        const int64_t e0 = er.x, e1 = er.y;
         // four neighbours per lane at a time: their loads and atomics are
         // independent and overlap (hubs have thousands of neighbours)
         for (int64_t e = e0 + lane; e < e1; e += 128) {
@@ -120,24 +119,98 @@ __device__ __forceinline__ void peel_remove(int cnt, int64_t warp0, int64_t nwar
                     rnd[w[u]] = round + 1;
                     core[w[u]] = level;
                     const int64_t idx = (int64_t)atomicAdd(counter, 1) + pos_off;
-                    if (idx >= 0 && idx < n) order[idx] = w[u];
+                    if (idx >= 0 && idx < n) order[idx] = make_longlong2(off[w[u]], off[w[u] + 1]);
                 }
             }
         }
     }
 }
 
-// The frontiers are consecutive ranges of one array, the peel order: round r
+// A run of small rounds in block 0 alone, while the other blocks wait at a
+// grid barrier.  The frontier lives in shared memory as the edge ranges of its
+// vertices; a vertex that joins the next round takes a slot from a shared
+// counter, is written to the peel order after the current frontier (where the
+// grid reads it if the run stops) and, while the next frontier has room, to
+// the other shared buffer with its edge range.  A round is then a chain of
+// three global accesses (the neighbour list, the atomic decrement, the edge
+// range of a joining vertex) and two block barriers.  On return order[s, e)
+// is the next frontier (empty, or larger than PEEL_SMALL) and `round` its
+// round.  Every thread of block 0 calls this.
+__device__ __forceinline__ void peel_local_run(int64_t &s, int64_t &e, int &round, int level,
+                                               int64_t n, const int64_t *__restrict__ off,
+                                               const int32_t *__restrict__ adj, int32_t *deg,
+                                               int32_t *rnd, int32_t *core, longlong2 *order,
+                                               PeelCtl *ctl) {
+    __shared__ long long le0[2][PEEL_SMALL], le1[2][PEEL_SMALL];
+    __shared__ int lcnt[2];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < (int)(e - s); i += blockDim.x) {
+        const longlong2 er = __ldcg(order + s + i);
+        le0[0][i] = er.x;
+        le1[0][i] = er.y;
+    }
+    if (threadIdx.x == 0) {
+        lcnt[0] = 0;
+        lcnt[1] = 0;
+    }
+    __syncthreads();
+    int cur = 0;
+    while (true) {
+        const int cnt = (int)(e - s), nx = cur ^ 1;
+        for (int i = wib; i < cnt; i += nw) {
+            const int64_t e0 = le0[cur][i], e1 = le1[cur][i];
+            for (int64_t x = e0 + lane; x < e1; x += 128) {
+                int32_t w[4];
+                int old[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w[u] = x + 32 * u < e1 ? adj[x + 32 * u] : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) old[u] = w[u] >= 0 ? atomicSub(deg + w[u], 1) : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (w[u] >= 0 && old[u] == level + 1) {
+                        rnd[w[u]] = round + 1;
+                        core[w[u]] = level;
+                        const int slot = atomicAdd(&lcnt[nx], 1);
+                        const long long a0 = off[w[u]], a1 = off[w[u] + 1];
+                        if (e + slot < n) order[e + slot] = make_longlong2(a0, a1);
+                        if (slot < PEEL_SMALL) {
+                            le0[nx][slot] = a0;
+                            le1[nx][slot] = a1;
+                        }
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (level > ctl->degeneracy) ctl->degeneracy = level;
+            ctl->rounds = round + 1;
+        }
+        __syncthreads();
+        const int next = lcnt[nx];
+        if (threadIdx.x == 0) lcnt[cur] = 0;   // read by everyone before the barrier above
+        __syncthreads();
+        ++round;
+        s = e;
+        e = e + next < n ? e + next : n;   // (appends beyond n are dropped; caught by the caller)
+        cur = nx;
+        if (next == 0 || next > PEEL_SMALL) break;   // uniform in the block
+    }
+}
+
+// The frontiers are consecutive ranges of one array, the peel order, which
+// holds each queued vertex as its edge range (off[v], off[v + 1]): a round
+// starts from the ranges without a dependent load of off.  Round r
 // removes order[S_r, S_{r+1}).  Round r appends through acnt[(r + 1) & 1] and
 // round r + 1 reads that counter to find its end, so no round's appends touch
 // the counter the same round reads (a late block may still be reading it
 // while others append), and no counter is ever reset.  Each block keeps the
 // value of each counter it last read; a counter changes only between two of
 // its reads, so the differences give the rounds' sizes.  A run of rounds in
-// block 0 appends through its own counter and leaves acnt untouched.
+// block 0 appends through a shared-memory counter and leaves acnt untouched.
 __global__ void __launch_bounds__(PEEL_THREADS, 1)
 k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-       int32_t *deg, int32_t *rnd, int32_t *core, int32_t *order, PeelCtl *ctl,
+       int32_t *deg, int32_t *rnd, int32_t *core, longlong2 *order, PeelCtl *ctl,
        uint64_t timeout_ns, unsigned int phantom) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -186,7 +259,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
             for (int64_t v = tid; v < n; v += nth)
                 if (__ldcg(rnd + v) < 0 && __ldcg(deg + v) <= level) {
                     const int64_t idx = (int64_t)atomicAdd(&ctl->acnt[pr], 1) + base;
-                    if (idx >= 0 && idx < n) order[idx] = (int32_t)v;
+                    if (idx >= 0 && idx < n) order[idx] = make_longlong2(off[v], off[v + 1]);
                     rnd[v] = round;
                     core[v] = level;
                 }
@@ -202,23 +275,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
             if (blockIdx.x == 0) {
                 // consecutive small rounds in this block alone
                 int64_t s = S, e = E;
-                if (threadIdx.x == 0) ctl->ltail = (int)e;
-                __syncthreads();
-                while (true) {
-                    peel_remove((int)(e - s), threadIdx.x >> 5, blockDim.x >> 5, order + s, order, off,
-                                adj, deg, rnd, core, &ctl->ltail, 0, n, level, round);
-                    if (threadIdx.x == 0) {
-                        if (level > ctl->degeneracy) ctl->degeneracy = level;
-                        ctl->rounds = round + 1;
-                    }
-                    __syncthreads();
-                    const int64_t e2 = *(volatile int *)&ctl->ltail;
-                    __syncthreads();   // every thread has read ltail before the next appends
-                    ++round;
-                    s = e;
-                    e = e2 < n ? e2 : n;   // (appends beyond n are dropped; caught below)
-                    if (e == s || e - s > PEEL_SMALL) break;   // uniform in the block
-                }
+                peel_local_run(s, e, round, level, n, off, adj, deg, rnd, core, order, ctl);
                 if (threadIdx.x == 0) {
                     ctl->pub_round = round;
                     ctl->pub_start = (int)s;
@@ -365,7 +422,8 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
     out.core = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
     out.rnd = DBuf<int32_t>(c, (size_t)std::max<int64_t>(n, 1));
     if (n > 0) {
-        DBuf<int32_t> deg(c, (size_t)n), order(c, (size_t)n);
+        DBuf<int32_t> deg(c, (size_t)n);
+        DBuf<longlong2> order(c, (size_t)n);
         DBuf<PeelCtl> ctl(c, 1);
         zero(c, ctl.p, sizeof(PeelCtl));
         unsigned int ff = 0xffffffffu;
@@ -388,7 +446,8 @@ void build_graph(const Ctx &c, const kdss_graph_desc &g, int order, GraphDev &ou
         int64_t nn = n;
         const int64_t *offp = out.off.p;
         const int32_t *adjp = out.adj.p;
-        int32_t *degp = deg.p, *rndp = out.rnd.p, *corep = out.core.p, *orderp = order.p;
+        int32_t *degp = deg.p, *rndp = out.rnd.p, *corep = out.core.p;
+        longlong2 *orderp = order.p;
         PeelCtl *ctlp = ctl.p;
         void *args[] = {&nn, &offp, &adjp, &degp, &rndp, &corep, &orderp, &ctlp, &timeout_ns,
                         &phantom};
