@@ -704,10 +704,13 @@ constexpr int SB_ROUNDS = 24;
 // The walk of one pair on levels relative to its lowest receiving node, all
 // in 32 bits: lane j holds node j's relative level rl, its cap cl (0: never
 // receives) and its id (-1 past the pair); n_C = nC32 < 2^31 and every
-// rl < 2^31.  Adds each node's allocation to acc[id].
+// rl < 2^31.  Adds each node's allocation to acc[id].  The walk starts at
+// water level L0 with rem0 units left (0 and n_C from the start; a caller
+// that already took the first rounds passes the state they reached).
 template <class AV>
 __device__ __forceinline__ void walk_rel32(uint32_t rl, uint32_t cl, int32_t id, int len,
-                                           uint32_t nC32, void *acc, uint64_t *sr_w, int *err) {
+                                           uint32_t nC32, void *acc, uint64_t *sr_w, int *err,
+                                           uint32_t L0 = 0u, uint32_t rem0 = 0xffffffffu) {
     const unsigned FULL_ = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     // The walk of Alg. 3 with warp-uniform state: at water level L the
@@ -725,7 +728,7 @@ __device__ __forceinline__ void walk_rel32(uint32_t rl, uint32_t cl, int32_t id,
         // arithmetic: rl and cl are below 2^31, so L - lo wraps to at least
         // 2^31 > cl when lo > L (and cl = 0 never holds).
         const uint32_t lo = cl > 0 ? rl : INF32, hi = rl + cl;
-        uint32_t L = 0, rem = nC32, Ls = 0, R = 0;
+        uint32_t L = L0, rem = rem0 == 0xffffffffu ? nC32 : rem0, Ls = 0, R = 0;
         bool done = false;
         for (int round = 0; round < SB_ROUNDS; ++round) {
             const bool act = L - lo < cl;
@@ -1996,11 +1999,14 @@ __device__ __forceinline__ uint64_t rword_add<double>(uint64_t a, uint64_t b) {
                                           __longlong_as_double((long long)b));
 }
 
-// walk scratch; r words, accumulators and ids of the distinct nodes; local
+// walk scratch; the walk list's first-step states (uint4 each); r words,
+// accumulators and ids of the distinct nodes; walk-list tags and caps; local
 // indices; local pair offsets; the walk list; h
 size_t resident_smem_bytes(int ncap, int pcap, int ucap) {
     size_t b = (size_t)RS_WARPS * 64 * sizeof(uint64_t);
+    b += (size_t)pcap * sizeof(uint4);
     b += (size_t)ucap * (2 * sizeof(uint64_t) + sizeof(int32_t));
+    b += (size_t)pcap * 2 * sizeof(uint32_t);
     b += (size_t)ncap * sizeof(uint16_t);
     b += (size_t)(pcap + 1) * sizeof(uint16_t) + (size_t)pcap * sizeof(uint16_t) + (size_t)pcap;
     return (b + 15) & ~(size_t)15;
@@ -2131,13 +2137,43 @@ k_resident_plan(const int64_t *__restrict__ pair_off, const int32_t *__restrict_
     }
 }
 
+// Lane 0 of a warp waits for walk-list entry wi of iteration tag `tag`:
+// returns 1 once it is written, 0 when it will never be (every first-step
+// tile is done and the list ended before wi) or when the wait ran past its
+// deadline (DERR_TIMEOUT).  The wait sleeps between polls so that the warps
+// still in their first-step tiles keep the issue slots.
+__device__ __forceinline__ int resident_wait_entry(int wi, int np, unsigned tag, const unsigned *stag,
+                                                   const int *s_tdone, const int *s_nslow, int ntile,
+                                                   int *err) {
+    uint64_t t0 = 0;
+    for (unsigned polls = 1;; ++polls) {
+        if (wi < np && *(volatile const unsigned *)(stag + wi) == tag) {
+            __threadfence_block();
+            return 1;
+        }
+        if (*(volatile const int *)s_tdone == ntile) {
+            __threadfence_block();
+            if (wi >= *(volatile const int *)s_nslow) return 0;
+        }
+        if ((polls & 63u) == 0u) {
+            const uint64_t t = globaltimer_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 1000000000ull) {   // 1 s: far beyond any iteration
+                atomicOr(err, DERR_TIMEOUT);
+                return 0;
+            }
+        }
+        __nanosleep(32);
+    }
+}
+
 // L32: every level stays below 2^31 for the whole launch ((t + T) c_k < 2^31,
 // as r_t(u) <= t c_k), so levels, n_C, caps and the per-iteration sums run
 // in 32 bits.
 template <class RT, bool L32>
 __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const ResidentArgs a) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
-    __shared__ int s_cursor, s_nslow, s_wcur;
+    __shared__ int s_cursor, s_nslow, s_wcur, s_tdone;
     // the block accumulates in integers (every allocation is an integer
     // below 2^53, and integer adds are native shared-memory atomics) and
     // converts once per node when it flushes; a node's allocations in one
@@ -2149,11 +2185,14 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint64_t *wsr = reinterpret_cast<uint64_t *>(rs_smem) + wib * 64;
     uint64_t *wsc = wsr + 32;
-    uint64_t *sval = reinterpret_cast<uint64_t *>(rs_smem) + RS_WARPS * 64;
+    uint4 *sent = reinterpret_cast<uint4 *>(rs_smem + (size_t)RS_WARPS * 64 * sizeof(uint64_t));
+    uint64_t *sval = reinterpret_cast<uint64_t *>(sent + a.pcap);
     LT *slev = reinterpret_cast<LT *>(sval);   // integer level of each distinct node
     AV *sacc = reinterpret_cast<AV *>(sval + a.ucap);
     int32_t *suid = reinterpret_cast<int32_t *>(sval + 2 * (size_t)a.ucap);
-    uint16_t *slid = reinterpret_cast<uint16_t *>(suid + a.ucap);
+    unsigned *stag = reinterpret_cast<unsigned *>(suid + a.ucap);
+    uint32_t *scap = stag + a.pcap;
+    uint16_t *slid = reinterpret_cast<uint16_t *>(scap + a.pcap);
     uint16_t *poff = slid + a.ncap;
     uint16_t *slist = poff + a.pcap + 1;
     uint8_t *hh = reinterpret_cast<uint8_t *>(slist + a.pcap);
@@ -2178,6 +2217,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
         const int o = a.loff[q];
         poff[j] = (uint16_t)o;
         hh[j] = a.h[q];
+        stag[j] = 0u;   // no entry of this launch yet (tags are iteration + 1)
         if (o + len <= nn)
             for (int x = 0; x < len; ++x) slid[o + x] = a.lidx[e0 + x];
     }
@@ -2192,10 +2232,12 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
         const uint64_t *Ap = a.A[(j + 2) % 3];
         uint64_t *Az = a.A[(j + 1) % 3];
         GV *gacc = reinterpret_cast<GV *>(a.A[j % 3]);
+        const unsigned tag = (unsigned)j + 1u;
         if (threadIdx.x == 0) {
             s_cursor = 0;
             s_nslow = 0;
             s_wcur = 0;
+            s_tdone = 0;
         }
         // r_j of the block's distinct nodes (L2 reads: other blocks wrote them)
         for (int i = threadIdx.x; i < nu; i += blockDim.x) {
@@ -2203,14 +2245,11 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
             slev[i] = (LT)level_of<RT>(rword_add<RT>(__ldcg(Rc + u), __ldcg(Ap + u)));
             sacc[i] = AV(0);
         }
-        // fold the previous delta into the other copy of r, clear the
-        // delta that iteration j + 1 adds into
-        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-            __stcg(Rn + v, rword_add<RT>(__ldcg(Rc + v), __ldcg(Ap + v)));
-            __stcg(Az + v, 0ull);
-        }
         __syncthreads();
-        // first step of every pair; the pairs it leaves go to the block list
+        // One work loop per warp: first-step tiles while any are left, then
+        // the walks of the pairs they leave.  A warp out of tiles starts on
+        // the walk list while other warps still fill it; every entry carries
+        // a tag (the iteration + 1) written after its fields.
         while (true) {
             int ti = 0;
             if (lane == 0) ti = atomicAdd(&s_cursor, 1);
@@ -2223,15 +2262,16 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
             const int h = valid ? (int)hh[qi] : 0;
             uint32_t rmask = 0;
             bool want_slow = false;
-            LT w = 0, R = 0;
+            LT w = 0, R = 0, m1 = 0, lim = 0, nC = 0, cap_p = 0, na = 0;
             if (valid && h <= k && k <= len && len <= 32) {
                 const int p = len - h;
-                const LT nC = (LT)__ldg(a.binom + (size_t)p * bcols + (k - h));
-                const LT cap_p = (p >= 1 && k - h - 1 >= 0)
-                                     ? (LT)__ldg(a.binom + (size_t)(p - 1) * bcols + (k - h - 1)) : LT(0);
+                nC = (LT)__ldg(a.binom + (size_t)p * bcols + (k - h));
+                cap_p = (p >= 1 && k - h - 1 >= 0)
+                            ? (LT)__ldg(a.binom + (size_t)(p - 1) * bcols + (k - h - 1)) : LT(0);
                 const LT NONE = ~LT(0);
                 const LT pm = cap_p > 0 ? LT(0) : NONE;
-                LT m1 = NONE, m2 = NONE;
+                LT m2 = NONE;
+                m1 = NONE;
                 uint32_t mask1 = 0;
                 bool piv1 = false;
                 for (int s2 = 0; s2 < len; ++s2) {
@@ -2248,14 +2288,22 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
                     piv1 = lt ? !hold : (piv1 || (eq && !hold));
                 }
                 if (mask1) {
-                    const LT na = (LT)__popc(mask1);
+                    na = (LT)__popc(mask1);
                     const LT mu = piv1 ? cap_p : nC;
                     const LT gap = m2 == NONE ? NONE : m2 - m1;
-                    w = nC / na;
-                    R = nC - w * na;
-                    const LT lim = mu < gap ? mu : gap;
-                    if (!(R == 0 ? w > lim : w >= lim)) rmask = mask1;
-                    else want_slow = true;
+                    lim = mu < gap ? mu : gap;
+                    // the first round settles the pair iff the units fit
+                    // below the next event: n_C <= lim * na
+                    bool fits;
+                    if constexpr (L32) fits = (uint64_t)nC <= (uint64_t)lim * na;
+                    else fits = na == 1 ? nC <= lim : lim >= (nC + na - 1) / na;
+                    if (fits) {
+                        w = na == 1 ? nC : nC / na;
+                        R = nC - w * na;
+                        rmask = mask1;
+                    } else {
+                        want_slow = true;
+                    }
                 }
             } else if (valid && len > 32) {
                 atomicOr(a.err, DERR_CAPACITY);
@@ -2265,7 +2313,18 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&s_nslow, __popc(um));
                 base = __shfl_sync(FULL_, base, 0);
-                if (want_slow) slist[base + __popc(um & lanemask_lt())] = (uint16_t)qi;
+                if (want_slow) {
+                    const int slot = base + __popc(um & lanemask_lt());
+                    slist[slot] = (uint16_t)qi;
+                    if constexpr (L32) {
+                        // the walk resumes after the first round: level lim
+                        // above m1 with n_C - lim * na units left
+                        sent[slot] = make_uint4(m1, lim, nC - lim * na, nC);
+                        scap[slot] = cap_p;
+                    }
+                    __threadfence_block();
+                    *(volatile unsigned *)(stag + slot) = tag;
+                }
             }
             LT rank = 0;
             while (__any_sync(FULL_, rmask != 0)) {
@@ -2283,15 +2342,22 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
                 }
                 warp_seg_add<AV>(rid, amount, sacc);
             }
+            if (lane == 0) {   // this tile's reservations precede its count
+                __threadfence_block();
+                atomicAdd(&s_tdone, 1);
+            }
         }
-        __syncthreads();
         // the walks of the block list, one pair per warp at a time
-        const int nslow = s_nslow;
         while (true) {
-            int wi = 0;
-            if (lane == 0) wi = atomicAdd(&s_wcur, 1);
+            int wi = 0, go = 0;
+            if (lane == 0) {
+                wi = atomicAdd(&s_wcur, 1);
+                go = resident_wait_entry(wi, np, tag, stag, &s_tdone, &s_nslow, ntile, a.err);
+            }
+            __syncwarp();
+            go = __shfl_sync(FULL_, go, 0);
+            if (!go) break;
             wi = __shfl_sync(FULL_, wi, 0);
-            if (wi >= nslow) break;
             const int q = slist[wi];
             const int so = poff[q];
             const int sl = (int)poff[q + 1] - so;
@@ -2302,10 +2368,27 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
                 rawc = (int32_t)(l & 0x7fffu) | ((l & 0x8000u) ? (int32_t)0x80000000 : 0);
                 lev = slev[l & 0x7fffu];
             }
-            if constexpr (L32)
-                slow_pair_walk32<AV>(sl, (int)hh[q], rawc, lev, k, a.binom, bcols, sacc, wsr, a.err);
-            else
+            if constexpr (L32) {
+                const uint4 e = sent[wi];   // m1, level and units after the first round, n_C
+                const uint32_t cp = scap[wi];
+                int32_t id = -1;
+                uint32_t cj = 0;
+                if (lane < sl) {
+                    id = rawc & 0x7fffffff;
+                    cj = rawc < 0 ? e.w : cp;
+                }
+                walk_rel32<AV>(cj > 0 ? (uint32_t)lev - e.x : 0u, cj, id, sl, e.w, sacc, wsr, a.err,
+                               e.y, e.z);
+            } else {
                 slow_pair_walk<AV>(sl, (int)hh[q], rawc, lev, k, a.binom, bcols, sacc, wsr, wsc, a.err);
+            }
+        }
+        // fold the previous delta into the other copy of r and clear the
+        // delta that iteration j + 1 adds into (no other block touches these
+        // words in this iteration), while other warps finish their walks
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            __stcg(Rn + v, rword_add<RT>(__ldcg(Rc + v), __ldcg(Ap + v)));
+            __stcg(Az + v, 0ull);
         }
         __syncthreads();
         // one global add per distinct node that received units
@@ -2313,7 +2396,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
             const AV x = sacc[i];
             if (x != AV(0)) atomicAdd(gacc + suid[i], (GV)x);
         }
-        if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
+        if (!grid_sync_count(&a.bar->count, (unsigned)(j + 1) * (unsigned)G, a.err, a.timeout_ns)) return;
     }
     // r_T = R[T%2] + A[(T+2)%3] into R[0]; clear the two deltas still set
     const uint64_t *Rc = a.R[a.T & 1];
@@ -2451,6 +2534,8 @@ void fw_run_resident(const Ctx &c, const SctDev &s, StateDev &st, int T, bool pr
                             ((long double)st.ck_lo + (long double)st.ck_hi * 18446744073709551616.0L);
     auto kern = resident_kernel(st.precision, top < 2147483648.0L);
     void *args[] = {&a};
+    // the barrier counter starts from zero in every launch
+    zero(c, st.res_bar.p, sizeof(GridBarrier));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profile) {
         while (st.events.size() < 2) {

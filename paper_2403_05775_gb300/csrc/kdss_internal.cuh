@@ -226,6 +226,38 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned int nblo
     return s_ok != 0;
 }
 
+// Grid barrier on a counter that only grows: every block adds 1 per barrier,
+// and barrier number e (from 1) is passed once the counter reaches e x the
+// number of blocks.  The counter starts at zero for each launch (the host
+// clears it), so no block resets anything: an arrival is one release add and
+// a wait polls with acquire loads.  Returns false when the wait timed out
+// (the error word then holds DERR_TIMEOUT).
+__device__ __forceinline__ bool grid_sync_count(unsigned int *count, unsigned int target, int *err,
+                                                uint64_t timeout_ns) {
+    __syncthreads();
+    __shared__ int s_okc;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        int ok = 1;
+        const uint64_t t0 = globaltimer_ns();
+        unsigned int polls = 0;
+        while (true) {
+            unsigned int cur;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+            if ((int)(cur - target) >= 0) break;
+            if ((++polls & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+                atomicOr(err, DERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        s_okc = ok;
+    }
+    __syncthreads();
+    return s_okc != 0;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
