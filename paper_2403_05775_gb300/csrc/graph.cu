@@ -217,6 +217,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
     // phantom > 0 (failure-injection test only): the barriers wait for blocks
     // that do not exist, so the first wait expires in every block
     const unsigned int nb = gridDim.x + phantom;
+    unsigned int epoch = 0;      // grid barriers passed (the host clears the counter)
     int level = 0, round = 0;
     int64_t S = 0, E = 0;        // this round's frontier: order[S, E)
     int last0 = 0, last1 = 0;    // acnt[0], acnt[1] as this block last read them
@@ -246,7 +247,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
                 mn = t < mn ? t : mn;
             }
             if ((threadIdx.x & 31) == 0 && mn != 0xffffffffu) atomicMin(&ctl->minval, mn);
-            if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+            if (!grid_sync_count(&ctl->bar.count, ++epoch * nb, &ctl->err, timeout_ns)) return;
             unsigned int mv = *(volatile unsigned int *)&ctl->minval;
             if (mv == 0xffffffffu) {  // nothing alive: inconsistent counters
                 if (tid == 0) atomicOr(&ctl->err, DERR_LOGIC);
@@ -263,7 +264,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
                     rnd[v] = round;
                     core[v] = level;
                 }
-            if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+            if (!grid_sync_count(&ctl->bar.count, ++epoch * nb, &ctl->err, timeout_ns)) return;
             // minval is next read after at least one more barrier
             if (tid == 0) ctl->minval = 0xffffffffu;
             const int a = vacnt[pr];
@@ -282,7 +283,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
                     ctl->pub_end = (int)e;
                 }
             }
-            if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+            if (!grid_sync_count(&ctl->bar.count, ++epoch * nb, &ctl->err, timeout_ns)) return;
             round = *(volatile int *)&ctl->pub_round;
             S = *(volatile int *)&ctl->pub_start;
             E = *(volatile int *)&ctl->pub_end;
@@ -297,7 +298,7 @@ k_peel(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ a
             if (level > ctl->degeneracy) ctl->degeneracy = level;
             ctl->rounds = round + 1;
         }
-        if (!grid_barrier(&ctl->bar, nb, &ctl->err, timeout_ns)) return;
+        if (!grid_sync_count(&ctl->bar.count, ++epoch * nb, &ctl->err, timeout_ns)) return;
         S = E;
         ++round;
     }

@@ -166,11 +166,12 @@ void row_offsets_from_sorted(const Ctx &c, const uint64_t *keys, int64_t nkeys, 
 // Max of a u64 array (synchronises).
 uint64_t reduce_max_u64(const Ctx &c, const uint64_t *in, int64_t n);
 
-// Bounded grid barrier for cooperative kernels: every wait gives up after a
-// deadline (ns of %globaltimer) and sets DERR_TIMEOUT in *err.
+// State of the bounded grid barrier of the cooperative kernels
+// (grid_sync_count below): arrivals so far, cleared by the host before each
+// launch.  Every wait gives up after a deadline (ns of %globaltimer) and sets
+// DERR_TIMEOUT in the kernel's error word.
 struct GridBarrier {
     unsigned int count;
-    unsigned int gen;
 };
 
 }  // namespace kdss
@@ -187,45 +188,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// All threads of all (co-resident) blocks call this.  Returns false when the
-// wait timed out (the error word then holds DERR_TIMEOUT).
-__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned int nblocks, int *err,
-                                             uint64_t timeout_ns) {
-    __syncthreads();
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &bar->gen;
-        unsigned int g = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&bar->count, 1u);
-        int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            // poll without sleeping (the wait is usually a few microseconds);
-            // check the deadline only every 256 polls
-            uint64_t t0 = globaltimer_ns();
-            unsigned int polls = 0;
-            while (true) {
-                unsigned int cur;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
-                if (cur != g) break;
-                if ((++polls & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
-                    atomicOr(err, DERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Grid barrier on a counter that only grows: every block adds 1 per barrier,
 // and barrier number e (from 1) is passed once the counter reaches e x the
 // number of blocks.  The counter starts at zero for each launch (the host
@@ -237,7 +199,8 @@ __device__ __forceinline__ bool grid_sync_count(unsigned int *count, unsigned in
     __syncthreads();
     __shared__ int s_okc;
     if (threadIdx.x == 0) {
-        __threadfence();
+        // the release orders every write of the block before the arrival:
+        // bar.sync above places the other threads' writes before it
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();

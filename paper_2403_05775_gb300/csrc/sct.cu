@@ -185,7 +185,11 @@ k_sct(int64_t n, const int64_t *__restrict__ out_off, const int32_t *__restrict_
         }
         rr = __shfl_sync(FULL, rr, 0);
         if (rr >= (unsigned long long)NI) break;
-        const int64_t item = (int64_t)rr;
+        // items are handed out last to first: the roots late in the build
+        // order (the densest region, the longest recursions) start first and
+        // the many short items fill in behind them; every pass maps the
+        // counter to items the same way, so outputs keep their item slots
+        const int64_t item = MODE == MODE_TOTAL ? (int64_t)rr : NI - 1 - (int64_t)rr;
         const uint32_t *rec = items.rec ? items.rec + (size_t)item * items.stride : nullptr;
         const int64_t root = rec ? (int64_t)rec[0]
                                  : (MODE == MODE_TOTAL ? (int64_t)(((unsigned long long)item * po.perm_mul) %
