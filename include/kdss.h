@@ -316,6 +316,44 @@ kdss_status kdss_fw_iterate_at(kdss_sct *s, int32_t k, kdss_state **state, int32
                                const kdss_opts *opts);
 
 /*
+ * kdss_sct_share_prefixes -- the prefix-shared form of an SCT's pairs (Sec. 2,
+ * Lemmas 2.4-2.5: the pairs of one recursion repeat its hold and pivot
+ * nodes).  Within each length class the pairs are put in lexicographic order
+ * of their node lists (ids ascending, V_h and V_p marked), and each pair keeps
+ * only the nodes after the prefix it shares with the pair before it; every
+ * block of 32 pairs starts with a pair kept whole.  The kept nodes are the
+ * nodes of the prefix tree of the pairs, so equal prefixes are stored once.
+ *   in          : a k-pruned or k-agnostic SCT handle (flat pairs); it stays
+ *                 valid and owned by the caller.
+ *   chunk_pairs : pairs decoded at a time when iterating or extracting
+ *                 (rounded to whole blocks; 0 = 2^22).
+ *   out         : a new handle (free it with kdss_sct_free) holding the
+ *                 shared form, the counts and the binomial tables, and no
+ *                 graph.
+ * The new handle iterates with kdss_fw_iterate / kdss_fw_iterate_at
+ * (synchronous rule, any precision; r_T equal bit for bit to the flat
+ * handle's in the integer rule) and extracts with kdss_extract: each
+ * iteration decodes one chunk at a time into the flat layout on the device
+ * and runs the same PBUpdate kernels, so the flat pairs exist one chunk at a
+ * time.  kdss_sct_info reports the same eta_k, L_k and c_k, and device_bytes
+ * of the shared form; kdss_sct_copy_pairs returns the pairs in the shared
+ * order.  KDSS_FLAG_ASYNC, work-queue chunks, kdss_sct_restrict, the explicit
+ * clique list and kdss_fw_iterate_noalloc need the flat handle (INVALID_ARG or
+ * UNSUPPORTED).
+ * Errors: INVALID_ARG (NULL, chunk_pairs < 0, a shared input), UNSUPPORTED
+ *   (2^31 pairs or more), OOM, CUDA.
+ */
+kdss_status kdss_sct_share_prefixes(const kdss_sct *in, int64_t chunk_pairs, const kdss_opts *opts,
+                                    kdss_sct **out);
+
+/*
+ * kdss_sct_shared_words -- node words kept by a prefix-shared SCT (against
+ * L_k of the flat pairs) and the chunks an iteration decodes.  Either output
+ * may be NULL.  Errors: INVALID_ARG (NULL handle, not prefix-shared).
+ */
+kdss_status kdss_sct_shared_words(const kdss_sct *s, int64_t *words, int64_t *chunks);
+
+/*
  * kdss_fw_cliques -- T iterations of Alg. 1 (the Frank-Wolfe step over the
  * explicit k-clique list): every k-clique gives its unit to its member of
  * least (r, id), all cliques of iteration t reading r_{t-1} (synchronous

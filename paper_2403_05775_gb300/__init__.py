@@ -180,6 +180,8 @@ def load(build_if_missing: bool = False):
             "kdss_fw_cliques": (i32, [vp, P(vp), i32, P(kdss_opts)]),
             "kdss_build_sct_multi": (i32, [P(kdss_graph_desc), i32, P(kdss_opts), P(vp)]),
             "kdss_sct_restrict": (i32, [vp, i32, P(kdss_opts), P(vp)]),
+            "kdss_sct_share_prefixes": (i32, [vp, i64, P(kdss_opts), P(vp)]),
+            "kdss_sct_shared_words": (i32, [vp, P(i64), P(i64)]),
             "kdss_cpsample": (i32, [P(kdss_graph_desc), i32, i64, i32, C.c_uint64, P(kdss_opts),
                                     P(kdss_result), P(kdss_cpsample_stats)]),
             "kdss_sct_copy_cliques": (i32, [vp, vp, i64, P(i64)]),
@@ -347,6 +349,21 @@ def kdss_sct_restrict(multi: Sct, k, opts: kdss_opts | None = None) -> Sct:
     out = C.c_void_p()
     _check(load().kdss_sct_restrict(multi.ptr, int(k), C.byref(opts or make_opts()), C.byref(out)))
     return Sct(out.value)
+
+
+def kdss_sct_share_prefixes(s: Sct, chunk_pairs: int = 0, opts: kdss_opts | None = None) -> Sct:
+    """The prefix-shared form of an SCT's pairs as a new handle."""
+    out = C.c_void_p()
+    _check(load().kdss_sct_share_prefixes(s.ptr, int(chunk_pairs), C.byref(opts or make_opts()),
+                                          C.byref(out)))
+    return Sct(out.value)
+
+
+def kdss_sct_shared_words(s: Sct) -> dict:
+    """Node words kept by a prefix-shared SCT and the chunks an iteration decodes."""
+    w, ch = C.c_int64(0), C.c_int64(0)
+    _check(load().kdss_sct_shared_words(s.ptr, C.byref(w), C.byref(ch)))
+    return {"words": w.value, "chunks": ch.value}
 
 
 def kdss_sct_count(n, src, dst, k, budget_s=0.0, opts: kdss_opts | None = None) -> dict:

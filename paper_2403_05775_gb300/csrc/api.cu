@@ -70,7 +70,15 @@ int64_t sct_bytes(const kdss_sct *h) {
     const SctDev &s = h->s;
     return (int64_t)(g.off.bytes() + g.adj.bytes() + g.core.bytes() + g.rnd.bytes() +
                      g.rank.bytes() + g.vert.bytes() + g.out_off.bytes() + g.out_adj.bytes() +
-                     s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + binom_bytes(s));
+                     s.pair_off.bytes() + s.nodes.bytes() + s.h.bytes() + binom_bytes(s) +
+                     (h->shared ? h->fc.bytes() : 0));
+}
+
+// Calls that need the flat pairs refuse the prefix-shared form.
+void require_flat(const kdss_sct *s) {
+    if (s->shared)
+        fail(KDSS_ERR_INVALID_ARG,
+             "a prefix-shared SCT: this call needs the flat pairs (keep the handle it was made from)");
 }
 
 kdss_status build_impl(const kdss_graph_desc *g, int32_t k, const kdss_opts *opts, kdss_sct **out,
@@ -137,6 +145,7 @@ kdss_status kdss_sct_restrict(const kdss_sct *multi, int32_t k, const kdss_opts 
     API_BEGIN
     if (!multi || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
+    require_flat(multi);
     if (multi->kmax_multi <= 0) fail(KDSS_ERR_INVALID_ARG, "not a k-agnostic SCT (kdss_build_sct_multi)");
     if (k < 2 || k > multi->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "k must be in [2, k_max of the SCT]");
     Ctx c = make_ctx(opts);
@@ -288,11 +297,14 @@ kdss_status kdss_sct_copy_pairs(const kdss_sct *s, int64_t *pair_off, int32_t *n
     API_BEGIN
     if (!s) fail(KDSS_ERR_INVALID_ARG, "NULL handle");
     const Ctx &c = s->ctx;
-    if (pair_off) to_host(c, pair_off, s->s.pair_off.p, (size_t)s->s.npairs + 1);
-    if (nodes) to_host(c, nodes, s->s.nodes.p, (size_t)s->s.nnodes);
+    SctDev dec;
+    if (s->shared) fc_decode_all(c, s->s, s->fc, dec);   // the pairs in the shared order
+    const SctDev &f = s->shared ? dec : s->s;
+    if (pair_off) to_host(c, pair_off, f.pair_off.p, (size_t)s->s.npairs + 1);
+    if (nodes) to_host(c, nodes, f.nodes.p, (size_t)s->s.nnodes);
     if (h && s->s.npairs > 0) {
         std::vector<uint8_t> tmp((size_t)s->s.npairs);
-        to_host(c, tmp.data(), s->s.h.p, tmp.size());
+        to_host(c, tmp.data(), f.h.p, tmp.size());
         for (size_t i = 0; i < tmp.size(); ++i) h[i] = tmp[i];
     }
     API_END
@@ -329,6 +341,10 @@ kdss_status fw_iterate_impl(kdss_sct *s, int32_t k, kdss_state **state, int32_t 
     if (*state && k >= 0 && (*state)->st.k != k)
         fail(KDSS_ERR_INVALID_ARG, "the state iterates another k");
     Ctx c = make_ctx(opts);
+    if (s->shared && opts && ((opts->flags & KDSS_FLAG_ASYNC) || opts->chunk > 0))
+        fail(KDSS_ERR_UNSUPPORTED,
+             "a prefix-shared SCT iterates in the synchronous form on the per-class kernels "
+             "(no KDSS_FLAG_ASYNC, no work-queue chunk)");
     bool created = false;
     if (!*state) {
         const int prec = opts ? opts->precision : KDSS_INT64;
@@ -341,7 +357,8 @@ kdss_status fw_iterate_impl(kdss_sct *s, int32_t k, kdss_state **state, int32_t 
         }
         st->st.force_rooted = opts && (opts->flags & KDSS_FLAG_ROOTED);
         try {
-            fw_init(c, s->s, prec, st->st, k);
+            if (s->shared) fc_state_init(c, s->s, s->fc, k < 0 ? s->s.k : k, prec, st->st);
+            else fw_init(c, s->s, prec, st->st, k);
         } catch (...) {
             delete st;
             throw;
@@ -352,7 +369,9 @@ kdss_status fw_iterate_impl(kdss_sct *s, int32_t k, kdss_state **state, int32_t 
     if ((*state)->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
     (*state)->st.per_iteration = opts && (opts->flags & KDSS_FLAG_PER_ITERATION);
     try {
-        if (opts && (opts->flags & KDSS_FLAG_ASYNC))
+        if (s->shared)
+            fc_iterate(c, s->s, s->fc, (*state)->st, T, opts && (opts->flags & KDSS_FLAG_PROFILE));
+        else if (opts && (opts->flags & KDSS_FLAG_ASYNC))
             fw_run_async(c, s->s, (*state)->st, T);
         else
             fw_run(c, s->s, (*state)->st, T, opts && (opts->flags & KDSS_FLAG_PROFILE));
@@ -378,6 +397,7 @@ kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacit
                                   int64_t *count) {
     API_BEGIN
     if (!s || !count) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    require_flat(s);
     if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (capacity < 0 || (capacity > 0 && !cliques)) fail(KDSS_ERR_INVALID_ARG, "bad output buffer");
     if (s->nclq < 0) expand_cliques(s->ctx, s->s, s->cliques, s->nclq);
@@ -390,6 +410,7 @@ kdss_status kdss_sct_copy_cliques(kdss_sct *s, int32_t *cliques, int64_t capacit
 kdss_status kdss_fw_cliques(kdss_sct *s, kdss_state **state, int32_t T, const kdss_opts *opts) {
     API_BEGIN
     if (!s || !state) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    require_flat(s);
     if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
     if (T < 0) fail(KDSS_ERR_INVALID_ARG, "T must be >= 0");
     Ctx c = make_ctx(opts);
@@ -465,7 +486,65 @@ kdss_status kdss_extract(const kdss_sct *s, const kdss_state *st, const kdss_opt
     if (st->st.n != s->s.n) fail(KDSS_ERR_INVALID_ARG, "state and SCT differ in n");
     if (st->st.k < 2 || st->st.k > s->s.k) fail(KDSS_ERR_INVALID_ARG, "the state's k is not in the SCT");
     Ctx c = make_ctx(opts);
-    extract_prefix(c, s->s, st->st, out);
+    if (s->shared) fc_extract(c, s->s, s->fc, st->st, out);
+    else extract_prefix(c, s->s, st->st, out);
+    API_END
+}
+
+kdss_status kdss_sct_share_prefixes(const kdss_sct *in, int64_t chunk_pairs, const kdss_opts *opts,
+                                    kdss_sct **out) {
+    API_BEGIN
+    if (!in || !out) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    require_flat(in);
+    if (chunk_pairs < 0) fail(KDSS_ERR_INVALID_ARG, "chunk_pairs must be >= 0");
+    Ctx c = make_ctx(opts);
+    kdss_sct *h = new kdss_sct();
+    try {
+        h->ctx = c;
+        const SctDev &f = in->s;
+        SctDev &m = h->s;
+        m.k = f.k;
+        m.n = f.n;
+        m.npairs = f.npairs;
+        m.nnodes = f.nnodes;
+        for (int cl = 0; cl <= NCLASS; ++cl) m.class_begin[cl] = f.class_begin[cl];
+        m.ck_lo = f.ck_lo;
+        m.ck_hi = f.ck_hi;
+        m.max_len = f.max_len;
+        m.binom = DBuf<uint64_t>(c, f.binom.n);
+        m.binom128 = DBuf<U128>(c, f.binom128.n);
+        m.binomf = DBuf<float>(c, f.binomf.n);
+        if (f.binom.n)
+            KDSS_CUDA(cudaMemcpyAsync(m.binom.p, f.binom.p, f.binom.bytes(), cudaMemcpyDeviceToDevice, c.stream));
+        if (f.binom128.n)
+            KDSS_CUDA(cudaMemcpyAsync(m.binom128.p, f.binom128.p, f.binom128.bytes(),
+                                      cudaMemcpyDeviceToDevice, c.stream));
+        if (f.binomf.n)
+            KDSS_CUDA(cudaMemcpyAsync(m.binomf.p, f.binomf.p, f.binomf.bytes(), cudaMemcpyDeviceToDevice,
+                                      c.stream));
+        m.binom_rows = f.binom_rows;
+        fc_encode(c, f, chunk_pairs > 0 ? chunk_pairs : (int64_t)1 << 22, h->fc);
+        h->shared = true;
+        h->m = in->m;
+        h->degeneracy = in->degeneracy;
+        h->max_out = in->max_out;
+        h->kmax_multi = in->kmax_multi;
+        sync(c);
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    API_END
+}
+
+kdss_status kdss_sct_shared_words(const kdss_sct *s, int64_t *words, int64_t *chunks) {
+    API_BEGIN
+    if (!s) fail(KDSS_ERR_INVALID_ARG, "NULL handle");
+    if (!s->shared) fail(KDSS_ERR_INVALID_ARG, "not a prefix-shared SCT (kdss_sct_share_prefixes)");
+    if (words) *words = s->fc.nwords;
+    if (chunks) *chunks = (int64_t)s->fc.chunks.size();
     API_END
 }
 

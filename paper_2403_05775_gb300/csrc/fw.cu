@@ -2844,18 +2844,19 @@ void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, S
     fw_init(c, shell, precision, st);
 }
 
-void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off) {
+void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off, int k) {
+    if (k < 0) k = s.k;
     // the slow-pair list is shared by the groups of one iteration
     KDSS_CUDA(cudaMemsetAsync(st.ovf_count.p, 0, sizeof(int), c.stream));
     if (st.precision == KDSS_FP32K) {
-        launch_pbupdate_f32_on(c, s, s.k, st, st.r32.p + node_off, st.a32.p + node_off,
+        launch_pbupdate_f32_on(c, s, k, st, st.r32.p + node_off, st.a32.p + node_off,
                                st.a32c.p + node_off);
     } else if (st.precision == KDSS_FP64) {
-        launch_pbupdate_int<double>(c, s, s.k, (double *)st.r.p + node_off,
+        launch_pbupdate_int<double>(c, s, k, (double *)st.r.p + node_off,
                                     (double *)st.acc.p + node_off, st.ovf_list.p, st.ovf_count.p,
                                     st.err.p);
     } else {
-        launch_pbupdate_int<uint64_t>(c, s, s.k, st.r.p + node_off, st.acc.p + node_off,
+        launch_pbupdate_int<uint64_t>(c, s, k, st.r.p + node_off, st.acc.p + node_off,
                                       st.ovf_list.p, st.ovf_count.p, st.err.p);
     }
 }

@@ -98,7 +98,8 @@ void fw_run_async(const Ctx &c, const SctDev &s, StateDev &st, int T);
 void fw_enqueue_inplace(const Ctx &c, const SctDev &s, StateDev &st);
 // batches: several SCTs over disjoint node ranges of one state
 void fw_init_n(const Ctx &c, int64_t n, int64_t short_capacity, int precision, StateDev &st);
-void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off);
+// k < 0: the SCT's own k; otherwise P_k of a k-agnostic SCT (the P_k filter).
+void fw_enqueue_group(const Ctx &c, const SctDev &s, StateDev &st, int64_t node_off, int k = -1);
 void fw_enqueue_step_range(const Ctx &c, StateDev &st, int64_t node_off, int64_t n, bool advance);
 long long fw_capture(const Ctx &c, cudaGraphExec_t *exec, const std::function<void(const Ctx &)> &fn);
 // Work-queue PBUpdate: one launch over every (SCT, state slice) of `sets`.
@@ -120,5 +121,13 @@ void prefix_add(const Ctx &c, const SctDev &s, int k, PrefixAcc &a);
 void prefix_end(const Ctx &c, PrefixAcc &a, const StateDev &st, kdss_result *out);
 void fw_run_external(const Ctx &c, const SctDev &s, uint64_t *r, uint64_t *acc, int32_t *slow,
                      int *slow_count, int *err, unsigned long long *maxr, int T);
+// Prefix-shared SCTs (share.cu): encoding of a flat SCT, c_k at k, states,
+// synchronous iterations and extraction chunk by chunk, and a full decode.
+void fc_encode(const Ctx &c, const SctDev &s, int64_t chunk_pairs, FcDev &fc);
+void fc_ck_at(const Ctx &c, const SctDev &meta, const FcDev &fc, int k, uint64_t &lo, uint64_t &hi);
+void fc_state_init(const Ctx &c, const SctDev &meta, const FcDev &fc, int k, int precision, StateDev &st);
+void fc_iterate(const Ctx &c, const SctDev &meta, const FcDev &fc, StateDev &st, int T, bool profile);
+void fc_extract(const Ctx &c, const SctDev &meta, const FcDev &fc, const StateDev &st, kdss_result *out);
+void fc_decode_all(const Ctx &c, const SctDev &meta, const FcDev &fc, SctDev &out);
 
 }  // namespace kdss

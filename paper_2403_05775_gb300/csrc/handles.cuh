@@ -14,6 +14,10 @@ struct kdss_sct {
     int kmax_multi = 0;           // > 0: a k-agnostic SCT for k <= kmax_multi (restrict first)
     kdss::DBuf<int32_t> cliques;  // explicit k-clique list (expanded on first use)
     int64_t nclq = -1;            // its length, -1 before expansion
+    // prefix-shared form (kdss_sct_share_prefixes): the pairs live in `fc`;
+    // `s` keeps the counts, classes and binomial tables, not the pairs
+    bool shared = false;
+    kdss::FcDev fc;
 };
 
 namespace kdss {

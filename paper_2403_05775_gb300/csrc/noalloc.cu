@@ -108,6 +108,7 @@ extern "C" kdss_status kdss_fw_iterate_noalloc(const kdss_sct *s, uint64_t *r, i
     try {
         if (!s || !r) fail(KDSS_ERR_INVALID_ARG, "NULL argument");
         if (s->kmax_multi) fail(KDSS_ERR_INVALID_ARG, "a k-agnostic SCT: restrict it to one k first");
+        if (s->shared) fail(KDSS_ERR_INVALID_ARG, "a prefix-shared SCT: iterate it with kdss_fw_iterate");
         if (T < 0 || t_done < 0) fail(KDSS_ERR_INVALID_ARG, "T and t_done must be >= 0");
         const SctDev &sd = s->s;
         int dev = 0;

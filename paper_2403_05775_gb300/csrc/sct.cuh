@@ -52,6 +52,33 @@ struct SctDev {
     bool rooted() const { return proot.p != nullptr; }
 };
 
+// Prefix-shared form of an SCT's pairs (front coding).  Within each length
+// class the pairs are in lexicographic order of their node words (ids
+// ascending, HOLD_BIT on V_h nodes), so pairs that share a prefix of nodes
+// sit together; a pair keeps only the words after the prefix it shares with
+// the pair before it, and every block of FC_BLOCK pairs (a warp, a lane per
+// pair) starts with a pair kept whole.  The FW iterations and the
+// extraction decode chunks of whole blocks into the flat layout of SctDev.
+constexpr int FC_BLOCK = 32;
+struct FcDev {
+    int64_t npairs = 0, nnodes = 0, nwords = 0, nblocks = 0;
+    DBuf<uint32_t> words;                  // [nwords + 1] the kept node words
+    DBuf<uint16_t> lcp, len;               // [npairs] shared prefix, length
+    DBuf<uint8_t> h;                       // [npairs] |V_h|
+    DBuf<int64_t> bpair, bword, bnode;     // [nblocks + 1] first pair, first kept word,
+                                           // first flat node of every block
+    struct Chunk {
+        int64_t b0, b1, p0, p1, n0, n1;    // blocks, pairs and flat nodes of the chunk
+        int64_t class_begin[NCLASS + 1];   // relative to p0
+    };
+    std::vector<Chunk> chunks;
+    int64_t max_chunk_pairs = 0, max_chunk_nodes = 0, max_chunk_short = 0;
+    int64_t bytes() const {
+        return (int64_t)(words.bytes() + lcp.bytes() + len.bytes() + h.bytes() + bpair.bytes() +
+                         bword.bytes() + bnode.bytes());
+    }
+};
+
 // Host tables of C(a, b) for a < rows, b <= k: in 64 bits (entries that need
 // 63 bits or more hold ~0ull, treated as overflow by the integer kernels),
 // in 128 bits (U128_OVF beyond) and rounded to float.
