@@ -360,11 +360,27 @@ def k_agnostic(K, torch, dev, n, src, dst, kmax=8):
                     "same_size": ia["eta_k"] == K.kdss_sct_info(b)["eta_k"]}
         a.free()
         b.free()
+    # the prefix-shared form of the k-agnostic SCT, iterated at k = 5 where it
+    # stands, against the flat form (bytes of the pair stream per iteration)
+    sh, ms_share = wall(lambda: K.kdss_sct_share_prefixes(multi))
+    words = K.kdss_sct_shared_words(sh)["words"]
+    eta, L = info["eta_k"], info["L_k"]
+    shared = {"share_ms": ms_share, "kept_words": words, "node_words": L,
+              "pair_bytes_flat": 4 * L + 9 * eta,
+              "pair_bytes_shared": 4 * words + 5 * eta + 24 * -(-eta // 32)}
+    o = K.make_opts(precision=K.KDSS_FP64, flags=K.KDSS_FLAG_PROFILE)
+    for name, h in (("flat", multi), ("shared", sh)):
+        st = K.kdss_fw_iterate_at(h, 5, None, 20, o)
+        tm = K.kdss_state_timing(st)
+        shared[f"us_per_iteration_at_k5_{name}"] = 1e3 * tm["fw_kernel_ms"] / max(tm["fw_launches"], 1)
+        st.free()
+    sh.free()
     multi.free()
     return {"k_max": kmax, "multi_build_ms": ms_multi, "multi_pairs": info["eta_k"],
             "multi_nodes": info["L_k"], "per_k": per_k,
             "all_k_restrict_ms": ms_multi + sum(v["restrict_ms"] for v in per_k.values()),
-            "all_k_build_ms": sum(v["build_ms"] for v in per_k.values())}
+            "all_k_build_ms": sum(v["build_ms"] for v in per_k.values()),
+            "prefix_shared": shared}
 
 
 def large_rmat_report(K, torch, dev):
