@@ -498,10 +498,12 @@ typedef struct kdss_query {
 kdss_status kdss_solve_batch(const kdss_query *q, int32_t nq, kdss_result *out,
                              const kdss_opts *opts);
 
-/* What the last kdss_solve_batch of the calling thread ran its integer-rule
- * iterations with: the chunk and lanes per long pair it used and, when it
- * tuned them, the configurations it timed (one iteration each, after two
- * warm-up iterations; every one of those is an iteration of the run). */
+/* What the last kdss_solve_batch of the calling thread ran its iterations
+ * with: the chunk (tiles of 32 pairs per work item of the work-queue pass;
+ * 0 = each group's per-class kernels in turn) and lanes per long pair it used
+ * and, when it tuned them, the configurations it timed (one iteration each,
+ * after two warm-up iterations; every one of those is an iteration of the
+ * run). */
 typedef struct kdss_batch_tuning {
     int32_t chunk;
     int32_t threads_per_path;

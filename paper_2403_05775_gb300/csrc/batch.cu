@@ -415,10 +415,11 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
     for (Group *g : gl) Ts.push_back(g->T);
     std::sort(Ts.begin(), Ts.end());
     Ts.erase(std::unique(Ts.begin(), Ts.end()), Ts.end());
-    // Every iteration is one work-queue pass over every active group
-    // (k_pb_queue / k_pb_queue_f32 and the long-pair queue kernels) and the
-    // groups' steps, as one replayed CUDA graph.
-    const bool queue = true;
+    // Every iteration is one replayed CUDA graph: a work-queue pass over
+    // every active group (k_pb_queue / k_pb_queue_f32 and the long-pair queue
+    // kernels, `chunk` tiles per item), or the per-class kernels of each
+    // group in turn (chunk 0), then the groups' steps.  The autotuner times
+    // both forms on the run's own iterations.
     int chunk = opts ? opts->chunk : 0, tpp = opts ? opts->threads_per_path : 0;
     BatchTuning tune;
     int done = 0;
@@ -453,18 +454,12 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
                 cudaEventDestroy(e1);
             }
         };
-        if (!queue) {
-            cudaGraphExec_t exec = nullptr;
-            const long long nk = fw_capture(c, &exec, [&](const Ctx &cc) {
-                for (Group *g : act) fw_enqueue_group(cc, g->s, st, g->node_off);
-                steps(cc);
-            });
-            run(exec, nk, Tp - done, nullptr);
-            cudaGraphExecDestroy(exec);
-            done = Tp;
-            continue;
-        }
         auto graph_for = [&](int ch, int tp, QueuePlan &qp, cudaGraphExec_t *exec) {
+            if (ch <= 0)
+                return fw_capture(c, exec, [&](const Ctx &cc) {
+                    for (Group *g : act) fw_enqueue_group(cc, g->s, st, g->node_off);
+                    steps(cc);
+                });
             queue_plan(c, sets, ch, tp, qp);
             return fw_capture(c, exec, [&](const Ctx &cc) {
                 queue_enqueue(cc, qp, st);
@@ -479,6 +474,7 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
             std::vector<std::pair<int, int>> cand;
             bool has_long = false;
             for (Group *g : act) has_long |= g->s.class_begin[4] > g->s.class_begin[3];
+            if (chunk <= 0 && (tpp <= 0 || tpp == 32)) cand.push_back({0, 32});   // per-class kernels
             for (int ch : {1, 4, 16})
                 for (int tp : {32, 8})
                     if ((chunk <= 0 || ch == chunk) && (tpp <= 0 || tp == tpp) && (tp == 32 || has_long))
@@ -519,7 +515,7 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
         tune.tpp = tp;
         done = Tp;
     }
-    set_last_batch_tuning(queue ? tune : BatchTuning{});
+    set_last_batch_tuning(tune);
     int herr = 0;
     to_host(c, &herr, st.err.p, 1);
     if (herr) fail(KDSS_ERR_CUDA, "batch FW: water-filling invariant failed on the device");
