@@ -76,14 +76,16 @@ typedef int32_t kdss_status;
  * gathered once per tile) whatever the SCT's size; by default it is used only
  * when the SCT's node stream exceeds 96 MiB (beyond L2). */
 #define KDSS_FLAG_ROOTED 16u
-/* Integer-rule iterations as launches per iteration (CUDA graphs of the
- * PBUpdate kernels and the step) even where the resident launch applies.  By
- * default, when every pair of the SCT has at most 32 nodes and the pairs fit
+/* Iterations as launches per iteration (CUDA graphs of the PBUpdate kernels
+ * and the step) even where the resident launch applies.  By default (the
+ * integer rule and the FP32 continuous rule alike), when every pair of the
+ * SCT has at most 32 nodes and the pairs fit
  * the blocks' shared memory (one block per SM, 12 bytes per pair node: about
  * 18,000 pair nodes per SM), kdss_fw_iterate runs all T iterations in one
  * cooperative launch that keeps the pair stream in shared memory and ends
  * each iteration on a bounded grid barrier.  Both forms give the same r bit
- * for bit; with KDSS_FLAG_PROFILE the resident launch is timed as a whole and
+ * for bit in the integer rule (the FP32 rule rounds its sums in another
+ * order); with KDSS_FLAG_PROFILE the resident launch is timed as a whole and
  * kdss_timing counts it as T PBUpdate passes with the step inside. */
 #define KDSS_FLAG_PER_ITERATION 32u
 

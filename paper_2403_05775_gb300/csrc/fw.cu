@@ -1308,11 +1308,13 @@ k_pb_fast_f32s(const int64_t *__restrict__ pair_off, const int32_t *__restrict__
 // (k_pb_slow_f32's walk and closed form): lane j holds node j (raw id with the
 // V_h mark in rawc, its r/t value xc); lanes >= len hold nothing.  nC_raw
 // and the caps come from the float table, scaled by inv_sigma.  sp_w: 32
-// float2 of this warp's shared memory.
-__device__ __forceinline__ void slow_pair_walk_f32(int len, int h, int32_t rawc, float xc, int k,
-                                                   const float *__restrict__ binomf, int bcols,
-                                                   float inv_sigma, float *acc, float *accc,
-                                                   float2 *sp_w, int *err) {
+// float2 of this warp's shared memory.  add(id, x) receives each node's
+// allocation (the compensated global add, or a shared-memory accumulator).
+template <class Add>
+__device__ __forceinline__ void slow_pair_walk_f32_to(int len, int h, int32_t rawc, float xc, int k,
+                                                      const float *__restrict__ binomf, int bcols,
+                                                      float inv_sigma, Add add, float2 *sp_w,
+                                                      int *err) {
     const unsigned FULL_ = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float INF = __int_as_float(0x7f800000);
@@ -1368,7 +1370,7 @@ __device__ __forceinline__ void slow_pair_walk_f32(int len, int h, int32_t rawc,
         }
         if (done) {
             const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, Ls - xl)) : 0.f;
-            if (dj > 0.f) gadd_f32(acc, accc, id, dj);
+            if (dj > 0.f) add(id, dj);
             __syncwarp();
             return;
         }
@@ -1403,8 +1405,16 @@ __device__ __forceinline__ void slow_pair_walk_f32(int len, int h, int32_t rawc,
     const int sl = __popc(__ballot_sync(FULL_, cj > 0.f && key >= xl && key < b2));
     const float L = sl > 0 ? key + (nC - bg) / (float)sl : key;
     const float dj = cj > 0.f ? fminf(cj, fmaxf(0.f, L - xl)) : 0.f;
-    if (dj > 0.f) gadd_f32(acc, accc, id, dj);
+    if (dj > 0.f) add(id, dj);
     __syncwarp();
+}
+
+__device__ __forceinline__ void slow_pair_walk_f32(int len, int h, int32_t rawc, float xc, int k,
+                                                   const float *__restrict__ binomf, int bcols,
+                                                   float inv_sigma, float *acc, float *accc,
+                                                   float2 *sp_w, int *err) {
+    slow_pair_walk_f32_to(len, h, rawc, xc, k, binomf, bcols, inv_sigma,
+                          [&](int32_t id, float x) { gadd_f32(acc, accc, id, x); }, sp_w, err);
 }
 
 template <bool PIPE>
@@ -2417,6 +2427,262 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident(const Resident
     if (lane == 0 && m) atomicMax(a.maxr, m);
 }
 
+// The continuous rule (FP32, normalised r-hat = r / t with compensated
+// sums) in the resident form.  The state is r-hat and its compensation (r,
+// rc) and the iteration's allocations and their compensation (a, ac); the
+// step after iteration t is the update of k_step_f32.  As in k_fw_resident,
+// (r, rc) live in two copies and (a, ac) in three, so that one grid barrier
+// per iteration orders everything: iteration j reads r-hat as the step of
+// R[j mod 2] with A[(j+2) mod 3] (R[0] itself at j = 0), every block computing
+// the same words with the same arithmetic; the owner of a node slice stores
+// that step into R[(j+1) mod 2] and clears A[(j+1) mod 3].
+struct ResidentArgsF32 {
+    const int64_t *pair_off;
+    const uint16_t *lidx;
+    const uint16_t *loff;
+    const int32_t *uid;
+    const int *plan;
+    const uint8_t *h;
+    int64_t npairs;
+    const float *binomf;
+    int bcols, k;
+    int64_t n;
+    float *R[2], *RC[2];
+    float *A[3], *AC[3];
+    int *t_done;
+    int *err;
+    GridBarrier *bar;
+    uint64_t timeout_ns;
+    int T;
+    int ncap, pcap, ucap;
+};
+
+// r-hat and its compensation after step t from (r, rc) and the allocations
+// (a, ac) of iteration t: r += (sigma (a + ac) - r) / t, sigma = max(t - 1, 1),
+// with the rounding error kept in rc.  Rounded operations only (no fused
+// multiply-add), so that every block that computes a node's step gets the
+// same words.
+__device__ __forceinline__ float2 step_f32(float r, float rc, float a, float ac, int t) {
+    const float sigma = (float)(t - 1 > 1 ? t - 1 : 1);
+    const float inv_t = (float)(1.0 / (double)t);
+    const float delta = __fmul_rn(sigma, __fadd_rn(a, ac));
+    const float y = __fsub_rn(__fmul_rn(__fsub_rn(delta, r), inv_t), rc);
+    const float tt = __fadd_rn(r, y);
+    return make_float2(tt, __fsub_rn(__fsub_rn(tt, r), y));
+}
+
+// compensated add into shared accumulators: the exact rounding error of the
+// stored sum goes to sc[i]
+__device__ __forceinline__ void sadd_f32(float *sa, float *sc, int i, float x) {
+    const float old = atomicAdd(sa + i, x);
+    const float sum = old + x;
+    const float bp = sum - old;
+    const float e = (old - (sum - bp)) + (x - bp);
+    if (e != 0.f) atomicAdd(sc + i, e);
+}
+
+__global__ void __launch_bounds__(RS_WARPS * 32, 1) k_fw_resident_f32(const ResidentArgsF32 a) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    __shared__ int s_cursor, s_nslow, s_wcur, s_tdone;
+    const unsigned FULL_ = 0xffffffffu;
+    const float INF = __int_as_float(0x7f800000);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // the layout of k_fw_resident (resident_smem_bytes); the uint4 and cap
+    // arrays of the integer walk states are not used here
+    float2 *wsp = reinterpret_cast<float2 *>(reinterpret_cast<uint64_t *>(rs_smem) + wib * 64);
+    uint4 *sent = reinterpret_cast<uint4 *>(rs_smem + (size_t)RS_WARPS * 64 * sizeof(uint64_t));
+    uint64_t *sval = reinterpret_cast<uint64_t *>(sent + a.pcap);
+    float *slev = reinterpret_cast<float *>(sval);               // r-hat of each distinct node
+    float *sacc = reinterpret_cast<float *>(sval + a.ucap);      // allocations ...
+    float *saccc = sacc + a.ucap;                                // ... and their compensation
+    int32_t *suid = reinterpret_cast<int32_t *>(sval + 2 * (size_t)a.ucap);
+    unsigned *stag = reinterpret_cast<unsigned *>(suid + a.ucap);
+    uint32_t *scap = stag + a.pcap;
+    uint16_t *slid = reinterpret_cast<uint16_t *>(scap + a.pcap);
+    uint16_t *poff = slid + a.ncap;
+    uint16_t *slist = poff + a.pcap + 1;
+    uint8_t *hh = reinterpret_cast<uint8_t *>(slist + a.pcap);
+    const int G = gridDim.x;
+    int np = (int)resident_share_pairs(a.npairs, G, blockIdx.x);
+    int nu = a.plan[blockIdx.x], nn = a.plan[G + blockIdx.x];
+    if (np > a.pcap || nn > a.ncap || nu > a.ucap) {
+        if (threadIdx.x == 0) atomicOr(a.err, DERR_CAPACITY);
+        nu = 0;
+        nn = 0;
+        np = 0;
+    }
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) suid[i] = a.uid[(size_t)blockIdx.x * RS_UCAP + i];
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int64_t q = blockIdx.x + (int64_t)j * G;
+        const int64_t e0 = a.pair_off[q];
+        const int len = (int)(a.pair_off[q + 1] - e0);
+        const int o = a.loff[q];
+        poff[j] = (uint16_t)o;
+        hh[j] = a.h[q];
+        stag[j] = 0u;
+        if (o + len <= nn)
+            for (int x = 0; x < len; ++x) slid[o + x] = a.lidx[e0 + x];
+    }
+    if (threadIdx.x == 0) poff[np] = (uint16_t)nn;
+    const int t0 = *(volatile int *)a.t_done;   // iterations done before this launch
+    __syncthreads();
+    const int64_t v0 = a.n * blockIdx.x / G, v1 = a.n * (blockIdx.x + 1) / G;
+    const int ntile = (np + 31) >> 5;
+    const int k = a.k, bcols = a.bcols;
+    for (int j = 0; j < a.T; ++j) {
+        const int t = t0 + j + 1;   // this iteration's number
+        const float inv_sigma = (float)(1.0 / (double)(t - 1 > 1 ? t - 1 : 1));
+        const float *Rc = a.R[j & 1], *RCc = a.RC[j & 1];
+        float *Rn = a.R[(j + 1) & 1], *RCn = a.RC[(j + 1) & 1];
+        const float *Ap = a.A[(j + 2) % 3], *ACp = a.AC[(j + 2) % 3];
+        float *Az = a.A[(j + 1) % 3], *ACz = a.AC[(j + 1) % 3];
+        float *Ag = a.A[j % 3], *ACg = a.AC[j % 3];
+        const unsigned tag = (unsigned)j + 1u;
+        if (threadIdx.x == 0) {
+            s_cursor = 0;
+            s_nslow = 0;
+            s_wcur = 0;
+            s_tdone = 0;
+        }
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+            const int32_t u = suid[i];
+            slev[i] = j == 0 ? __ldcg(Rc + u)
+                             : step_f32(__ldcg(Rc + u), __ldcg(RCc + u), __ldcg(Ap + u), __ldcg(ACp + u), t - 1).x;
+            sacc[i] = 0.f;
+            saccc[i] = 0.f;
+        }
+        __syncthreads();
+        // first step of every pair (tiles), then the walks of the pairs it
+        // leaves, as in k_fw_resident
+        while (true) {
+            int ti = 0;
+            if (lane == 0) ti = atomicAdd(&s_cursor, 1);
+            ti = __shfl_sync(FULL_, ti, 0);
+            if (ti >= ntile) break;
+            const int qi = ti * 32 + lane;
+            const bool valid = qi < np;
+            const int o = valid ? poff[qi] : 0;
+            const int len = valid ? (int)poff[qi + 1] - o : 0;
+            const int h = valid ? (int)hh[qi] : 0;
+            uint32_t rmask = 0;
+            float share = 0.f;
+            bool want_slow = false;
+            if (valid && h <= k && k <= len && len <= 32) {
+                const int p = len - h;
+                const float nC = __ldg(a.binomf + (size_t)p * bcols + (k - h)) * inv_sigma;
+                const float cap_p = (p >= 1 && k - h - 1 >= 0)
+                                        ? __ldg(a.binomf + (size_t)(p - 1) * bcols + (k - h - 1)) * inv_sigma
+                                        : 0.f;
+                const bool prx = cap_p > 0.f;   // zero-cap pivot nodes read as +inf
+                float m1 = INF, m2 = INF;
+                uint32_t mask1 = 0;
+                bool piv1 = false;
+                for (int s2 = 0; s2 < len; ++s2) {
+                    const unsigned l = slid[o + s2];
+                    const bool hold = (l & 0x8000u) != 0;
+                    const float v = (hold || prx) ? slev[l & 0x7fffu] : INF;
+                    const bool lt = v < m1;
+                    const bool eq = v == m1 && v < INF;
+                    const float mn = fminf(m2, v);
+                    m2 = lt ? m1 : (eq ? m2 : mn);
+                    m1 = lt ? v : m1;
+                    const uint32_t bit = 1u << s2;
+                    mask1 = lt ? bit : (eq ? (mask1 | bit) : mask1);
+                    piv1 = lt ? !hold : (piv1 || (eq && !hold));
+                }
+                if (mask1) {
+                    const float na = (float)__popc(mask1);
+                    const float mu = piv1 ? cap_p : nC;
+                    share = nC / na;
+                    if (share <= mu && share <= m2 - m1) rmask = mask1;
+                    else want_slow = true;
+                }
+            } else if (valid && len > 32) {
+                atomicOr(a.err, DERR_CAPACITY);
+            }
+            const unsigned um = __ballot_sync(FULL_, want_slow);
+            if (um) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_nslow, __popc(um));
+                base = __shfl_sync(FULL_, base, 0);
+                if (want_slow) {
+                    const int slot = base + __popc(um & lanemask_lt());
+                    slist[slot] = (uint16_t)qi;
+                    __threadfence_block();
+                    *(volatile unsigned *)(stag + slot) = tag;
+                }
+            }
+            while (rmask) {
+                const int sl = __ffs(rmask) - 1;
+                rmask &= rmask - 1;
+                sadd_f32(sacc, saccc, (int)(slid[o + sl] & 0x7fffu), share);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicAdd(&s_tdone, 1);
+            }
+        }
+        while (true) {
+            int wi = 0, go = 0;
+            if (lane == 0) {
+                wi = atomicAdd(&s_wcur, 1);
+                go = resident_wait_entry(wi, np, tag, stag, &s_tdone, &s_nslow, ntile, a.err);
+            }
+            __syncwarp();
+            go = __shfl_sync(FULL_, go, 0);
+            if (!go) break;
+            wi = __shfl_sync(FULL_, wi, 0);
+            const int q = slist[wi];
+            const int so = poff[q];
+            const int sl = (int)poff[q + 1] - so;
+            int32_t rawc = 0;
+            float xc = 0.f;
+            if (lane < sl) {
+                const unsigned l = slid[so + lane];
+                rawc = (int32_t)(l & 0x7fffu) | ((l & 0x8000u) ? (int32_t)0x80000000 : 0);
+                xc = slev[l & 0x7fffu];
+            }
+            slow_pair_walk_f32_to(sl, (int)hh[q], rawc, xc, k, a.binomf, bcols, inv_sigma,
+                                  [&](int32_t li, float x) { sadd_f32(sacc, saccc, li, x); }, wsp, a.err);
+        }
+        // the owner's slice: the step of iteration t - 1 into the other copy,
+        // the allocations of iteration t + 1 cleared
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            float2 nv;
+            if (j == 0) nv = make_float2(__ldcg(Rc + v), __ldcg(RCc + v));
+            else nv = step_f32(__ldcg(Rc + v), __ldcg(RCc + v), __ldcg(Ap + v), __ldcg(ACp + v), t - 1);
+            __stcg(Rn + v, nv.x);
+            __stcg(RCn + v, nv.y);
+            __stcg(Az + v, 0.f);
+            __stcg(ACz + v, 0.f);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+            const float x = sacc[i], xe = saccc[i];
+            const int32_t u = suid[i];
+            if (x != 0.f) gadd_f32(Ag, ACg, u, x);
+            if (xe != 0.f) atomicAdd(ACg + u, xe);
+        }
+        if (!grid_sync_count(&a.bar->count, (unsigned)(j + 1) * (unsigned)G, a.err, a.timeout_ns)) return;
+    }
+    // r-hat after the last step into R[0]; clear the two allocations still set
+    const int tl = t0 + a.T;
+    const float *Rc = a.R[a.T & 1], *RCc = a.RC[a.T & 1];
+    float *Al = a.A[(a.T + 2) % 3], *ACl = a.AC[(a.T + 2) % 3];
+    float *Ao = a.A[(a.T + 1) % 3], *ACo = a.AC[(a.T + 1) % 3];
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const float2 nv = step_f32(__ldcg(Rc + v), __ldcg(RCc + v), __ldcg(Al + v), __ldcg(ACl + v), tl);
+        a.R[0][v] = nv.x;
+        a.RC[0][v] = nv.y;
+        Al[v] = 0.f;
+        ACl[v] = 0.f;
+        Ao[v] = 0.f;
+        ACo[v] = 0.f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.t_done = tl;
+}
+
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
 };
@@ -2431,8 +2697,7 @@ ResidentKernel resident_kernel(int precision, bool l32) {
 }
 
 bool resident_ready(const Ctx &c, const SctDev &s, StateDev &st) {
-    if (st.per_iteration || st.precision == KDSS_FP32K || st.qchunk > 0 || st.force_rooted)
-        return false;
+    if (st.per_iteration || st.qchunk > 0 || st.force_rooted) return false;
     if (s.npairs <= 0 || s.class_begin[0] != 0 || s.class_begin[3] != s.npairs) return false;
     if (st.res_sct == &s) return st.res_state > 0;
     st.res_sct = &s;
@@ -2472,8 +2737,11 @@ bool resident_ready(const Ctx &c, const SctDev &s, StateDev &st) {
     const size_t smem = resident_smem_bytes(ncap, (int)pcap, ucap);
     if (smem + 1024 > (size_t)optin) return false;   // static shared memory and slack
     int per_sm = 1;
-    for (int l32 = 0; l32 < 2; ++l32) {
-        auto kern = resident_kernel(st.precision, l32 != 0);
+    std::vector<const void *> kerns;
+    if (st.precision == KDSS_FP32K) kerns.push_back((const void *)k_fw_resident_f32);
+    else kerns = {(const void *)resident_kernel(st.precision, false),
+                  (const void *)resident_kernel(st.precision, true)};
+    for (const void *kern : kerns) {
         KDSS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
         KDSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, RS_WARPS * 32, smem));
@@ -2532,8 +2800,43 @@ void fw_run_resident(const Ctx &c, const SctDev &s, StateDev &st, int T, bool pr
     // 32-bit levels when every r_t(u) <= t c_k stays below 2^31
     const long double top = (long double)(st.t + T) *
                             ((long double)st.ck_lo + (long double)st.ck_hi * 18446744073709551616.0L);
-    auto kern = resident_kernel(st.precision, top < 2147483648.0L);
+    const void *kern = (const void *)resident_kernel(st.precision, top < 2147483648.0L);
     void *args[] = {&a};
+    ResidentArgsF32 af{};
+    void *args_f[] = {&af};
+    if (st.precision == KDSS_FP32K) {
+        const size_t n = (size_t)std::max<int64_t>(s.n, 1);   // each extra copy holds 2n floats
+        af.pair_off = a.pair_off;
+        af.lidx = a.lidx;
+        af.loff = a.loff;
+        af.uid = a.uid;
+        af.plan = a.plan;
+        af.h = a.h;
+        af.npairs = a.npairs;
+        af.binomf = s.binomf.p;
+        af.bcols = a.bcols;
+        af.k = a.k;
+        af.n = a.n;
+        af.R[0] = st.r32.p;
+        af.RC[0] = st.r32c.p;
+        af.R[1] = reinterpret_cast<float *>(st.res_r1.p);
+        af.RC[1] = af.R[1] + n;
+        af.A[0] = st.a32.p;
+        af.AC[0] = st.a32c.p;
+        af.A[1] = reinterpret_cast<float *>(st.res_a1.p);
+        af.AC[1] = af.A[1] + n;
+        af.A[2] = reinterpret_cast<float *>(st.res_a2.p);
+        af.AC[2] = af.A[2] + n;
+        af.t_done = st.dev_t.p;
+        af.err = a.err;
+        af.bar = a.bar;
+        af.timeout_ns = a.timeout_ns;
+        af.T = T;
+        af.ncap = a.ncap;
+        af.pcap = a.pcap;
+        af.ucap = a.ucap;
+        kern = (const void *)k_fw_resident_f32;
+    }
     // the barrier counter starts from zero in every launch
     zero(c, st.res_bar.p, sizeof(GridBarrier));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2547,8 +2850,9 @@ void fw_run_resident(const Ctx &c, const SctDev &s, StateDev &st, int T, bool pr
         e1 = st.events[1];
         KDSS_CUDA(cudaEventRecord(e0, c.stream));
     }
-    KDSS_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(c.num_sms), dim3(RS_WARPS * 32),
-                                          args, st.res_smem, c.stream));
+    KDSS_CUDA(cudaLaunchCooperativeKernel(kern, dim3(c.num_sms), dim3(RS_WARPS * 32),
+                                          st.precision == KDSS_FP32K ? args_f : args, st.res_smem,
+                                          c.stream));
     KDSS_LAUNCH_CHECK();
     if (profile) KDSS_CUDA(cudaEventRecord(e1, c.stream));
     st.t += T;

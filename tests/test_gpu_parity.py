@@ -223,10 +223,16 @@ def test_fw_large_counts_are_bit_exact():
 def test_profiled_and_graph_runs_agree():
     """The profiled per-iteration path (every 8th iteration as separate graphs
     between events, the others fused) and the default path (the resident
-    launch for the integer rule, one graph per iteration for FP32K) give the
-    same r, for every precision."""
+    launch) give the same r for the integer rule.  For the continuous FP32
+    rule the two forms add their allocations in different orders, and the
+    rule's trajectory amplifies rounding differences (a 1e-13 perturbation
+    grows about 100x per 10 iterations), so after 30 iterations they agree in
+    what the iterations fix -- sum r-hat = c_k -- and in the extracted
+    density; per-iteration agreement with the FP64 oracle is tested in
+    test_fp32_one_iteration_matches_fp64_oracle."""
     n, s, d = GRAPHS["rmat2k"]()
     sct = K.kdss_build_sct(n, s, d, 4)
+    ck = K.kdss_sct_info(sct)["c_k"]
     for prec in (K.KDSS_INT64, K.KDSS_FP64, K.KDSS_FP32K):
         a = K.kdss_fw_iterate(sct, None, 30, K.make_opts(
             precision=prec, flags=K.KDSS_FLAG_PROFILE | K.KDSS_FLAG_PER_ITERATION))
@@ -234,7 +240,10 @@ def test_profiled_and_graph_runs_agree():
         ra, _ = K.kdss_state_copy_r(a, n, prec)
         rb, _ = K.kdss_state_copy_r(b, n, prec)
         if prec == K.KDSS_FP32K:
-            assert np.max(np.abs(ra - rb)) <= FP32_RTOL * np.max(np.abs(rb))
+            for r in (ra, rb):
+                assert abs(float(r.astype(np.float64).sum()) - ck) <= FP32_RTOL * ck
+            da, db = K.kdss_extract(sct, a)["density"], K.kdss_extract(sct, b)["density"]
+            assert abs(da - db) <= 0.01 * db
         else:
             assert np.array_equal(ra, rb)
         tm = K.kdss_state_timing(a)
@@ -275,15 +284,18 @@ def test_resume_equals_uninterrupted_run():
     assert ta == tb == 40 and np.array_equal(ra, rb)
 
 
-def _fp32_state(sct, T):
-    return K.kdss_fw_iterate(sct, None, T, K.make_opts(precision=K.KDSS_FP32K)) if T > 0 else None
+def _fp32_state(sct, T, flags=0):
+    return (K.kdss_fw_iterate(sct, None, T, K.make_opts(precision=K.KDSS_FP32K, flags=flags))
+            if T > 0 else None)
 
 
 @pytest.mark.parametrize("name", ["er300", "chunglu3k", "rmat2k"])
 @pytest.mark.parametrize("t", [1, 2, 5, 30, 80])
-def test_fp32_one_iteration_matches_fp64_oracle(name, t):
+@pytest.mark.parametrize("flags", [0, K.KDSS_FLAG_PER_ITERATION])
+def test_fp32_one_iteration_matches_fp64_oracle(name, t, flags):
     """From the GPU's own r_{t-1}/(t-1), one FP32 iteration of the continuous
-    rule equals one FP64 oracle iteration within 1e-5 (relative, inf-norm).
+    rule equals one FP64 oracle iteration within 1e-5 (relative, inf-norm),
+    in the resident launch (default) and in the per-iteration kernels.
     Over many iterations the continuous rule amplifies rounding differences
     (a 1e-13 perturbation grows about 100x per 10 iterations), so agreement is
     checked per iteration, at every horizon."""
@@ -291,9 +303,9 @@ def test_fp32_one_iteration_matches_fp64_oracle(name, t):
     k = 4
     o = oracle_graph(n, s, d, k, K.KDSS_ORDER_PEEL)
     sct = K.kdss_build_sct(n, s, d, k)
-    st = _fp32_state(sct, t - 1)
+    st = _fp32_state(sct, t - 1, flags)
     prev = K.kdss_state_copy_r(st, n, K.KDSS_FP32K)[0].astype(np.float64) if st else np.zeros(n)
-    st = K.kdss_fw_iterate(sct, st, 1, K.make_opts(precision=K.KDSS_FP32K))
+    st = K.kdss_fw_iterate(sct, st, 1, K.make_opts(precision=K.KDSS_FP32K, flags=flags))
     got, tt = K.kdss_state_copy_r(st, n, K.KDSS_FP32K)
     assert tt == t
     want = O.fw_cont(n, o["sct"], k, 1, r0=prev * (t - 1)) / t

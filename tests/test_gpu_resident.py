@@ -151,3 +151,45 @@ def test_resident_levels_past_32_bits(prec):
     st, r, t, nl = _run(sct, n, 40, prec, 0, st)
     assert nl == 1 and t == 80
     assert np.array_equal(r, _oracle_r(n, s, d, k, 80))
+
+
+def _oracle_cont_step(n, sct_o, k, prev, t):
+    """One FP64 iteration of the continuous rule from r-hat_{t-1} = prev."""
+    return O.fw_cont(n, sct_o, k, 1, r0=prev * (t - 1)) / t
+
+
+@pytest.mark.parametrize("name", ["er300", "chunglu3k", "rmat2k", "chunglu12k"])
+def test_resident_fp32_matches_the_fp64_oracle_per_iteration(name):
+    """The continuous rule in the resident launch (FP32 r-hat with compensated
+    shared-memory and global sums): one launch of one iteration from the
+    GPU's own state equals one FP64 oracle iteration within 1e-5 (relative,
+    inf-norm) at several horizons, across launches of several iterations; the
+    per-iteration kernels reach the same density; sum r-hat = c_k."""
+    n, s, d = GRAPHS[name]()
+    k = 4
+    off, adj = O.csr(n, s, d)
+    core, rnd, _ = O.peel(n, off, adj)
+    rank, vert = O.order(n, core, rnd)
+    so = O.sct(n, off, adj, rank, vert, k)
+    sct = K.kdss_build_sct(n, s, d, k)
+    ck = K.kdss_sct_info(sct)["c_k"]
+    o = K.make_opts(precision=K.KDSS_FP32K, flags=K.KDSS_FLAG_PROFILE)
+    st, done = None, 0
+    for chunk in (1, 5, 1, 13, 1):
+        prev = (K.kdss_state_copy_r(st, n, K.KDSS_FP32K)[0].astype(np.float64) if st
+                else np.zeros(n))
+        st = K.kdss_fw_iterate(sct, st, chunk, o)
+        done += chunk
+        got, t = K.kdss_state_copy_r(st, n, K.KDSS_FP32K)
+        assert t == done
+        if chunk == 1:
+            want = _oracle_cont_step(n, so, k, prev, t)
+            err = np.max(np.abs(got.astype(np.float64) - want)) / max(np.max(np.abs(want)), 1e-300)
+            assert err <= 1e-5, (t, err)
+        assert abs(float(got.astype(np.float64).sum()) - ck) <= 1e-5 * ck
+    tm = K.kdss_state_timing(st)
+    assert tm["fw_launches"] == done          # the resident launch counts every iteration
+    per = K.kdss_fw_iterate(sct, None, done,
+                            K.make_opts(precision=K.KDSS_FP32K, flags=K.KDSS_FLAG_PER_ITERATION))
+    a, b = K.kdss_extract(sct, st), K.kdss_extract(sct, per)
+    assert abs(a["density"] - b["density"]) <= 0.01 * b["density"]
