@@ -863,7 +863,8 @@ def main():
     # path times every 8th PBUpdate pass
     resident = fw_launches == T * args.steps and not args.chunk
     fw_src = os.path.join(ROOT, "paper_2403_05775_gb300", "csrc", "fw.cu")
-    traffic = ncu_traffic(fw_src, "fw_resident_chunglu1e5.md" if resident
+    traffic = ncu_traffic(fw_src, ("fw_resident_f32_chunglu1e5.md" if args.precision == "fp32k"
+                                   else "fw_resident_chunglu1e5.md") if resident
                           else "fw_pbupdate_chunglu1e5.md")
     achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
 
@@ -893,9 +894,10 @@ def main():
                             "peak_gbs": l2_gbs, "frac": achieved / l2_gbs if l2_gbs else None},
                      "kernel": ("PBUpdate pass of one FW iteration (k_pb_queue + k_pb_queue_long)"
                                 if args.chunk else
-                                "one FW iteration of the resident launch k_fw_resident (gather of "
-                                "r, PBUpdate of every pair, fold of the delta, grid barrier); "
-                                "launch time / T" if resident else
+                                ("one FW iteration of the resident launch " +
+                                 ("k_fw_resident_f32" if args.precision == "fp32k" else "k_fw_resident") +
+                                 " (gather of r, PBUpdate of every pair, fold of the delta, grid "
+                                 "barrier); launch time / T") if resident else
                                 "PBUpdate pass of one FW iteration (k_pb_fast + k_pb_slow + "
                                 "length-class group kernels)"),
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,
