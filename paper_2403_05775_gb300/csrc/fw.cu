@@ -742,23 +742,38 @@ __device__ __forceinline__ void walk_rel32(uint32_t rl, uint32_t cl, int32_t id,
             // the units end before the next event, or exactly at it
             // (then nothing is left over and L* = ev allocates the
             // same): floor(rem / na) < ev - L, or rem = (ev - L) na,
-            // which is rem <= (ev - L) na; one division at the end
-            const uint64_t span = (uint64_t)(ev - L) * na;
-            if (ev == INF32 || rem <= span) {
-                const uint32_t qd = rem / na;
-                Ls = L + qd;
-                R = rem - qd * na;
-                done = true;
-                break;
+            // which is rem <= (ev - L) na; one division at the end.
+            // With receiving nodes ev is finite (a cap ends below 2^32).
+            // One receiving node (the usual case) needs neither the
+            // 64-bit product nor the division.
+            if (na == 1) {
+                if (rem <= ev - L) {
+                    Ls = L + rem;
+                    R = 0;
+                    done = true;
+                    break;
+                }
+                rem -= ev - L;
+            } else {
+                const uint64_t span = (uint64_t)(ev - L) * na;
+                if (rem <= span) {
+                    const uint32_t qd = rem / na;
+                    Ls = L + qd;
+                    R = rem - qd * na;
+                    done = true;
+                    break;
+                }
+                rem -= (uint32_t)span;
             }
-            rem -= (uint32_t)span;
             L = ev;
         }
         if (done) {
-            const bool elig = Ls - lo < cl;
             uint32_t dj = Ls > lo ? min(Ls - lo, cl) : 0u;
-            const unsigned eb = __ballot_sync(FULL_, elig);
-            if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+            if (R) {   // warp-uniform: the remainder goes to the first R eligible lanes
+                const bool elig = Ls - lo < cl;
+                const unsigned eb = __ballot_sync(FULL_, elig);
+                if (elig && (uint32_t)__popc(eb & lanemask_lt()) < R) dj += 1;
+            }
             if (dj) atomicAdd((AV *)acc + id, (AV)dj);
             __syncwarp();
             return;
