@@ -514,8 +514,8 @@ def fp32_error_vs_oracle(K, n, s_np, d_np, k, T, r32, dens32, rho_oracle):
                     "convergence-error scale; per-iteration agreement (1e-5) is tested"}
 
 
-def config1_er2000(K, torch, dev, stream):
-    """Config 1: G(2000, 0.01) seed 1, k = 3, T = 100 (and the paper's G1):
+def er2000_k3(K, torch, dev, stream):
+    """Erdos-Renyi G(2000, 0.01) from seed 1, k = 3, T = 100 (and the paper's G1):
     device-timed clique-updates/s and the extracted set against the oracle."""
     import oracle as O
     n, s_np, d_np = synth.workload_er2000()
@@ -544,7 +544,7 @@ def config1_er2000(K, torch, dev, stream):
 
 
 def rmat24_count(K, torch, dev, budget_s=30.0):
-    """Config 4 (R-MAT scale 24, edge factor 32, planted 200-node near-clique,
+    """R-MAT scale 24 (edge factor 32, planted 200-node near-clique,
     k = 6, seed 4): the count-only SCT pass measures P_6 without storing a
     pair; roots are taken in a pseudo-random order until the budget ends, so
     the counted roots are a sample and counts * n / roots_done estimates the
@@ -584,8 +584,8 @@ def rmat24_count(K, torch, dev, budget_s=30.0):
 
 
 def batched_upper_range(K, torch, dev, count=256, budget_s=3.0):
-    """Config 3 as specified (n log-uniform in [1e3, 1e5]): the count-only
-    SCT pass on its three largest instances measures why the upper part of
+    """The batch of 256 R-MAT graphs with n log-uniform in [1e3, 1e5]: the
+    count-only SCT pass on its three largest instances measures why the upper part of
     the range cannot be held on one device."""
     ns, ks = synth.batch_rmat_specs(count, nmax=1e5)
     order = np.argsort(-ns)[:3]
@@ -940,9 +940,9 @@ def main():
         except Exception as e:  # the oracle leg is a report, not the measurement
             extras["fp32k"]["error_vs_fp64_oracle"] = {"error": str(e)}
         try:
-            extras["config1"] = config1_er2000(K, torch, dev, stream)
+            extras["er2000_k3"] = er2000_k3(K, torch, dev, stream)
         except Exception as e:
-            extras["config1"] = {"error": str(e)}
+            extras["er2000_k3"] = {"error": str(e)}
         # time to reach 99% of the oracle's density: build, then chunks of 5
         # iterations each followed by an extraction
         target = rho_oracle if rho_oracle is not None else res["density"]
@@ -982,7 +982,7 @@ def main():
             extras["batched"] = batched_rmat(K, torch, dev, stream, flush, args.allocator)
         except K.KdssError as e:
             extras["batched"] = {"error": str(e)}
-        # serving: the config-5 stream (4,000 queries at 200/s on a pool of
+        # serving: the Poisson stream (4,000 queries at 200/s on a pool of
         # 64) with queries iterating in place, the same at a sustainable rate,
         # and the synchronous form at 200/s and at a sustainable rate
         runs = {"serving_in_place": dict(count=4000, rate=200.0, flags=K.KDSS_FLAG_ASYNC),
