@@ -112,7 +112,10 @@ typedef struct kdss_opts {
 /* An undirected graph as a raw edge list.  Duplicates, both orientations and
  * self-loops are allowed; the build drops self-loops and duplicates (Sec. 2's
  * simple graph G(V, E)).  src/dst are host pointers, or device pointers when
- * on_device != 0. */
+ * on_device != 0.  Device edge arrays must be device (or managed) memory of
+ * the device the call runs on at their first and last entries
+ * (cudaPointerGetAttributes); otherwise every call taking the descriptor
+ * returns INVALID_ARG before any launch (a batch marks that query alone). */
 typedef struct kdss_graph_desc {
     int64_t n;
     int64_t m;
@@ -228,7 +231,9 @@ kdss_status kdss_sct_count(const kdss_graph_desc *g, int32_t k, double budget_s,
  * nodes[pair_off[q] .. pair_off[q+1]) with its first h[q] entries the hold
  * set V_h and the rest the pivot set V_p (Sec. 2, Lemma 2.4); 0 <= h <= k <=
  * |V(P)| <= 1024 is required.  Arrays are host pointers, or device pointers when
- * on_device != 0; they are copied.
+ * on_device != 0; they are copied.  Device arrays must be device (or managed)
+ * memory of the current device at their first and last entries
+ * (cudaPointerGetAttributes), else INVALID_ARG before any launch.
  * Errors: INVALID_ARG (sizes, h, k, ids outside [0, n)), OVERFLOW, OOM, CUDA.
  */
 kdss_status kdss_sct_from_pairs(int64_t n, int32_t k, int64_t npairs, const int64_t *pair_off,

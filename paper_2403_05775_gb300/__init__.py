@@ -263,18 +263,33 @@ def make_opts(precision=KDSS_INT64, order=KDSS_ORDER_PEEL, flags=0, stream=None,
     return o
 
 
+def _is_cuda_tensor(a):
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
 def _graph_desc(n, src, dst):
-    """Host numpy int32 arrays, or CUDA int32 tensors (on_device)."""
+    """Host arrays (numpy, lists or CPU tensors; copied by the library), or
+    CUDA int32 tensors on the current device (read in place, on_device)."""
     g = kdss_graph_desc()
     g.n = int(n)
     keep = []
-    if hasattr(src, "data_ptr"):
-        if src.dtype.__str__() != "torch.int32" or not src.is_contiguous() or not src.is_cuda:
-            raise ValueError("device edge arrays must be contiguous CUDA int32 tensors")
+    if _is_cuda_tensor(src) or _is_cuda_tensor(dst):
+        for a in (src, dst):
+            if not _is_cuda_tensor(a) or str(a.dtype) != "torch.int32" or not a.is_contiguous():
+                raise ValueError("device edge arrays: src and dst must both be contiguous "
+                                 "CUDA int32 tensors")
+        if src.numel() != dst.numel():
+            raise ValueError("src and dst differ in length")
+        import torch
+        if src.device != dst.device or src.device.index != torch.cuda.current_device():
+            raise ValueError("src and dst must be on the current CUDA device")
         g.m = src.numel()
         g.src, g.dst, g.on_device = src.data_ptr(), dst.data_ptr(), 1
         keep = [src, dst]
     else:
+        # CPU tensors take the host path
+        src = src.numpy() if hasattr(src, "data_ptr") else src
+        dst = dst.numpy() if hasattr(dst, "data_ptr") else dst
         s = np.ascontiguousarray(src, np.int32)
         d = np.ascontiguousarray(dst, np.int32)
         if s.shape != d.shape:
@@ -382,10 +397,12 @@ def kdss_sct_count(n, src, dst, k, budget_s=0.0, opts: kdss_opts | None = None) 
 
 
 def kdss_sct_from_pairs(n, k, pair_off, nodes, h, opts: kdss_opts | None = None) -> Sct:
-    L = load()
     po = np.ascontiguousarray(pair_off, np.int64)
     nd = np.ascontiguousarray(nodes, np.int32)
     hh = np.ascontiguousarray(h, np.int32)
+    if po.size != hh.size + 1 or po[0] != 0 or int(po[-1]) != nd.size:
+        raise ValueError("pair_off must hold len(h) + 1 offsets from 0 to len(nodes)")
+    L = load()
     out = C.c_void_p()
     _check(L.kdss_sct_from_pairs(int(n), int(k), hh.size, po.ctypes.data, nd.ctypes.data,
                                  hh.ctypes.data, 0, C.byref(opts or make_opts()), C.byref(out)))

@@ -59,6 +59,10 @@ void check_graph(const kdss_graph_desc *g) {
     if (g->m < 0) fail(KDSS_ERR_INVALID_ARG, "m must be >= 0");
     if (g->m > 0 && (!g->src || !g->dst)) fail(KDSS_ERR_INVALID_ARG, "edge arrays are NULL");
     if (g->m > ((int64_t)1 << 30)) fail(KDSS_ERR_UNSUPPORTED, "more than 2^30 edge records");
+    if (g->on_device && g->m > 0) {
+        check_device_array(g->src, (size_t)g->m * sizeof(int32_t), "src");
+        check_device_array(g->dst, (size_t)g->m * sizeof(int32_t), "dst");
+    }
 }
 
 void check_k(int32_t k) {
@@ -248,7 +252,11 @@ kdss_status kdss_sct_from_pairs(int64_t n, int32_t k, int64_t npairs, const int6
         int64_t nn = 0;
         if (npairs > 0) {
             if (on_device) {
+                check_device_array(pair_off, (size_t)(npairs + 1) * sizeof(int64_t), "pair_off");
+                check_device_array(h, (size_t)npairs * sizeof(int32_t), "h");
                 to_host(c, &nn, pair_off + npairs, 1);
+                if (nn < 0) fail(KDSS_ERR_INVALID_ARG, "pair_off[npairs] must be >= 0");
+                check_device_array(nodes, (size_t)nn * sizeof(int32_t), "nodes");
             } else {
                 nn = pair_off[npairs];
                 if (pair_off[0] != 0) fail(KDSS_ERR_INVALID_ARG, "pair_off[0] must be 0");

@@ -330,6 +330,16 @@ void solve_batch(const kdss_query *q, int nq, kdss_result *out, const kdss_opts 
             msgs[i] = "bad query: k in [2, 255], T >= 0, n in [0, 2^31 - 1), m in [0, 2^30], edge arrays";
             continue;
         }
+        if (x.graph.on_device && x.graph.m > 0) {
+            try {
+                check_device_array(x.graph.src, (size_t)x.graph.m * sizeof(int32_t), "src");
+                check_device_array(x.graph.dst, (size_t)x.graph.m * sizeof(int32_t), "dst");
+            } catch (const Error &e) {
+                status[i] = e.code;
+                msgs[i] = e.msg;
+                continue;
+            }
+        }
         Group &g = groups[{x.k, x.T}];
         g.k = x.k;
         g.T = x.T;

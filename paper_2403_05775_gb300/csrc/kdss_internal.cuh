@@ -26,6 +26,12 @@ struct Error {
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 
 #define KDSS_CUDA(call) ::kdss::check_cuda((call), #call, __FILE__, __LINE__)
+// Arrays a caller passes as device memory must be device (or managed) memory
+// of the device the work runs on (`dev`; -1: the current device) from their
+// first to their last byte: the kernels would fault on a host pointer and
+// write another device's memory through a peer pointer.  Throws INVALID_ARG,
+// naming `what`, before any launch.
+void check_device_array(const void *p, size_t bytes, const char *what, int dev = -1);
 // Every kernel launch is followed by KDSS_LAUNCH_CHECK(), which also counts it.
 void count_launch();
 long long launches();               // kernels launched so far (process-wide)

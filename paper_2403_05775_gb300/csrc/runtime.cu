@@ -30,6 +30,32 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
     fail(KDSS_ERR_CUDA, buf);
 }
 
+void check_device_array(const void *p, size_t bytes, const char *what, int dev) {
+    if (bytes == 0) return;
+    if (dev < 0) KDSS_CUDA(cudaGetDevice(&dev));
+    const char *ends[2] = {static_cast<const char *>(p), static_cast<const char *>(p) + (bytes - 1)};
+    for (int i = 0; i < 2; ++i) {
+        cudaPointerAttributes a{};
+        const cudaError_t e = cudaPointerGetAttributes(&a, ends[i]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            char buf[256];
+            snprintf(buf, sizeof buf, "%s: cudaPointerGetAttributes failed: %s", what,
+                     cudaGetErrorString(e));
+            fail(KDSS_ERR_INVALID_ARG, buf);
+        }
+        const bool dev_mem = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+        if (!dev_mem || a.device != dev) {
+            char buf[256];
+            snprintf(buf, sizeof buf,
+                     "%s must be device memory of device %d over its %zu bytes (its %s byte is %s)",
+                     what, dev, bytes, i ? "last" : "first",
+                     dev_mem ? "on another device" : "not device memory");
+            fail(KDSS_ERR_INVALID_ARG, buf);
+        }
+    }
+}
+
 Ctx make_ctx(const kdss_opts *o) {
     Ctx c;
     if (o) {

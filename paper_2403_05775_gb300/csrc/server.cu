@@ -382,6 +382,10 @@ kdss_status kdss_server_submit(kdss_server *s, const kdss_query *q, int64_t *tic
         if (g.n < 0 || g.n >= (int64_t)INT32_MAX) fail(KDSS_ERR_INVALID_ARG, "n must be in [0, 2^31 - 1)");
         if (g.m < 0 || g.m > ((int64_t)1 << 30)) fail(KDSS_ERR_INVALID_ARG, "m must be in [0, 2^30]");
         if (g.m > 0 && (!g.src || !g.dst)) fail(KDSS_ERR_INVALID_ARG, "edge arrays are NULL");
+        if (g.m > 0 && g.on_device) {
+            check_device_array(g.src, (size_t)g.m * sizeof(int32_t), "src", s->bctx.device);
+            check_device_array(g.dst, (size_t)g.m * sizeof(int32_t), "dst", s->bctx.device);
+        }
         std::unique_ptr<Query> x(new Query());
         x->k = q->k;
         x->T = q->T;
