@@ -867,6 +867,18 @@ def main():
                                    else "fw_resident_chunglu1e5.md") if resident
                           else "fw_pbupdate_chunglu1e5.md")
     achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
+    # the same work counted per pair and per pair node, over the whole step
+    # and over the FW iterations alone (T times the mean iteration time)
+    step_s = total_ms / args.steps / 1e3
+    fw_s = avg_s * T
+    rates = {"note": "value is T c_k per whole step (build, T iterations, extraction); the "
+                     "*_fw rates divide the same work by the FW iterations' CUDA-event time",
+             "clique_updates_per_s_fw": T * ck * world / fw_s if fw_s > 0 else None,
+             "path_updates_per_s": T * info["eta_k"] * world / step_s,
+             "path_updates_per_s_fw": T * info["eta_k"] * world / fw_s if fw_s > 0 else None,
+             "node_visits_per_s": T * info["L_k"] * world / step_s,
+             "node_visits_per_s_fw": T * info["L_k"] * world / fw_s if fw_s > 0 else None,
+             "fw_ms_per_step": fw_s * 1e3}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -902,6 +914,7 @@ def main():
                                 "length-class group kernels)"),
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,
                      "peak_source": f"{peak_kind} hbm_gbs"},
+        "rates": rates,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
