@@ -116,18 +116,24 @@ def code_digest(path):
     return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
 
 
-def ncu_traffic(kernel_src, summary="fw_resident_chunglu1e5.md"):
-    """Per-iteration DRAM bytes of the FW kernels from the committed ncu
-    summary, or None when the kernel code changed since it was taken."""
+def ncu_figure(kernel_src, summary, field):
+    """A per-iteration figure of the FW kernels (DRAM bytes, warp
+    instructions) from the committed ncu summary, or None when the kernel
+    code changed since it was taken."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_iteration:\s*([0-9.eE+]+)", text)
+    m = re.search(field + r":\s*([0-9.eE+]+)", text)
     h = re.search(r"fw\.cu code digest:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
     return float(m.group(1)) if code_digest(kernel_src) == h.group(1) else None
+
+
+def ncu_traffic(kernel_src, summary="fw_resident_chunglu1e5.md"):
+    """Per-iteration DRAM bytes of the FW kernels (ncu), or None."""
+    return ncu_figure(kernel_src, summary, "traffic_bytes_per_iteration")
 
 
 class ClockSampler:
@@ -863,10 +869,26 @@ def main():
     # path times every 8th PBUpdate pass
     resident = fw_launches == T * args.steps and not args.chunk
     fw_src = os.path.join(ROOT, "paper_2403_05775_gb300", "csrc", "fw.cu")
-    traffic = ncu_traffic(fw_src, ("fw_resident_f32_chunglu1e5.md" if args.precision == "fp32k"
-                                   else "fw_resident_chunglu1e5.md") if resident
-                          else "fw_pbupdate_chunglu1e5.md")
+    prof = (("fw_resident_f32_chunglu1e5.md" if args.precision == "fp32k"
+             else "fw_resident_chunglu1e5.md") if resident else "fw_pbupdate_chunglu1e5.md")
+    traffic = ncu_traffic(fw_src, prof)
     achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
+    # the ceiling the resident launch works against: instruction issue, one
+    # warp instruction per cycle on each of an SM's four schedulers, at the SM
+    # clock sampled during the timed region
+    clocks = clk.summary()
+    winst = ncu_figure(fw_src, prof, "warp_instructions_per_iteration")
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    issue = None
+    if winst and mhz and avg_s > 0:
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_ips = nsm * 4 * mhz * 1e6
+        issue = {"warp_instructions_per_iteration": winst,
+                 "achieved_warp_inst_per_s": winst / avg_s, "peak_warp_inst_per_s": peak_ips,
+                 "frac": winst / avg_s / peak_ips, "sms": nsm, "schedulers_per_sm": 4,
+                 "sm_mhz": mhz,
+                 "source": f"warp instructions from the committed ncu capture (profiles/{prof}), "
+                           "iteration time from this run's CUDA events"}
     # the same work counted per pair and per pair node, over the whole step
     # and over the FW iterations alone (T times the mean iteration time)
     step_s = total_ms / args.steps / 1e3
@@ -913,10 +935,10 @@ def main():
                                 "PBUpdate pass of one FW iteration (k_pb_fast + k_pb_slow + "
                                 "length-class group kernels)"),
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_s * 1e6,
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+                     "peak_source": f"{peak_kind} hbm_gbs", "issue": issue},
         "rates": rates,
         "cpu_baseline": cpu,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "gpu_launches": int(launches),
         "result": {"istar": res["istar"], "count": res["count"], "density": res["density"],
                    "upper_bound": res["upper_bound"], "gap": res["gap"]},
