@@ -55,6 +55,17 @@ typedef int32_t kdss_status;
 #define KDSS_FP64 1
 #define KDSS_FP32K 2
 
+/* PBUpdate rule (kdss_opts.rule).  INTEGER: Alg. 3 as written (whole units,
+ * the remainder to the lowest ids of the last plateau, Sec. 3.2); its r is
+ * held in KDSS_INT64 or KDSS_FP64.  CONTINUOUS: the same water-filling with
+ * a real water level and no floor or remainder (what Alg. 3's unit-by-unit
+ * filling tends to as the units shrink); it runs in KDSS_FP32K.  DEFAULT: the
+ * rule of the precision.  A rule its precision does not hold is
+ * KDSS_ERR_UNSUPPORTED. */
+#define KDSS_RULE_DEFAULT 0
+#define KDSS_RULE_INTEGER 1
+#define KDSS_RULE_CONTINUOUS 2
+
 /* Vertex order of the SCT build.  PEEL: key (peel round, id), a degeneracy
  * order (every vertex has at most core(v) <= delta later neighbours).  CORE:
  * key (core number, id); reproduces the paper's Example 2.2 on its graph G1
@@ -107,6 +118,8 @@ typedef struct kdss_opts {
                                kdss_fw_iterate / kdss_solve: 0 = the per-class kernels) */
     int32_t threads_per_path; /* lanes per pair of 33..256 nodes in the work-queue kernels:
                                8 or 32 (0 = autotuned in batches, 32 otherwise) */
+    int32_t rule;           /* KDSS_RULE_*: 0 = the precision's rule; INTEGER with KDSS_INT64 or
+                               KDSS_FP64, CONTINUOUS with KDSS_FP32K (else UNSUPPORTED) */
 } kdss_opts;
 
 /* An undirected graph as a raw edge list.  Duplicates, both orientations and

@@ -33,6 +33,9 @@ KDSS_ERR_UNSUPPORTED = -8
 KDSS_INT64 = 0
 KDSS_FP64 = 1
 KDSS_FP32K = 2
+KDSS_RULE_DEFAULT = 0
+KDSS_RULE_INTEGER = 1
+KDSS_RULE_CONTINUOUS = 2
 KDSS_ORDER_PEEL = 0
 KDSS_ORDER_CORE = 1
 KDSS_FLAG_PROFILE = 1
@@ -50,7 +53,7 @@ class kdss_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("order", C.c_int32), ("flags", C.c_uint32),
                 ("check_every", C.c_int32), ("eps_stop", C.c_double), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("chunk", C.c_int32), ("threads_per_path", C.c_int32)]
+                ("chunk", C.c_int32), ("threads_per_path", C.c_int32), ("rule", C.c_int32)]
 
 
 class kdss_batch_tuning(C.Structure):
@@ -240,12 +243,14 @@ _FREE_CB = FREE_FN(_torch_free)
 
 def make_opts(precision=KDSS_INT64, order=KDSS_ORDER_PEEL, flags=0, stream=None,
               allocator="torch", check_every=0, eps_stop=0.0, chunk=0,
-              threads_per_path=0) -> kdss_opts:
+              threads_per_path=0, rule=KDSS_RULE_DEFAULT) -> kdss_opts:
     """Build a kdss_opts.  stream: a torch.cuda.Stream, a raw cudaStream_t
     (int) or None (torch's current stream when torch is present).
-    allocator: 'torch' (caching allocator) or 'library' (cudaMallocAsync)."""
+    allocator: 'torch' (caching allocator) or 'library' (cudaMallocAsync).
+    rule: KDSS_RULE_DEFAULT (the precision's rule), KDSS_RULE_INTEGER or
+    KDSS_RULE_CONTINUOUS (checked against the precision by the library)."""
     o = kdss_opts()
-    o.precision, o.order, o.flags = precision, order, flags
+    o.precision, o.order, o.flags, o.rule = precision, order, flags, int(rule)
     o.check_every, o.eps_stop = check_every, eps_stop
     o.chunk, o.threads_per_path = int(chunk), int(threads_per_path)
     t = _torch()

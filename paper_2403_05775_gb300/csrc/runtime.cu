@@ -66,6 +66,14 @@ Ctx make_ctx(const kdss_opts *o) {
         c.flags = o->flags;
         if ((c.alloc == nullptr) != (c.free == nullptr))
             fail(KDSS_ERR_INVALID_ARG, "opts.alloc and opts.free must be set together");
+        if (o->rule < KDSS_RULE_DEFAULT || o->rule > KDSS_RULE_CONTINUOUS)
+            fail(KDSS_ERR_INVALID_ARG, "unknown rule");
+        if (o->rule == KDSS_RULE_INTEGER && o->precision == KDSS_FP32K)
+            fail(KDSS_ERR_UNSUPPORTED, "KDSS_FP32K runs the continuous rule; the integer rule of "
+                                       "Alg. 3 is held in KDSS_INT64 or KDSS_FP64");
+        if (o->rule == KDSS_RULE_CONTINUOUS && o->precision != KDSS_FP32K)
+            fail(KDSS_ERR_UNSUPPORTED, "the continuous rule runs in KDSS_FP32K; KDSS_INT64 and "
+                                       "KDSS_FP64 hold the integer rule of Alg. 3");
     }
     KDSS_CUDA(cudaGetDevice(&c.device));
     KDSS_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));

@@ -136,3 +136,29 @@ def test_binding_checks_both_edge_tensors(torch_cuda):
     assert sorted(res["ids"].tolist()) == want
     res = K.kdss_solve(n, torch.from_numpy(s), torch.from_numpy(d), 3, 100)   # CPU tensors
     assert sorted(res["ids"].tolist()) == want
+
+
+@pytest.mark.gpu
+def test_rule_option_is_checked_against_the_precision(torch_cuda):
+    """kdss_opts.rule: the default and the matching rule give the precision's
+    rule; a rule the precision does not hold, or an unknown one, is refused."""
+    n, s, d = _g1_arrays()
+    sct = K.kdss_build_sct(n, s, d, 3)
+    base = K.kdss_state_copy_r(K.kdss_fw_iterate(sct, None, 20), n, K.KDSS_INT64)[0]
+    st = K.kdss_fw_iterate(sct, None, 20, K.make_opts(rule=K.KDSS_RULE_INTEGER))
+    assert np.array_equal(K.kdss_state_copy_r(st, n, K.KDSS_INT64)[0], base)
+    st = K.kdss_fw_iterate(sct, None, 100, K.make_opts(precision=K.KDSS_FP32K,
+                                                       rule=K.KDSS_RULE_CONTINUOUS))
+    assert abs(K.kdss_extract(sct, st)["density"] - 4.0 / 3.0) < 1e-12
+    for prec, rule, code in ((K.KDSS_FP32K, K.KDSS_RULE_INTEGER, K.KDSS_ERR_UNSUPPORTED),
+                             (K.KDSS_INT64, K.KDSS_RULE_CONTINUOUS, K.KDSS_ERR_UNSUPPORTED),
+                             (K.KDSS_FP64, K.KDSS_RULE_CONTINUOUS, K.KDSS_ERR_UNSUPPORTED),
+                             (K.KDSS_INT64, 7, K.KDSS_ERR_INVALID_ARG)):
+        with pytest.raises(K.KdssError) as e:
+            K.kdss_fw_iterate(sct, None, 5, K.make_opts(precision=prec, rule=rule))
+        assert e.value.code == code
+        with pytest.raises(K.KdssError) as e:
+            K.kdss_solve(n, s, d, 3, 5, K.make_opts(precision=prec, rule=rule))
+        assert e.value.code == code
+    _g1_still_solves()
+
