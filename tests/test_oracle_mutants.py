@@ -64,6 +64,11 @@ MUTANTS = {
         "            rc = orc_pbupdate_alg3(len, ids, rv, hcnt[q], k, dv);\n"
         "            if (rc) break;\n"
         "            for (int i = 0; i < len; ++i) r[ids[i]] += dv[i];"),
+    "rho_prime_pair_enters_before_its_pivot_nodes": (
+        "int32_t mall = mh;\n        for (int j = 0; j < p; ++j) if (pp[j] > mall) mall = pp[j];",
+        "int32_t mall = mh;"),
+    "rho_prime_counts_one_per_pair": (
+        "facc[mall + 1] += binom128(p, k - h);", "facc[mall + 1] += 1;"),
     "plateau_gap_ignored": (
         "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
         "if (nC / (uint64_t)na < w)"),
@@ -86,6 +91,7 @@ PINS = [
     P.test_g1_continuous_iterations_match_hand_trace,
     P.test_g1_continuous_rule_converges_to_sct_cp_optimum,
     P.test_fw_cont_and_fw_seq_invariants_and_weak_duality,
+    P.test_rho_prime_prefix_counts_equal_their_definition,
 ]
 
 

@@ -501,6 +501,33 @@ def test_prefix_counts_from_pairs_equal_explicit_list():
             assert a.tolist() == b.tolist() and ah.tolist() == bh.tolist()
 
 
+def test_rho_prime_prefix_counts_equal_their_definition():
+    """F_i, the numerator of rho'(V_i) (Thm 3.6: the cliques of the pairs P
+    whose node set V(P) lies inside V_i, n_C = C(|V_p|, k - |V_h|) each, Lemma
+    2.6), equals a direct count over the pairs for every prefix of a random
+    order; a pair enters once its last node does."""
+    rng = np.random.default_rng(5)
+    for seed in range(4):
+        n, s, d = _planted(40, 0.15, 10, 120 + seed)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        for k in (3, 4):
+            sc = O.sct(n, off, adj, rank, vert, k)
+            pm, ph, nodes = sc["pair_off"], sc["h"], sc["nodes"]
+            ordr = rng.permutation(n).astype(np.int32)
+            pos = np.empty(n, np.int64)
+            pos[ordr] = np.arange(n)
+            want = [0] * (n + 1)
+            for q in range(len(ph)):
+                seg = nodes[pm[q]:pm[q + 1]]
+                enter = int(pos[seg].max()) + 1          # V(P) inside V_i from i = enter on
+                nc = O.binom(len(seg) - int(ph[q]), k - int(ph[q]))
+                for i in range(enter, n + 1):
+                    want[i] += nc
+            _, _, flo, fhi = O.prefix_counts_pairs(n, ordr, sc, k)
+            got = [int(a) | (int(b) << 64) for a, b in zip(flo, fhi)]
+            assert got == want
+
+
 def test_argmax_takes_the_largest_prefix_on_ties():
     lo = np.array([0, 1, 2, 3, 3, 5, 6], np.uint64)   # 1/1 = 2/2 = 3/3 = 6/6
     hi = np.zeros(7, np.uint64)
