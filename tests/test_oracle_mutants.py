@@ -69,6 +69,37 @@ MUTANTS = {
         "int32_t mall = mh;"),
     "rho_prime_counts_one_per_pair": (
         "facc[mall + 1] += binom128(p, k - h);", "facc[mall + 1] += 1;"),
+    # the round counter moves only when the level rises, so the rounds of one
+    # level merge (cores stay right; the order of the SCT build changes)
+    "peel_round_advances_only_with_the_level": (
+        "            c = mn;\n"
+        "            continue;\n"
+        "        }\n"
+        "        for (int64_t i = 0; i < ns; ++i) {\n"
+        "            alive[S[i]] = 0; core[S[i]] = (int32_t)c; round_out[S[i]] = (int32_t)rnd;\n"
+        "        }\n"
+        "        for (int64_t i = 0; i < ns; ++i) {\n"
+        "            int32_t v = S[i];\n"
+        "            for (int64_t e = off[v]; e < off[v + 1]; ++e)\n"
+        "                if (alive[adj[e]]) deg[adj[e]]--;\n"
+        "        }\n"
+        "        if (c > maxcore) maxcore = c;\n"
+        "        removed += ns;\n"
+        "        rnd++;\n",
+        "            c = mn;\n"
+        "            rnd++;\n"
+        "            continue;\n"
+        "        }\n"
+        "        for (int64_t i = 0; i < ns; ++i) {\n"
+        "            alive[S[i]] = 0; core[S[i]] = (int32_t)c; round_out[S[i]] = (int32_t)rnd;\n"
+        "        }\n"
+        "        for (int64_t i = 0; i < ns; ++i) {\n"
+        "            int32_t v = S[i];\n"
+        "            for (int64_t e = off[v]; e < off[v + 1]; ++e)\n"
+        "                if (alive[adj[e]]) deg[adj[e]]--;\n"
+        "        }\n"
+        "        if (c > maxcore) maxcore = c;\n"
+        "        removed += ns;\n"),
     "plateau_gap_ignored": (
         "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
         "if (nC / (uint64_t)na < w)"),
@@ -92,6 +123,7 @@ PINS = [
     P.test_g1_continuous_rule_converges_to_sct_cp_optimum,
     P.test_fw_cont_and_fw_seq_invariants_and_weak_duality,
     P.test_rho_prime_prefix_counts_equal_their_definition,
+    P.test_peel_rounds_satisfy_their_definition,
 ]
 
 

@@ -183,6 +183,31 @@ def test_csr_and_core_numbers_against_networkx():
             assert later <= core[v]
 
 
+def test_peel_rounds_satisfy_their_definition():
+    """The rounds of the peeling that orders the SCT build (Sec. 2's
+    degeneracy; the key (round, id) of the vertex order).  The rounds are
+    checked against the conditions that fix them, not recomputed: round r at
+    level L removes exactly the present vertices with at most L present
+    neighbours, and L rises, to the smallest present degree, only when no
+    present vertex is at or below it; every vertex is removed."""
+    for seed in range(4):
+        n, s, d, _ = synth.chung_lu(300, 8.0, 2.3, 40 + seed, plant_size=12, plant_prob=0.8)
+        off, adj, core, rnd, dg, rank, vert = _graph(n, s, d)
+        alive = np.ones(n, bool)
+        level = 0
+        for r in range(int(rnd.max()) + 1):
+            deg = np.array([int(alive[adj[off[v]:off[v + 1]]].sum()) for v in range(n)])
+            take = rnd == r
+            levels = set(core[take].tolist())
+            assert len(levels) == 1, (seed, r)
+            lr = levels.pop()
+            assert lr == max(level, int(deg[alive].min()))
+            assert np.array_equal(take, alive & (deg <= lr)), (seed, r)
+            alive &= ~take
+            level = lr
+        assert not alive.any() and dg == level
+
+
 # ---------------------------------------------------------------------------
 # The SCT against the explicit clique list (Lemmas 2.4-2.6)
 # ---------------------------------------------------------------------------
