@@ -100,6 +100,12 @@ MUTANTS = {
         "        }\n"
         "        if (c > maxcore) maxcore = c;\n"
         "        removed += ns;\n"),
+    "final_sort_u64_ties_to_descending_ids": (
+        "if (g_key_u[x] != g_key_u[y]) return g_key_u[x] > g_key_u[y] ? -1 : 1;\n    return x < y ? -1 : x > y;",
+        "if (g_key_u[x] != g_key_u[y]) return g_key_u[x] > g_key_u[y] ? -1 : 1;\n    return x > y ? -1 : x < y;"),
+    "final_sort_f64_ties_to_descending_ids": (
+        "if (g_key_d[x] != g_key_d[y]) return g_key_d[x] > g_key_d[y] ? -1 : 1;\n    return x < y ? -1 : x > y;",
+        "if (g_key_d[x] != g_key_d[y]) return g_key_d[x] > g_key_d[y] ? -1 : 1;\n    return x > y ? -1 : x < y;"),
     "plateau_gap_ignored": (
         "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
         "if (nC / (uint64_t)na < w)"),
@@ -124,6 +130,7 @@ PINS = [
     P.test_fw_cont_and_fw_seq_invariants_and_weak_duality,
     P.test_rho_prime_prefix_counts_equal_their_definition,
     P.test_peel_rounds_satisfy_their_definition,
+    P.test_final_sort_is_r_descending_with_ties_to_ascending_ids,
 ]
 
 

@@ -553,6 +553,20 @@ def test_rho_prime_prefix_counts_equal_their_definition():
             assert got == want
 
 
+def test_final_sort_is_r_descending_with_ties_to_ascending_ids():
+    """The node order of the extraction (Alg. 2's final sort; reading R4 for
+    ties) against numpy's lexicographic sort on the keys (-r, id), for
+    integer and FP64 r with many ties."""
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 7, 300, 2000):
+        ru = rng.integers(0, 6, n).astype(np.uint64) * np.uint64(1 << 40)
+        want = np.lexsort((np.arange(n), -ru.astype(np.float64)))
+        assert O.sort_desc(ru).tolist() == want.tolist()
+        rf = rng.integers(0, 6, n).astype(np.float64) / 3.0
+        want = np.lexsort((np.arange(n), -rf))
+        assert O.sort_desc(rf).tolist() == want.tolist()
+
+
 def test_argmax_takes_the_largest_prefix_on_ties():
     lo = np.array([0, 1, 2, 3, 3, 5, 6], np.uint64)   # 1/1 = 2/2 = 3/3 = 6/6
     hi = np.zeros(7, np.uint64)
