@@ -106,6 +106,43 @@ MUTANTS = {
     "final_sort_f64_ties_to_descending_ids": (
         "if (g_key_d[x] != g_key_d[y]) return g_key_d[x] > g_key_d[y] ? -1 : 1;\n    return x < y ? -1 : x > y;",
         "if (g_key_d[x] != g_key_d[y]) return g_key_d[x] > g_key_d[y] ? -1 : 1;\n    return x > y ? -1 : x < y;"),
+    # the synchronous iterations add each pair's units into r at once, so later
+    # pairs of the iteration read them (the in-place form of Alg. 2)
+    "sync_pairs_update_r_in_place": (
+        "            for (int i = 0; i < len; ++i) dr[ids[i]] += dv[i];\n"
+        "        }\n"
+        "        for (int64_t v = 0; v < n; ++v) r[v] += dr[v];\n"
+        "    }\n"
+        "    free(dr); free(rv); free(dv);\n"
+        "    return rc;\n"
+        "}\n"
+        "\n"
+        "/* The synchronous iterations of orc_fw_sync with",
+        "            for (int i = 0; i < len; ++i) r[ids[i]] += dv[i];\n"
+        "        }\n"
+        "        for (int64_t v = 0; v < n; ++v) r[v] += 0;\n"
+        "    }\n"
+        "    free(dr); free(rv); free(dv);\n"
+        "    return rc;\n"
+        "}\n"
+        "\n"
+        "/* The synchronous iterations of orc_fw_sync with"),
+    # the synchronous iterations keep summing into the previous iteration's delta
+    "sync_delta_not_cleared": (
+        "    for (int t = 1; t <= T && rc == ORC_OK; ++t) {\n"
+        "        memset(dr, 0, sizeof(uint64_t) * (size_t)n);\n"
+        "        for (int64_t q = 0; q < npairs; ++q) {\n"
+        "            int len = (int)(pair_off[q + 1] - pair_off[q]);\n"
+        "            const int32_t *ids = nodes + pair_off[q];\n"
+        "            for (int i = 0; i < len; ++i) rv[i] = r[ids[i]];\n"
+        "            rc = orc_pbupdate_alg3(",
+        "    memset(dr, 0, sizeof(uint64_t) * (size_t)n);\n"
+        "    for (int t = 1; t <= T && rc == ORC_OK; ++t) {\n"
+        "        for (int64_t q = 0; q < npairs; ++q) {\n"
+        "            int len = (int)(pair_off[q + 1] - pair_off[q]);\n"
+        "            const int32_t *ids = nodes + pair_off[q];\n"
+        "            for (int i = 0; i < len; ++i) rv[i] = r[ids[i]];\n"
+        "            rc = orc_pbupdate_alg3("),
     "plateau_gap_ignored": (
         "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
         "if (nC / (uint64_t)na < w)"),
