@@ -18,6 +18,11 @@ import pytest
 import oracle as O
 import test_oracle_pins as P
 
+try:   # the CPSample pins compare with networkx
+    import test_oracle_cpsample as CP
+except ImportError:  # pragma: no cover - networkx missing
+    CP = None
+
 MUTANTS = {
     "pivot_cap_drops_the_minus_one": (
         "uint64_t up_p = orc_binom(p - 1, k - h - 1, &ovf);",
@@ -143,6 +148,14 @@ MUTANTS = {
         "            const int32_t *ids = nodes + pair_off[q];\n"
         "            for (int i = 0; i < len; ++i) rv[i] = r[ids[i]];\n"
         "            rc = orc_pbupdate_alg3("),
+    # CPSample (Alg. 4): colours taken in ascending instead of descending
+    # rank; the sample rank drawn from 52 instead of 53 bits of the word
+    "colour_in_rank_ascending": (
+        "qsort(ord, (size_t)n, sizeof(int32_t), cmp_rank_desc);",
+        "qsort(ord, (size_t)n, sizeof(int32_t), cmp_key);"),
+    "sample_rank_uses_52_bits": (
+        "uint64_t R = (uint64_t)(((unsigned __int128)(x >> 11) * tot) >> 53);",
+        "uint64_t R = (uint64_t)(((unsigned __int128)(x >> 12) * tot) >> 53);"),
     "plateau_gap_ignored": (
         "if (gap < w) w = gap;\n            if (nC / (uint64_t)na < w)",
         "if (nC / (uint64_t)na < w)"),
@@ -169,10 +182,17 @@ PINS = [
     P.test_peel_rounds_satisfy_their_definition,
     P.test_final_sort_is_r_descending_with_ties_to_ascending_ids,
 ]
+CPSAMPLE_MUTANTS = {"colour_in_rank_ascending", "sample_rank_uses_52_bits"}
+if CP is not None:
+    PINS += [lambda: CP.test_greedy_colouring_is_networkx_greedy_in_the_same_order(1),
+             lambda: CP.test_each_sample_is_the_path_of_its_rank(1),
+             CP.test_cpsample_finds_the_example_densest_subgraph]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path, monkeypatch):
+    if name in CPSAMPLE_MUTANTS and CP is None:
+        pytest.skip("the CPSample pins need networkx")
     old, new = MUTANTS[name]
     src = open(O.SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not unique"
