@@ -38,3 +38,23 @@ def test_generators_are_deterministic():
     assert all(np.array_equal(x, y) for x, y in zip(a[1:], b[1:]))
     c = synth.batch_rmat_graph(6, 1234)
     assert not np.array_equal(a[1], c[1])
+
+
+def test_chung_lu_benchmark_graph_has_the_stated_shape():
+    """The benchmark workload (Chung-Lu, n = 1e5, mean degree 20, degree
+    exponent 2.5, a planted 60-node near-clique at edge probability 0.9,
+    seed 2): the simple graph keeps a mean degree near 20 after duplicates
+    and self-loops go, the planted nodes are adjacent with probability near
+    0.9, and the degrees are heavy-tailed (the largest far above the mean)."""
+    n, s, d, planted = synth.chung_lu(100_000, 20.0, 2.5, 2, plant_size=60, plant_prob=0.9)
+    keep = s != d
+    u, v = np.minimum(s[keep], d[keep]), np.maximum(s[keep], d[keep])
+    key = np.unique(u.astype(np.int64) * n + v)
+    m = key.size
+    assert n == 100_000 and 19.0 < 2 * m / n < 21.0
+    deg = np.bincount(np.concatenate([key // n, key % n]), minlength=n)
+    assert deg.max() > 20 * 2 * m / n
+    pset = np.zeros(n, bool)
+    pset[planted] = True
+    inside = np.count_nonzero(pset[key // n] & pset[key % n])
+    assert planted.size == 60 and 0.85 < inside / (60 * 59 / 2) < 0.95
