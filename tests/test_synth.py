@@ -58,3 +58,19 @@ def test_chung_lu_benchmark_graph_has_the_stated_shape():
     pset[planted] = True
     inside = np.count_nonzero(pset[key // n] & pset[key % n])
     assert planted.size == 60 and 0.85 < inside / (60 * 59 / 2) < 0.95
+
+
+def test_batch_and_serving_recipes():
+    """The batched workload's 256 instances: n log-uniform in [1e3, 1e5]
+    (about half below the geometric midpoint 1e4) and k uniform in {3..8};
+    the serving stream: exponential gaps of mean 1/200 s, k uniform in
+    {3..10}, queries spread over the whole pool."""
+    ns, ks = synth.batch_rmat_specs(256)
+    assert ns.size == ks.size == 256 and ns.min() >= 1000 and ns.max() <= 100_000
+    assert 100 < np.count_nonzero(ns < 10_000) < 156
+    assert set(ks.tolist()) == set(range(3, 9))
+    t, g, k = synth.serving_stream(4000, 200.0, 64)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0) and abs(gaps.mean() * 200.0 - 1.0) < 0.05
+    assert abs(np.std(gaps) / gaps.mean() - 1.0) < 0.08     # exponential: cv = 1
+    assert set(k.tolist()) == set(range(3, 11)) and set(g.tolist()) == set(range(64))
