@@ -74,3 +74,16 @@ def test_batch_and_serving_recipes():
     assert np.all(gaps > 0) and abs(gaps.mean() * 200.0 - 1.0) < 0.05
     assert abs(np.std(gaps) / gaps.mean() - 1.0) < 0.08     # exponential: cv = 1
     assert set(k.tolist()) == set(range(3, 11)) and set(g.tolist()) == set(range(64))
+
+
+def test_er2000_has_the_expected_edges_and_triangles():
+    """G(2000, 0.01) from seed 1: about C(2000, 2) p = 19,990 edges and
+    C(2000, 3) p^3 = 1,331 triangles expected (each within a few standard
+    deviations), counted by the oracle's explicit listing."""
+    import oracle as O
+    n, s, d = synth.workload_er2000()
+    off, adj = O.csr(n, s, d)
+    m = adj.size // 2
+    assert n == 2000 and abs(m - 19_990) < 5 * np.sqrt(19_990)
+    c3 = O.count_cliques(n, off, adj, 3)
+    assert abs(c3 - 1331) < 6 * np.sqrt(1331)
